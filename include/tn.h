@@ -1,0 +1,220 @@
+/*
+ * tn.h -- C ABI of a single-GPU (sm_103a) sliced tensor-network contractor for
+ * random-quantum-circuit amplitudes, after arXiv 2111.01066
+ * ("Redefining the Quantum Supremacy Baseline With a New Generation Sunway
+ * Supercomputer").
+ *
+ * The problem, in the paper's terms:
+ *   - a circuit amplitude <x|U|0...0> is the contraction of a tensor network in
+ *     which gates are rank-2 / rank-4 tensors and the initial state and the
+ *     target basis are rank-1 tensors (SI, TN section, figure S2);
+ *   - the network is contracted pairwise along an order (a list of two-tuples)
+ *     found on the host (SI, TN section);
+ *   - index slicing fixes a set of wires so that the network is a sum of 2^S
+ *     smaller networks, each contracted alone (main text, section II);
+ *   - leaving k qubits open yields 2^k correlated amplitudes in one run (main
+ *     text, section III);
+ *   - the linear XEB fidelity follows from amplitudes (main text, Eq. (1)).
+ *
+ * Conventions used by every call:
+ *   - qubit q is bit q of a uint64_t; n_qubits <= 64;
+ *   - the index of an amplitude inside a batch is sum_j b(open_j) 2^j over the
+ *     open qubits in ascending order; bits of a closed bitstring at open
+ *     positions are ignored;
+ *   - a wire is labelled (q, t) = "qubit q after its t-th gate", t = 0 being the
+ *     input wire;
+ *   - slice id s fixes the j-th sliced wire of a plan to bit j of s;
+ *   - amplitudes crossing the ABI are interleaved complex128 (re, im doubles).
+ *
+ * Every call returns a tn_status; 0 is success.  On failure
+ * tn_last_error() returns a message for the calling thread's last failure.  No
+ * C++ exception crosses this boundary.  Errors found by device kernels after an
+ * asynchronous launch (a bounded wait that ran out, a violated bound) are
+ * sticky on the plan: they are returned by the plan's next call and by
+ * tn_plan_sync().
+ *
+ * Streams are passed as `void*` holding a cudaStream_t (NULL = legacy default
+ * stream) so that this header needs no CUDA include.
+ */
+#ifndef TN_GB300_H
+#define TN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tn_status;
+#define TN_OK               0
+#define TN_ERR_ARG         -1  /* invalid argument, size or range */
+#define TN_ERR_OOM         -2  /* device or host allocation failed */
+#define TN_ERR_CUDA        -3  /* a CUDA runtime call failed */
+#define TN_ERR_PLAN        -4  /* no plan satisfies the options (e.g. the bound) */
+#define TN_ERR_TIMEOUT     -5  /* a bounded device wait expired; the kernel returned early */
+#define TN_ERR_UNSUPPORTED -6  /* valid request this build does not implement */
+#define TN_ERR_DEVICE      -7  /* a device-side check failed (bounds, layout) */
+
+/* Message for the calling thread's last failing call ("" if none).  The
+ * pointer stays valid until the thread's next failing call. */
+const char* tn_last_error(void);
+
+/* ---------------------------------------------------------------- circuit */
+
+/* A gate list in time order, initial state |0...0> (SI, "Random quantum
+ * circuits").  gate_qubits[2g], gate_qubits[2g+1] are the qubits of gate g, the
+ * second one -1 for a single-qubit gate.  gate_matrices holds the matrices of
+ * all gates back to back as interleaved complex128, row-major, row = output:
+ * 4 complex entries for a single-qubit gate, 16 for a two-qubit gate, whose
+ * row/column index is 2*b(q0) + b(q1) with q0 = gate_qubits[2g].
+ * gate_layer is informational and may be NULL.  All arrays are host memory
+ * owned by the caller and are copied; they may be freed after the call. */
+typedef struct tn_circuit {
+    int32_t        n_qubits;
+    int32_t        n_gates;
+    const int32_t* gate_qubits;     /* [n_gates][2] */
+    const double*  gate_matrices;   /* interleaved complex128, see above */
+    const int32_t* gate_layer;      /* [n_gates] or NULL */
+} tn_circuit;
+
+typedef struct tn_network_s tn_network_t;
+typedef struct tn_plan_s    tn_plan_t;
+
+/* Circuit -> tensor network (SI, TN section, figure S2): one tensor per gate,
+ * legs labelled by wires (q, t).  Host only.  Fails with TN_ERR_ARG on a qubit
+ * index out of range, a gate acting twice on one qubit, n_qubits outside
+ * [1, 64] or a NULL pointer.  The network is owned by the caller and freed
+ * with tn_network_destroy(). */
+tn_status tn_network_from_circuit(const tn_circuit* circuit, tn_network_t** out);
+
+/* Number of wires carrying label (q, t) for t = 0..count-1: writes, for every
+ * qubit q, the number of gates on q into gates_per_qubit[q] (so that the
+ * output wire of q is (q, gates_per_qubit[q])).  Host only. */
+tn_status tn_network_wire_counts(const tn_network_t* net, int32_t* gates_per_qubit, int32_t cap);
+
+void tn_network_destroy(tn_network_t* net);
+
+/* ---------------------------------------------------------------- plan */
+
+#define TN_PREC_FP32    0  /* complex64 SIMT FMA (the plain FP32 path) */
+#define TN_PREC_TF32    1  /* tcgen05 kind::tf32, FP32 accumulate */
+#define TN_PREC_BF16X3  2  /* tcgen05 kind::f16, bf16 hi+lo split operands, FP32 accumulate */
+#define TN_PREC_FP16X3  3  /* tcgen05 kind::f16, fp16 hi+lo split operands, FP32 accumulate */
+
+typedef struct tn_plan_opts {
+    uint64_t open_mask;              /* qubits left open: 2^popcount amplitudes per batch */
+    int32_t  max_log2_intermediate;  /* bound on every per-slice intermediate (elements) */
+    int32_t  min_log2_slices;        /* slice at least this many wires (0: only what the bound needs) */
+    uint64_t seed;                   /* seeds the randomised order search */
+    int32_t  trials;                 /* order-search trials (<= 0: default) */
+    int32_t  precision;              /* TN_PREC_* */
+    int32_t  complex_mult;           /* 4 (4M) or 3 (3M) real products per complex product */
+    int32_t  log2_batch_slices;      /* slices contracted together per chunk (<= 0: auto) */
+    int64_t  max_arena_bytes;        /* device arena cap for one chunk (<= 0: 96 GiB) */
+    int32_t  fuse_permute;           /* 1: permutes folded into operand gathers; 0: explicit permute pass */
+    int32_t  reserved;
+} tn_plan_opts;
+
+/* Fill opts with defaults: no open qubits, bound 2^30, no forced slices, seed 1,
+ * 64 trials, FP32, 4M, automatic batch, 96 GiB arena, fused permutes. */
+tn_status tn_plan_default_opts(tn_plan_opts* opts);
+
+/* Find a contraction order and a slice set (SI, TN section: pairwise order as
+ * a list of two-tuples; main text, section II: slicing under a bound on the
+ * largest intermediate).  Host only; no CUDA call is made.  The network is
+ * simplified first (SI, TN section: rank-1 and rank-2 tensors are absorbed into
+ * neighbours; two tensors are pre-contracted when the result's rank is not
+ * larger than the larger input's).  The plan keeps its own copy of the
+ * network's data and is freed with tn_plan_destroy().  TN_ERR_PLAN if the open
+ * qubits alone exceed the bound. */
+tn_status tn_plan(const tn_network_t* net, const tn_plan_opts* opts, tn_plan_t** out);
+
+typedef struct tn_plan_stats {
+    int32_t  n_qubits;
+    int32_t  n_open;                 /* k: 2^k amplitudes per batch */
+    int32_t  n_leaves;               /* tensors after simplification */
+    int32_t  n_steps;                /* pairwise contractions per slice */
+    int32_t  log2_slices;            /* S */
+    int32_t  log2_batch_slices;      /* slices per chunk = 2^this */
+    int32_t  log2_max_intermediate;  /* largest per-slice intermediate */
+    int32_t  precision;
+    double   flops_per_slice;        /* 8 real flops per complex multiply-add */
+    double   bytes_per_slice;        /* 8 B per complex64 element: operands read once, result written once */
+    double   flops_per_chunk;        /* with slice-invariant parts shared inside a chunk */
+    double   bytes_per_chunk;
+    int64_t  arena_bytes;            /* device arena of one chunk */
+    int32_t  k_histogram[40];        /* steps per log2(contracted size k), as figure S4 */
+    int32_t  complex_mult;
+    int32_t  n_kernel_launches_per_chunk;
+} tn_plan_stats;
+
+tn_status tn_plan_info(const tn_plan_t* plan, tn_plan_stats* out);
+
+/* The sliced wires in slice-bit order: qubit[j], t[j] label slice bit j.
+ * `count` receives S; at most `cap` entries are written. */
+tn_status tn_plan_sliced_wires(const tn_plan_t* plan, int32_t* qubit, int32_t* t,
+                               int32_t cap, int32_t* count);
+
+/* Per-step shapes (for sweeps and reports): log2 of m (rows of the streamed
+ * operand), k (contracted size), n (columns of the small operand) and of the
+ * number of batch instances per chunk, for step i < n_steps. */
+tn_status tn_plan_step_shape(const tn_plan_t* plan, int32_t step, int32_t* log2_m,
+                             int32_t* log2_k, int32_t* log2_n, int32_t* log2_batch);
+
+/* Contract slices [slice_first, slice_first + slice_count) for n_batches
+ * correlated batches and ADD the result into out_amplitudes (main text, section
+ * II: the sliced network is the sum of the slices; section III: one run gives
+ * the 2^k amplitudes of a batch).
+ *   open_bitstrings  host array [n_batches]: the closed bits of each batch
+ *                    (bits at open positions ignored); copied before return.
+ *   out_amplitudes   DEVICE array of n_batches * 2^k interleaved complex128,
+ *                    accumulated (+=) in FP64; owned by the caller.
+ *   stream           cudaStream_t; the call is asynchronous on it.
+ * The first call on a plan allocates the plan's device arena (freed by
+ * tn_plan_destroy) and uploads the leaf tensors; that call synchronises.  A
+ * range beyond 2^S, n_batches < 1 or a NULL pointer gives TN_ERR_ARG.  Not
+ * thread-safe per plan. */
+tn_status tn_contract_slices(tn_plan_t* plan, uint64_t slice_first, uint64_t slice_count,
+                             const uint64_t* open_bitstrings, int32_t n_batches,
+                             double* out_amplitudes, void* stream);
+
+/* Wait for the plan's work on `stream` and return its sticky device error, if any. */
+tn_status tn_plan_sync(tn_plan_t* plan, void* stream);
+
+void tn_plan_destroy(tn_plan_t* plan);
+
+/* ---------------------------------------------------------------- XEB */
+
+/* Linear XEB (main text, Eq. (1): the mean of x = N p is 1 + F):
+ * F = 2^n_qubits * mean_i |a_i|^2 - 1 over `count` DEVICE complex128 amplitudes,
+ * summed in FP64 on the device.  Writes F to the HOST double *xeb_out.
+ * Synchronises `stream`.  count < 1 gives TN_ERR_ARG. */
+tn_status tn_xeb(const double* amplitudes, int64_t count, int32_t n_qubits, double* xeb_out,
+                 void* stream);
+
+/* ---------------------------------------------------------------- kernels */
+
+/* Index permutation of `batch` complex64 tensors of rank `rank` (every index of
+ * dimension 2, index 0 fastest): out index position p carries the input index
+ * at position perm[p] (SI, Eq. (2): the permutation that makes contracted
+ * indices one matrix dimension).  in/out are DEVICE interleaved complex64
+ * arrays of batch * 2^rank elements, not overlapping.  rank in [0, 34]. */
+tn_status tn_permute(const float* in, float* out, int32_t rank, const int32_t* perm,
+                     int64_t batch, void* stream);
+
+/* One pairwise contraction C = sum_shared A * B of two DEVICE complex64
+ * tensors (SI, Eq. (2)), through the same kernels as a plan step.  Wires are
+ * arbitrary int32 ids, listed in storage order (position 0 fastest); a wire in
+ * both A and B is contracted; c_wires must be the remaining wires in any order.
+ * `batch` independent instances are stored back to back in each array.
+ * precision and complex_mult as in tn_plan_opts.  Asynchronous on stream. */
+tn_status tn_contract_pair(const float* a, const int32_t* a_wires, int32_t a_rank,
+                           const float* b, const int32_t* b_wires, int32_t b_rank,
+                           float* c, const int32_t* c_wires, int32_t c_rank,
+                           int64_t batch, int32_t precision, int32_t complex_mult,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_GB300_H */

@@ -1,0 +1,224 @@
+"""Tensor-network contraction of a circuit amplitude batch, complex128 on the CPU.
+
+What it computes (SI, TN section and figure S2; main text, section II):
+
+* every gate is a tensor whose legs are wires: a single-qubit gate U has legs
+  (out, in) with entries U[out, in]; a two-qubit gate has legs
+  (out0, out1, in0, in1) with entries U[2 out0 + out1, 2 in0 + in1];
+* wires carry the canonical label (q, t) = "qubit q after its t-th gate", so
+  (q, 0) is the input wire and (q, T_q) the output wire of qubit q;
+* the initial state |0> is a rank-1 tensor [1, 0] on every input wire; a closed
+  output qubit with bit b gets the rank-1 tensor e_b on its output wire; the
+  output wires of open qubits stay free, so contracting the network yields the
+  2^k amplitudes of a correlated batch (main text, section III);
+* slicing (main text, section II): fixing a set of wires to values turns the
+  network into one of 2^S smaller networks; the sum over all assignments equals
+  the unsliced contraction.  Slice id s sets the j-th sliced wire to bit j of s.
+
+How: the oracle's own greedy pairwise order (at each step merge the pair of
+connected tensors whose merge removes the most memory, size(C) - size(A) -
+size(B) smallest, ties to the lowest tensor ids), executed with numpy.tensordot.
+When that order would create a tensor larger than 2^max_log2 entries the
+oracle slices extra wires of its own choosing and sums the sub-networks, which
+changes nothing but memory.  No blocking, fusion or reordering beyond that.
+
+Test infrastructure only (see the package docstring).
+"""
+from __future__ import annotations
+
+import heapq
+import itertools
+from typing import Dict, Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+Label = Tuple[int, int]
+
+
+class CircuitNetwork:
+    """The tensor network of one circuit and one batch (closed bits + open mask)."""
+
+    def __init__(self, circuit, closed_bits: int, open_mask: int):
+        n = circuit.n_qubits
+        self.n_qubits = n
+        t = [0] * n
+        legs: List[Tuple[Label, ...]] = []
+        data: List[np.ndarray] = []
+        for q in range(n):                       # |0> on every input wire
+            legs.append(((q, 0),))
+            data.append(np.array([1.0, 0.0], dtype=np.complex128))
+        for g in range(circuit.n_gates):
+            q0, q1 = int(circuit.gate_qubits[g, 0]), int(circuit.gate_qubits[g, 1])
+            u = np.asarray(circuit.gate_matrices[g], dtype=np.complex128)
+            if q1 < 0:
+                legs.append(((q0, t[q0] + 1), (q0, t[q0])))
+                data.append(u.copy())
+                t[q0] += 1
+            else:
+                legs.append(((q0, t[q0] + 1), (q1, t[q1] + 1), (q0, t[q0]), (q1, t[q1])))
+                data.append(u.reshape(2, 2, 2, 2).copy())
+                t[q0] += 1
+                t[q1] += 1
+        self.open_legs: List[Label] = []
+        for q in range(n):
+            out = (q, t[q])
+            if (open_mask >> q) & 1:
+                self.open_legs.append(out)
+            else:
+                b = (closed_bits >> q) & 1
+                legs.append((out,))
+                data.append(np.array([1.0 - b, float(b)], dtype=np.complex128))
+        self.legs = legs
+        self.data = data
+        self.wire_count = t
+
+    # -- planning ---------------------------------------------------------------
+    @staticmethod
+    def greedy_order(leg_sets: Sequence[frozenset]) -> Tuple[List[Tuple[int, int]], List[frozenset]]:
+        """Greedy pairwise order over leg sets.  Returns the merge list (ids into
+        a growing list: the i-th merge creates id len(leg_sets) + i) and the leg
+        set of every id."""
+        sets: List[frozenset] = list(leg_sets)
+        alive = set(range(len(sets)))
+        owner: Dict[Label, set] = {}
+        for i, s in enumerate(sets):
+            for leg in s:
+                owner.setdefault(leg, set()).add(i)
+        heap: List[Tuple[int, int, int]] = []
+
+        def push(i: int, j: int) -> None:
+            a, b = (i, j) if i < j else (j, i)
+            c = sets[a] ^ sets[b]
+            score = (1 << len(c)) - (1 << len(sets[a])) - (1 << len(sets[b]))
+            heapq.heappush(heap, (score, a, b))
+
+        for leg, ids in owner.items():
+            if len(ids) == 2:
+                i, j = sorted(ids)
+                push(i, j)
+        merges: List[Tuple[int, int]] = []
+        while heap:
+            _, a, b = heapq.heappop(heap)
+            if a not in alive or b not in alive:
+                continue
+            c = sets[a] ^ sets[b]
+            cid = len(sets)
+            sets.append(c)
+            alive.discard(a)
+            alive.discard(b)
+            alive.add(cid)
+            merges.append((a, b))
+            nbrs = set()
+            for leg in sets[a] | sets[b]:
+                ids = owner.get(leg)
+                if ids is None:
+                    continue
+                ids.discard(a)
+                ids.discard(b)
+                if leg in c:
+                    ids.add(cid)
+                    nbrs.update(x for x in ids if x != cid)
+            for x in sorted(nbrs):
+                push(x, cid)
+        # disconnected components: outer products, smallest first
+        rest = sorted(alive, key=lambda i: (len(sets[i]), i))
+        while len(rest) > 1:
+            a, b = rest[0], rest[1]
+            cid = len(sets)
+            sets.append(sets[a] ^ sets[b])
+            merges.append((a, b))
+            rest = sorted(rest[2:] + [cid], key=lambda i: (len(sets[i]), i))
+        return merges, sets
+
+    def plan(self, fixed_legs: Iterable[Label], max_log2: int = 27
+             ) -> Tuple[List[Tuple[int, int]], List[Label]]:
+        """Greedy order for the network with `fixed_legs` removed, plus the extra
+        wires the oracle itself slices so that no tensor exceeds 2^max_log2."""
+        fixed = set(fixed_legs)
+        extra: List[Label] = []
+        while True:
+            gone = fixed | set(extra)
+            base = [frozenset(l for l in legs if l not in gone) for legs in self.legs]
+            merges, sets = self.greedy_order(base)
+            big = [s for s in sets if len(s) > max_log2]
+            if not big:
+                return merges, extra
+            counts: Dict[Label, int] = {}
+            for s in big:
+                for leg in s:
+                    if leg not in self.open_legs:
+                        counts[leg] = counts.get(leg, 0) + 1
+            if not counts:
+                raise ValueError("open legs alone exceed the oracle's size limit")
+            best = max(sorted(counts), key=lambda l: counts[l])
+            extra.append(best)
+
+    @staticmethod
+    def flops_of(merges: Sequence[Tuple[int, int]], sets: Sequence[frozenset]) -> int:
+        """Complex multiply-adds of an order: 2^|legs(A) u legs(B)| per merge."""
+        return sum(1 << len(sets[a] | sets[b]) for a, b in merges)
+
+    # -- execution ---------------------------------------------------------------
+    def _fixed_arrays(self, values: Dict[Label, int]):
+        arrays, legs = [], []
+        for lg, arr in zip(self.legs, self.data):
+            keep = []
+            idx = []
+            for leg in lg:
+                if leg in values:
+                    idx.append(values[leg])
+                else:
+                    idx.append(slice(None))
+                    keep.append(leg)
+            arrays.append(arr[tuple(idx)])
+            legs.append(tuple(keep))
+        return arrays, legs
+
+    def _run(self, merges, values: Dict[Label, int]) -> np.ndarray:
+        arrays, legs = self._fixed_arrays(values)
+        arrays = list(arrays)
+        legs = list(legs)
+        for a, b in merges:
+            la, lb = legs[a], legs[b]
+            shared = [l for l in la if l in lb]
+            ax_a = [la.index(l) for l in shared]
+            ax_b = [lb.index(l) for l in shared]
+            out = np.tensordot(arrays[a], arrays[b], axes=(ax_a, ax_b))
+            arrays.append(out)
+            legs.append(tuple(l for l in la if l not in shared) + tuple(l for l in lb if l not in shared))
+            arrays[a] = arrays[b] = None
+        final, final_legs = arrays[-1], legs[-1]
+        # amplitude index = sum_j b(open_j) 2^j: C order wants open_{k-1} first
+        want = tuple(reversed(self.open_legs))
+        if len(merges) == 0:
+            final, final_legs = arrays[0], legs[0]
+        perm = [final_legs.index(l) for l in want]
+        return np.transpose(final, perm).reshape(-1)
+
+    def contract(self, sliced: Sequence[Label] = (), slice_ids: Optional[Iterable[int]] = None,
+                 max_log2: int = 27) -> np.ndarray:
+        """Sum over the given slice ids (all 2^S when None) of the network with the
+        sliced wires fixed: slice id s sets sliced[j] to bit j of s.  Returns the
+        2^k complex128 batch amplitudes (partial sums when not all slices)."""
+        sliced = list(sliced)
+        for leg in sliced:
+            if leg in self.open_legs:
+                raise ValueError("an open output wire cannot be sliced")
+        merges, extra = self.plan(sliced, max_log2)
+        if slice_ids is None:
+            slice_ids = range(1 << len(sliced))
+        total = np.zeros(1 << len(self.open_legs), dtype=np.complex128)
+        for s in slice_ids:
+            s = int(s)
+            base = {leg: (s >> j) & 1 for j, leg in enumerate(sliced)}
+            for sub in range(1 << len(extra)):
+                values = dict(base)
+                values.update({leg: (sub >> j) & 1 for j, leg in enumerate(extra)})
+                total += self._run(merges, values)
+        return total
+
+
+def batch_amplitudes(circuit, closed_bits: int, open_mask: int, sliced: Sequence[Label] = (),
+                     slice_ids: Optional[Iterable[int]] = None, max_log2: int = 27) -> np.ndarray:
+    """Convenience wrapper: amplitudes (or a slice subset's partial sum) of one batch."""
+    return CircuitNetwork(circuit, closed_bits, open_mask).contract(sliced, slice_ids, max_log2)

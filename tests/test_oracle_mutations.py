@@ -1,0 +1,73 @@
+"""Planted mistakes in the oracle (on the CPU): each must make a pin fail.
+
+This shows the pins in test_oracle_pins.py are sensitive to the mistakes they
+are meant to catch, rather than passing for any implementation.
+"""
+import numpy as np
+import pytest
+
+import rqcgen
+from oracle import statevector as sv
+from oracle import tensornet as tn
+
+from test_oracle_pins import _feynman_amplitude, _random_circuit
+
+
+def _mutated_network(monkeypatch, mutate):
+    orig_init = tn.CircuitNetwork.__init__
+
+    def init(self, circuit, closed_bits, open_mask):
+        orig_init(self, circuit, closed_bits, open_mask)
+        mutate(self)
+
+    monkeypatch.setattr(tn.CircuitNetwork, "__init__", init)
+
+
+def _tn_vs_pathsum(circ, open_mask, closed):
+    got = tn.batch_amplitudes(circ, closed, open_mask)
+    idx = sv.batch_indices(circ.n_qubits, closed, open_mask)
+    want = np.array([_feynman_amplitude(circ, int(x)) for x in idx])
+    return float(np.max(np.abs(got - want)))
+
+
+def test_planted_transposed_single_qubit_gates_are_caught(monkeypatch):
+    circ = _random_circuit(3, 6, 3)
+
+    def mutate(net):
+        net.data = [d.T.copy() if d.ndim == 2 else d for d in net.data]
+
+    assert _tn_vs_pathsum(circ, 0b111, 0) < 1e-12
+    _mutated_network(monkeypatch, mutate)
+    assert _tn_vs_pathsum(circ, 0b111, 0) > 1e-3
+
+
+def test_planted_swapped_two_qubit_order_is_caught(monkeypatch):
+    circ = _random_circuit(3, 6, 4)
+
+    def mutate(net):
+        net.data = [d.transpose(1, 0, 3, 2).copy() if d.ndim == 4 else d for d in net.data]
+
+    _mutated_network(monkeypatch, mutate)
+    assert _tn_vs_pathsum(circ, 0b111, 0) > 1e-3
+
+
+def test_planted_reversed_amplitude_bit_order_is_caught(monkeypatch):
+    circ, om, cb = rqcgen.config_circuit("c1")
+    psi = sv.simulate(circ)
+    want = sv.batch_amplitudes(psi, circ.n_qubits, cb, om)
+
+    def mutate(net):
+        net.open_legs = list(reversed(net.open_legs))
+
+    _mutated_network(monkeypatch, mutate)
+    got = tn.batch_amplitudes(circ, cb, om)
+    assert np.linalg.norm(got - want) > 1e-3 * np.linalg.norm(want)
+
+
+def test_planted_dropped_slice_is_caught():
+    circ, om, cb = rqcgen.config_circuit("c1")
+    net = tn.CircuitNetwork(circ, cb, om)
+    full = net.contract()
+    sliced = [(0, 3), (5, 4), (9, 2)]
+    partial = net.contract(sliced, range(1, 8))        # slice 0 left out
+    assert np.linalg.norm(partial - full) > 1e-6 * np.linalg.norm(full)

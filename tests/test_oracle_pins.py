@@ -1,0 +1,334 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test targets a plausible mistake: a transposed gate, a swapped qubit order
+in a two-qubit matrix, a wrong bit order in the amplitude index, a dropped
+slice, a wrong XEB formula.  None of them compares the oracle with itself.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import rqcgen
+from oracle import statevector as sv
+from oracle import tensornet as tn
+from oracle import xeb
+
+S2 = 1.0 / math.sqrt(2.0)
+
+
+# ----------------------------------------------------------------- gate set (SI)
+
+def test_gate_closed_forms():
+    """SI gate definitions: actions on basis states, and squares that are Pauli
+    matrices up to the phase -i (sqrt(X)^2 = -iX etc.)."""
+    x = np.array([[0, 1], [1, 0]], dtype=complex)
+    y = np.array([[0, -1j], [1j, 0]])
+    w = (x + y) / math.sqrt(2.0)
+    for f, p in ((rqcgen.sqrt_x, x), (rqcgen.sqrt_y, y), (rqcgen.sqrt_w, w)):
+        u = f()
+        np.testing.assert_allclose(u @ u.conj().T, np.eye(2), atol=1e-15)
+        np.testing.assert_allclose(u @ u, -1j * p, atol=1e-15)
+    np.testing.assert_allclose(rqcgen.sqrt_x() @ [1, 0], [S2, -1j * S2], atol=1e-16)
+    # sqrt(Y) is not symmetric: its first column is (1, 1)/sqrt2, second (-1, 1)/sqrt2
+    np.testing.assert_allclose(rqcgen.sqrt_y() @ [1, 0], [S2, S2], atol=1e-16)
+    np.testing.assert_allclose(rqcgen.sqrt_y() @ [0, 1], [-S2, S2], atol=1e-16)
+
+
+def test_fsim_closed_form():
+    """fSim(pi/2, phi): |00> fixed, |01> -> -i|10>, |10> -> -i|01>, |11> -> e^{-i phi}|11>."""
+    phi = math.pi / 6
+    u = rqcgen.fsim(math.pi / 2, phi)
+    e = np.eye(4)
+    np.testing.assert_allclose(u @ e[0], e[0], atol=1e-15)
+    np.testing.assert_allclose(u @ e[1], -1j * e[2], atol=1e-15)
+    np.testing.assert_allclose(u @ e[2], -1j * e[1], atol=1e-15)
+    np.testing.assert_allclose(u @ e[3], np.exp(-1j * phi) * e[3], atol=1e-15)
+    # the five-parameter form with the (2,2) entry read as exp(i(D+ - D-)) cos(theta) is unitary
+    v = rqcgen.fsim(0.7, 0.3, 0.2, 0.5, 0.9)
+    np.testing.assert_allclose(v @ v.conj().T, np.eye(4), atol=1e-14)
+
+
+# ----------------------------------------------------------------- generator (SI)
+
+def test_pattern_invariants():
+    """Every nearest-neighbour pair gets exactly one gate per block of A, B, C, D."""
+    for rows, cols in ((3, 4), (5, 6), (6, 7), (6, 9)):
+        allpairs = set()
+        for r in range(rows):
+            for c in range(cols):
+                if c + 1 < cols:
+                    allpairs.add(((r, c), (r, c + 1)))
+                if r + 1 < rows:
+                    allpairs.add(((r, c), (r + 1, c)))
+        seen = []
+        for letter in "ABCD":
+            pairs = rqcgen.pattern_pairs(rows, cols, letter)
+            qs = [q for p in pairs for q in p]
+            assert len(qs) == len(set(qs)), "a pattern must be a matching"
+            seen.extend(pairs)
+        assert sorted(seen) == sorted(allpairs)
+    assert rqcgen.cycle_patterns(8) == "ABCDCDAB"
+    assert rqcgen.cycle_patterns(12) == "ABCDCDABABCD"
+
+
+def test_generator_counts_and_determinism():
+    c1, _, _ = rqcgen.config_circuit("c1")
+    assert c1.n_qubits == 12 and c1.n_two_qubit() == 34
+    assert c1.n_gates - c1.n_two_qubit() == 9 * 12
+    c1b, _, _ = rqcgen.config_circuit("c1")
+    assert c1.to_json() == c1b.to_json()
+    c5, om5, _ = rqcgen.config_circuit("c5")
+    assert c5.n_qubits == 53 and bin(om5).count("1") == 6
+    # single-qubit gates never repeat on a qubit in consecutive layers
+    for circ in (c1, c5):
+        last = {}
+        for g in range(circ.n_gates):
+            q0, q1 = circ.gate_qubits[g]
+            if q1 < 0:
+                name = circ.gate_names[g]
+                assert last.get(int(q0)) != name
+                last[int(q0)] = name
+
+
+def test_circuit_json_roundtrip():
+    c, _, _ = rqcgen.config_circuit("c1")
+    d = rqcgen.Circuit.from_json(c.to_json())
+    assert d.n_gates == c.n_gates
+    for g in range(c.n_gates):
+        np.testing.assert_array_equal(d.gate_matrices[g], c.gate_matrices[g])
+
+
+# ----------------------------------------------------------------- state vector
+
+def _random_unitary(rng, dim):
+    z = rng.normal(size=(dim, dim)) + 1j * rng.normal(size=(dim, dim))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def _random_circuit(n, n_gates, seed):
+    """Random gates (Haar-ish 2x2 and 4x4, not symmetric) on random qubits."""
+    rng = np.random.default_rng(seed)
+    qs, mats = [], []
+    for _ in range(n_gates):
+        if n > 1 and rng.random() < 0.5:
+            a, b = rng.choice(n, size=2, replace=False)
+            qs.append((int(a), int(b)))
+            mats.append(_random_unitary(rng, 4))
+        else:
+            qs.append((int(rng.integers(n)), -1))
+            mats.append(_random_unitary(rng, 2))
+    return rqcgen.Circuit(n, np.array(qs, dtype=np.int32), mats,
+                          np.arange(len(qs), dtype=np.int32))
+
+
+def _dense_gate(n, qubits, u):
+    """Full 2^n x 2^n matrix of a gate, from the definition: entry (x', x) is
+    u[row(x'), col(x)] when all other bits agree, with row/col = 2 b(q0) + b(q1)."""
+    dim = 1 << n
+    m = np.zeros((dim, dim), dtype=complex)
+    for x in range(dim):
+        for xp in range(dim):
+            others_equal = all(((x >> q) & 1) == ((xp >> q) & 1)
+                               for q in range(n) if q not in qubits)
+            if not others_equal:
+                continue
+            if len(qubits) == 1:
+                r, c = (xp >> qubits[0]) & 1, (x >> qubits[0]) & 1
+            else:
+                q0, q1 = qubits
+                r = 2 * ((xp >> q0) & 1) + ((xp >> q1) & 1)
+                c = 2 * ((x >> q0) & 1) + ((x >> q1) & 1)
+            m[xp, x] = u[r, c]
+    return m
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_statevector_against_dense_definition(seed):
+    n = 4
+    circ = _random_circuit(n, 10, seed)
+    psi = np.zeros(1 << n, dtype=complex)
+    psi[0] = 1.0
+    for g in range(circ.n_gates):
+        q0, q1 = map(int, circ.gate_qubits[g])
+        qs = (q0,) if q1 < 0 else (q0, q1)
+        psi = _dense_gate(n, qs, circ.gate_matrices[g]) @ psi
+    np.testing.assert_allclose(sv.simulate(circ), psi, atol=1e-13)
+
+
+def test_statevector_closed_forms_and_norm():
+    n = 5
+    # sqrt(Y) on every qubit of |0..0>: every amplitude is +2^{-n/2}
+    c = rqcgen.Circuit(n, np.array([(q, -1) for q in range(n)], dtype=np.int32),
+                       [rqcgen.sqrt_y()] * n, np.zeros(n, dtype=np.int32))
+    np.testing.assert_allclose(sv.simulate(c), np.full(1 << n, 2 ** (-n / 2)), atol=1e-15)
+    # sqrt(X) on every qubit: amplitude of x is (-i)^{popcount(x)} 2^{-n/2}
+    c = rqcgen.Circuit(n, np.array([(q, -1) for q in range(n)], dtype=np.int32),
+                       [rqcgen.sqrt_x()] * n, np.zeros(n, dtype=np.int32))
+    want = np.array([(-1j) ** bin(x).count("1") for x in range(1 << n)]) * 2 ** (-n / 2)
+    np.testing.assert_allclose(sv.simulate(c), want, atol=1e-15)
+    # sqrt(X) on q0, then fSim(pi/2) on (q0, q1): (|00> - |01>... in bit order) / sqrt2
+    c = rqcgen.Circuit(2, np.array([(0, -1), (0, 1)], dtype=np.int32),
+                       [rqcgen.sqrt_x(), rqcgen.fsim(math.pi / 2, math.pi / 6)],
+                       np.zeros(2, dtype=np.int32))
+    psi = sv.simulate(c)
+    # sqrt(X)|0> on q0 = (|x=0> - i|x=1>)/sqrt2 (x = b0 + 2 b1); fSim maps b0=1,b1=0 (row 2) to -i * (b0=0,b1=1)
+    np.testing.assert_allclose(psi, [S2, 0, -S2, 0], atol=1e-15)
+    circ, _, _ = rqcgen.config_circuit("c1")
+    assert abs(np.linalg.norm(sv.simulate(circ)) - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------- tensor network
+
+def _feynman_amplitude(circ, x):
+    """<x|U|0> as an explicit sum over every value of every internal wire (the
+    definition of contracting the network), pure Python loops, tiny circuits."""
+    n = circ.n_qubits
+    t = [0] * n
+    gates = []
+    for g in range(circ.n_gates):
+        q0, q1 = map(int, circ.gate_qubits[g])
+        if q1 < 0:
+            gates.append(((q0,), [(q0, t[q0] + 1)], [(q0, t[q0])], circ.gate_matrices[g]))
+            t[q0] += 1
+        else:
+            gates.append(((q0, q1), [(q0, t[q0] + 1), (q1, t[q1] + 1)],
+                          [(q0, t[q0]), (q1, t[q1])], circ.gate_matrices[g]))
+            t[q0] += 1
+            t[q1] += 1
+    internal = [(q, k) for q in range(n) for k in range(1, t[q])]
+    total = 0j
+    for vals in itertools.product((0, 1), repeat=len(internal)):
+        val = dict(zip(internal, vals))
+        for q in range(n):
+            val[(q, 0)] = 0
+            val[(q, t[q])] = (x >> q) & 1
+        term = 1 + 0j
+        for _, outs, ins, u in gates:
+            if len(outs) == 1:
+                term *= u[val[outs[0]], val[ins[0]]]
+            else:
+                term *= u[2 * val[outs[0]] + val[outs[1]], 2 * val[ins[0]] + val[ins[1]]]
+            if term == 0:
+                break
+        total += term
+    return total
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_tensornet_against_path_sum(seed):
+    circ = _random_circuit(3, 6, seed)
+    for open_mask in (0b000, 0b101, 0b111):
+        closed = 0b010
+        got = tn.batch_amplitudes(circ, closed, open_mask)
+        idx = sv.batch_indices(3, closed, open_mask)
+        want = np.array([_feynman_amplitude(circ, int(x)) for x in idx])
+        np.testing.assert_allclose(got, want, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_tensornet_against_statevector(seed):
+    n = 9
+    circ = _random_circuit(n, 40, seed)
+    psi = sv.simulate(circ)
+    rng = np.random.default_rng(seed)
+    open_mask = int(rng.integers(1 << n))
+    closed = int(rng.integers(1 << n))
+    got = tn.batch_amplitudes(circ, closed, open_mask)
+    want = sv.batch_amplitudes(psi, n, closed, open_mask)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_tensornet_c1_against_statevector():
+    circ, om, cb = rqcgen.config_circuit("c1")
+    psi = sv.simulate(circ)
+    got = tn.batch_amplitudes(circ, cb, om)
+    want = sv.batch_amplitudes(psi, circ.n_qubits, cb, om)
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_slicing_identity_and_additivity():
+    """Main text, section II: the sliced network is the sum of the smaller networks."""
+    circ, om, cb = rqcgen.config_circuit("c1")
+    net = tn.CircuitNetwork(circ, cb, om & 0xF0F)
+    full = net.contract()
+    rng = np.random.default_rng(0)
+    internal = [(q, t) for q in range(circ.n_qubits) for t in range(1, net.wire_count[q])]
+    for s_count in (1, 3, 6):
+        pick = [internal[i] for i in rng.choice(len(internal), size=s_count, replace=False)]
+        tot = net.contract(pick)
+        assert np.linalg.norm(tot - full) <= 1e-12 * np.linalg.norm(full)
+        ids = np.arange(1 << s_count)
+        part_a = net.contract(pick, ids[: len(ids) // 3])
+        part_b = net.contract(pick, ids[len(ids) // 3:])
+        assert np.linalg.norm(part_a + part_b - full) <= 1e-12 * np.linalg.norm(full)
+        one = net.contract(pick, [1])
+        assert np.linalg.norm(one - full) > 1e-6 * np.linalg.norm(full)  # a slice is not the sum
+
+
+def test_oracle_subslicing_changes_nothing():
+    circ, om, cb = rqcgen.config_circuit("c1")
+    net = tn.CircuitNetwork(circ, cb, om)
+    a = net.contract(max_log2=27)
+    b = net.contract(max_log2=12)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+
+
+def test_batches_cover_unit_norm():
+    """Sum over all batches of |a|^2 is 1 (the state is normalised)."""
+    circ, _, _ = rqcgen.config_circuit("c1")
+    open_mask = 0b000011110000
+    total = 0.0
+    for closed_hi in range(1 << 8):
+        closed = (closed_hi & 0xF) | ((closed_hi >> 4) << 8)
+        a = tn.batch_amplitudes(circ, closed, open_mask)
+        total += float(np.sum(np.abs(a) ** 2))
+    assert abs(total - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------- XEB, Eq. (1)
+
+def test_fxeb_density_is_normalised_with_mean_one_plus_f():
+    x = np.linspace(0, 60, 600001)
+    for f in (0.0, 0.3, 1.0):
+        p = xeb.fxeb_density(x, f)
+        assert abs(np.trapezoid(p, x) - 1.0) < 1e-8
+        assert abs(np.trapezoid(x * p, x) - (1.0 + f)) < 1e-8
+        assert abs(np.trapezoid(x * x * p, x) - xeb.fxeb_moment(2, f)) < 1e-7
+
+
+def test_linear_xeb_special_cases():
+    n = 10
+    uniform = np.full(1 << n, 2 ** (-n / 2), dtype=complex)
+    assert abs(xeb.linear_xeb(uniform, n)) < 1e-13
+    # a point mass: F = 2^n - 1
+    delta = np.zeros(1 << n, dtype=complex)
+    delta[3] = 1.0
+    assert abs(xeb.linear_xeb(delta[3:4], n) - (2 ** n - 1)) < 1e-9
+
+
+def test_porter_thomas_and_ideal_xeb():
+    """A deep random circuit's output is Porter-Thomas: x = N p over all
+    bitstrings follows Eq. (1) with F = 0, so E[x] = 1, E[x^2] = 2, E[x^3] = 6.
+    Ideal sampling then gives XEB = N sum p^2 - 1 = E[x^2] - 1 ~ 1, and
+    bitstrings drawn from p give a sampled linear XEB near that value."""
+    circ = rqcgen.sycamore_style(4, 4, 20, seed=11)
+    n = circ.n_qubits
+    psi = sv.simulate(circ)
+    x = (1 << n) * np.abs(psi) ** 2
+    assert abs(x.mean() - 1.0) < 1e-12
+    sd2 = math.sqrt((xeb.fxeb_moment(4, 0.0) - 4.0) / x.size)   # sd of the mean of x^2
+    assert abs((x * x).mean() - xeb.fxeb_moment(2, 0.0)) < 4 * sd2
+    assert abs((x ** 3).mean() - xeb.fxeb_moment(3, 0.0)) < 0.25
+    ideal = float((1 << n) * np.sum(np.abs(psi) ** 4) - 1.0)
+    assert abs(ideal - 1.0) < 4 * sd2
+    m = 20000
+    picks = xeb.sample_bitstrings(np.abs(psi) ** 2, m, seed=0)
+    f = xeb.linear_xeb(psi[picks], n)
+    assert abs(f - ideal) < 4 * math.sqrt(6.0 / m)
+    # uniformly chosen bitstrings (F = 0 sampler) give XEB ~ 0
+    rng = np.random.default_rng(1)
+    f0 = xeb.linear_xeb(psi[rng.integers(0, 1 << n, size=m)], n)
+    assert abs(f0) < 4 * math.sqrt(1.0 / m)
