@@ -18,7 +18,8 @@ What it computes (SI, TN section and figure S2; main text, section II):
 How: the oracle's own greedy pairwise order (at each step merge the pair of
 connected tensors whose merge removes the most memory, size(C) - size(A) -
 size(B) smallest, ties to the lowest tensor ids), executed with numpy.tensordot.
-When that order would create a tensor larger than 2^max_log2 entries the
+Larger networks use the recursive bisection order of oracle.order instead.
+When the order would create a tensor larger than 2^max_log2 entries the
 oracle slices extra wires of its own choosing and sums the sub-networks, which
 changes nothing but memory.  No blocking, fusion or reordering beyond that.
 
@@ -130,28 +131,36 @@ class CircuitNetwork:
             rest = sorted(rest[2:] + [cid], key=lambda i: (len(sets[i]), i))
         return merges, sets
 
-    def plan(self, fixed_legs: Iterable[Label], max_log2: int = 27
-             ) -> Tuple[List[Tuple[int, int]], List[Label]]:
-        """Greedy order for the network with `fixed_legs` removed, plus the extra
-        wires the oracle itself slices so that no tensor exceeds 2^max_log2."""
+    def plan(self, fixed_legs: Iterable[Label], max_log2: int = 27, method: str = "greedy",
+             trials: int = 8) -> Tuple[List[Tuple[int, int]], List[Label]]:
+        """Pairwise order for the network with `fixed_legs` removed ("greedy", or
+        "bisect" for the recursive bisection of oracle.order), plus the extra
+        wires the oracle itself slices so that no tensor of that order exceeds
+        2^max_log2 entries (the order is kept; only legs are removed)."""
         fixed = set(fixed_legs)
-        extra: List[Label] = []
-        while True:
-            gone = fixed | set(extra)
-            base = [frozenset(l for l in legs if l not in gone) for legs in self.legs]
+        base = [frozenset(l for l in legs if l not in fixed) for legs in self.legs]
+        if method == "greedy":
             merges, sets = self.greedy_order(base)
-            big = [s for s in sets if len(s) > max_log2]
+        elif method == "bisect":
+            from . import order as _order
+            merges, sets = _order.best_bisection_order(base, trials=trials)
+        else:
+            raise ValueError(f"unknown order method {method!r}")
+        extra: List[Label] = []
+        open_set = set(self.open_legs)
+        while True:
+            gone = frozenset(extra)
+            big = [s - gone for s in sets if len(s - gone) > max_log2]
             if not big:
                 return merges, extra
             counts: Dict[Label, int] = {}
             for s in big:
                 for leg in s:
-                    if leg not in self.open_legs:
+                    if leg not in open_set:
                         counts[leg] = counts.get(leg, 0) + 1
             if not counts:
                 raise ValueError("open legs alone exceed the oracle's size limit")
-            best = max(sorted(counts), key=lambda l: counts[l])
-            extra.append(best)
+            extra.append(max(sorted(counts), key=lambda l: counts[l]))
 
     @staticmethod
     def flops_of(merges: Sequence[Tuple[int, int]], sets: Sequence[frozenset]) -> int:
@@ -196,7 +205,7 @@ class CircuitNetwork:
         return np.transpose(final, perm).reshape(-1)
 
     def contract(self, sliced: Sequence[Label] = (), slice_ids: Optional[Iterable[int]] = None,
-                 max_log2: int = 27) -> np.ndarray:
+                 max_log2: int = 27, method: str = "greedy", trials: int = 8) -> np.ndarray:
         """Sum over the given slice ids (all 2^S when None) of the network with the
         sliced wires fixed: slice id s sets sliced[j] to bit j of s.  Returns the
         2^k complex128 batch amplitudes (partial sums when not all slices)."""
@@ -204,7 +213,7 @@ class CircuitNetwork:
         for leg in sliced:
             if leg in self.open_legs:
                 raise ValueError("an open output wire cannot be sliced")
-        merges, extra = self.plan(sliced, max_log2)
+        merges, extra = self.plan(sliced, max_log2, method, trials)
         if slice_ids is None:
             slice_ids = range(1 << len(sliced))
         total = np.zeros(1 << len(self.open_legs), dtype=np.complex128)
@@ -219,6 +228,8 @@ class CircuitNetwork:
 
 
 def batch_amplitudes(circuit, closed_bits: int, open_mask: int, sliced: Sequence[Label] = (),
-                     slice_ids: Optional[Iterable[int]] = None, max_log2: int = 27) -> np.ndarray:
+                     slice_ids: Optional[Iterable[int]] = None, max_log2: int = 27,
+                     method: str = "greedy", trials: int = 8) -> np.ndarray:
     """Convenience wrapper: amplitudes (or a slice subset's partial sum) of one batch."""
-    return CircuitNetwork(circuit, closed_bits, open_mask).contract(sliced, slice_ids, max_log2)
+    return CircuitNetwork(circuit, closed_bits, open_mask).contract(sliced, slice_ids, max_log2,
+                                                                    method, trials)

@@ -1,0 +1,115 @@
+// Small kernels of the slice loop: leaf select (slicing, main text section II),
+// FP64 slice sum into the amplitudes, chunk advance, XEB reduction (Eq. (1))
+// and the standalone index permutation (SI Eq. (2)).
+#pragma once
+#include "kernels_common.cuh"
+#include "tn_internal.h"
+
+namespace tnx {
+
+__device__ __forceinline__ uint32_t pdep_u32(uint32_t x, uint32_t mask) {
+  uint32_t r = 0;
+  int k = 0;
+  while (mask) {
+    const uint32_t low = mask & (0u - mask);
+    if ((x >> k) & 1) r |= low;
+    ++k;
+    mask ^= low;
+  }
+  return r;
+}
+
+// Materialise every leaf of the chunk: the sliced wires take the bits of the
+// slice id, the closed output wires the bits of the batch's bitstring.
+__global__ void k_leaf_select(const float2* __restrict__ leaf_data, const LeafDesc* __restrict__ leaves,
+                              int n_leaves, float2* __restrict__ arena, const ChunkParam* __restrict__ params,
+                              const unsigned* __restrict__ counter) {
+  const ChunkParam p = params[*counter];
+  for (int li = blockIdx.x; li < n_leaves; li += gridDim.x) {
+    const LeafDesc& d = leaves[li];
+    const int rank = d.rank;
+    const int64_t per = (int64_t)1 << rank;
+    const int64_t total = per << __popc(d.bmask);
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+      const uint32_t inst = (uint32_t)(e >> rank);
+      const int64_t i = e & (per - 1);
+      const uint64_t sid = p.slice_base | (uint64_t)pdep_u32(inst, d.bmask);
+      int64_t fix = 0;
+      for (int f = 0; f < d.nfixed; ++f) {
+        const int idx = d.fixed_index[f];
+        const uint64_t v = d.fixed_kind[f] == 0 ? ((sid >> idx) & 1) : ((p.bitstring >> idx) & 1);
+        fix |= (int64_t)v << f;
+      }
+      arena[d.dst_off + e] = leaf_data[d.src_off + fix * per + i];
+    }
+  }
+}
+
+// out[batch][j] += sum over the chunk's valid slices of the root tensor, FP64.
+__global__ void k_root_accumulate(const float2* __restrict__ arena, const RootDesc r, int b,
+                                  double* __restrict__ out, const ChunkParam* __restrict__ params,
+                                  const unsigned* __restrict__ counter) {
+  const ChunkParam p = params[*counter];
+  const int k = r.rank;
+  const int64_t nout = (int64_t)1 << k;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nout;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int64_t ri = 0;
+    for (int q = 0; q < k; ++q)
+      if ((j >> q) & 1) ri |= (int64_t)1 << r.pos_of_open[q];
+    double sr = 0.0, si = 0.0;
+    const uint32_t nlow = 1u << b;
+    for (uint32_t s = 0; s < nlow; ++s) {
+      const uint64_t sid = p.slice_base + s;
+      if (sid < p.valid_lo || sid >= p.valid_hi) continue;
+      const uint32_t inst = pext_u32(s, r.bmask);
+      const float2 v = arena[r.off + ((int64_t)inst << k) + ri];
+      sr += (double)v.x;
+      si += (double)v.y;
+    }
+    double* o = out + 2 * (p.out_index * nout + j);
+    o[0] += sr;
+    o[1] += si;
+  }
+}
+
+__global__ void k_advance(unsigned* counter) { *counter += 1u; }
+
+// sum_i |a_i|^2 in FP64 (one block; count is small)
+__global__ void k_xeb_sum(const double2* __restrict__ a, int64_t n, double* __restrict__ out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 v = a[i];
+    s = fma(v.x, v.x, s);
+    s = fma(v.y, v.y, s);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+struct PermArgs {
+  int8_t src_pos[KMAXR];  // output bit p <- input bit src_pos[p]
+};
+
+// Standalone permutation: one thread per output element (coalesced writes,
+// gathered reads), used by tn_permute and the unfused path.
+__global__ void k_permute_gather(const float2* __restrict__ in, float2* __restrict__ out, int rank,
+                                 const PermArgs pa, int64_t total) {
+  const int64_t mask = ((int64_t)1 << rank) - 1;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = idx & mask;
+    int64_t src = 0;
+    for (int p = 0; p < rank; ++p)
+      if ((o >> p) & 1) src |= (int64_t)1 << pa.src_pos[p];
+    out[idx] = __ldg(in + (idx - o) + src);
+  }
+}
+
+}  // namespace tnx

@@ -1,0 +1,140 @@
+// Complex GEMM on the CUDA cores (complex64, FP32 FMA): the plain FP32 path.
+// Operands are gathered straight from their tensors' storage order, so the
+// index permutation of SI Eq. (2) is folded into the loads (the paper's fused
+// permutation-multiplication, SI figure S7a): each tile covers the lowest
+// memory positions of its operand, so the gathers read contiguous runs.
+#pragma once
+#include "kernels_common.cuh"
+
+namespace tnx {
+
+template <int TM, int TN, int TK, int RM, int RN>
+__global__ void __launch_bounds__((TM / RM) * (TN / RN))
+k_cgemm_simt(const GemmArgs g) {
+  constexpr int NTX = TM / RM, NTY = TN / RN, NT = NTX * NTY;
+  constexpr int AE = (TM * TK + NT - 1) / NT;
+  constexpr int BE = (TK * TN + NT - 1) / NT;
+  __shared__ float2 As[TK][TM];
+  __shared__ float2 Bs[TK][TN];
+  __shared__ int64_t offCm[TM];
+  __shared__ int64_t offCn[TN];
+  const int tid = threadIdx.x;
+  const int tx = tid % NTX, ty = tid / NTX;
+  const int TMv = 1 << g.tm, TKv = 1 << g.tk, TNv = 1 << g.tn;
+
+  for (int i = tid; i < TK * TM; i += NT) (&As[0][0])[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < TK * TN; i += NT) (&Bs[0][0])[i] = make_float2(0.f, 0.f);
+  for (int r = tid; r < TM; r += NT) offCm[r] = r < TMv ? deposit_hi((uint64_t)r, g.c_mpos, 0, g.tm) : 0;
+  for (int c = tid; c < TN; c += NT) offCn[c] = c < TNv ? deposit_hi((uint64_t)c, g.c_npos, 0, g.tn) : 0;
+
+  // Each thread's share of a tile, decoded once: element e of the tile has its
+  // bits assigned to tile bits in ascending memory position, so consecutive e
+  // (consecutive threads) read consecutive addresses.
+  int a_sm[AE];
+  int64_t a_off[AE];
+  const int a_elems = 1 << g.a_tbits;
+#pragma unroll
+  for (int j = 0; j < AE; ++j) {
+    const int e = tid + j * NT;
+    a_sm[j] = -1;
+    a_off[j] = 0;
+    if (e < a_elems) {
+      int r = 0, c = 0;
+      int64_t off = 0;
+      for (int t = 0; t < g.a_tbits; ++t)
+        if ((e >> t) & 1) {
+          const int s = g.a_tsel[t];
+          if (s & 64) c |= 1 << (s & 63); else r |= 1 << (s & 63);
+          off += (int64_t)1 << g.a_tpos[t];
+        }
+      a_sm[j] = c * TM + r;
+      a_off[j] = off;
+    }
+  }
+  int b_sm[BE];
+  int64_t b_off[BE];
+  const int b_elems = 1 << g.b_tbits;
+#pragma unroll
+  for (int j = 0; j < BE; ++j) {
+    const int e = tid + j * NT;
+    b_sm[j] = -1;
+    b_off[j] = 0;
+    if (e < b_elems) {
+      int k = 0, n = 0;
+      int64_t off = 0;
+      for (int t = 0; t < g.b_tbits; ++t)
+        if ((e >> t) & 1) {
+          const int s = g.b_tsel[t];
+          if (s & 64) k |= 1 << (s & 63); else n |= 1 << (s & 63);
+          off += (int64_t)1 << g.b_tpos[t];
+        }
+      b_sm[j] = k * TN + n;
+      b_off[j] = off;
+    }
+  }
+  __syncthreads();
+
+  const int nkc = 1 << (g.nk - g.tk);
+  for (int inst = blockIdx.z; inst < g.n_inst; inst += gridDim.z) {
+    const float2* A = g.A + (int64_t)pext_u32((uint32_t)inst, g.a_bsel) * g.a_size +
+                      deposit_hi(blockIdx.x, g.a_mpos, g.tm, g.nm);
+    const float2* B = g.B + (int64_t)pext_u32((uint32_t)inst, g.b_bsel) * g.b_size +
+                      deposit_hi(blockIdx.y, g.b_npos, g.tn, g.nn);
+    float2* C = g.C + (int64_t)inst * g.c_size + deposit_hi(blockIdx.x, g.c_mpos, g.tm, g.nm) +
+                deposit_hi(blockIdx.y, g.c_npos, g.tn, g.nn);
+    float2 acc[RM][RN];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    float2 ra[AE], rb[BE];
+    auto load = [&](int kc) {
+      const int64_t ka = deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
+      const int64_t kb = deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk);
+#pragma unroll
+      for (int j = 0; j < AE; ++j)
+        if (a_sm[j] >= 0) ra[j] = __ldg(A + ka + a_off[j]);
+#pragma unroll
+      for (int j = 0; j < BE; ++j)
+        if (b_sm[j] >= 0) rb[j] = __ldg(B + kb + b_off[j]);
+    };
+    load(0);
+    for (int kc = 0; kc < nkc; ++kc) {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < AE; ++j)
+        if (a_sm[j] >= 0) (&As[0][0])[a_sm[j]] = ra[j];
+#pragma unroll
+      for (int j = 0; j < BE; ++j)
+        if (b_sm[j] >= 0) (&Bs[0][0])[b_sm[j]] = rb[j];
+      __syncthreads();
+      if (kc + 1 < nkc) load(kc + 1);
+#pragma unroll 4
+      for (int kk = 0; kk < TKv; ++kk) {
+        float2 a[RM], b[RN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = As[kk][tx + i * NTX];
+#pragma unroll
+        for (int j = 0; j < RN; ++j) b[j] = Bs[kk][ty + j * NTY];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int j = 0; j < RN; ++j) {
+            acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+            acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+          }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < RN; ++j) {
+        const int r = tx + i * NTX, c = ty + j * NTY;
+        if (r < TMv && c < TNv) C[offCm[r] + offCn[c]] = acc[i][j];
+      }
+  }
+}
+
+}  // namespace tnx

@@ -1,0 +1,407 @@
+// Device executor: the slice loop of a plan on one GPU, the XEB reduction, and
+// the standalone kernel entry points of the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "k_misc.cuh"
+#include "k_simt.cuh"
+#include "kernels_common.cuh"
+#include "tn_internal.h"
+
+namespace tnx {
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) fail(TN_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------ kernel table
+enum KernelId {
+  K_SIMT_64x64 = 0,   // TM 64, TN 64, TK 8
+  K_SIMT_128x16 = 1,  // TM 128, TN 16, TK 16
+  K_SIMT_256x4 = 2,   // TM 256, TN 4, TK 16
+  K_TC = 3,           // tcgen05 (tile 128 x TN, see k_tc.cuh)
+  K_COUNT
+};
+struct KernelCfg {
+  int tm, tn, tk;  // log2 tile extents
+};
+static const KernelCfg kCfg[K_COUNT] = {{6, 6, 3}, {7, 4, 4}, {8, 2, 4}, {7, 5, 5}};
+
+static int pick_simt(const StepDesc& d) {
+  if (d.nn >= 5 && d.nm >= 5) return K_SIMT_64x64;
+  if (d.nn >= 3) return K_SIMT_128x16;
+  return K_SIMT_256x4;
+}
+
+// Tile decode tables: the tile's bits in ascending memory position.
+static GemmArgs make_args(const StepDesc& d, int kid, const float2* A, const float2* B, float2* C,
+                          int32_t n_inst) {
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.a_size = d.a_size;
+  g.b_size = d.b_size;
+  g.c_size = d.c_size;
+  g.a_bsel = d.a_bsel;
+  g.b_bsel = d.b_bsel;
+  g.n_inst = n_inst;
+  g.nm = d.nm;
+  g.nk = d.nk;
+  g.nn = d.nn;
+  const KernelCfg& k = kCfg[kid];
+  g.tm = std::min(k.tm, d.nm);
+  g.tk = std::min(k.tk, d.nk);
+  g.tn = std::min(k.tn, d.nn);
+  std::memcpy(g.a_mpos, d.a_mpos, KMAXR);
+  std::memcpy(g.a_kpos, d.a_kpos, KMAXR);
+  std::memcpy(g.b_kpos, d.b_kpos, KMAXR);
+  std::memcpy(g.b_npos, d.b_npos, KMAXR);
+  std::memcpy(g.c_mpos, d.c_mpos, KMAXR);
+  std::memcpy(g.c_npos, d.c_npos, KMAXR);
+  std::vector<std::pair<int, int>> ta, tb;  // (position, sel)
+  for (int i = 0; i < g.tm; ++i) ta.push_back({d.a_mpos[i], i});
+  for (int j = 0; j < g.tk; ++j) ta.push_back({d.a_kpos[j], j | 64});
+  for (int j = 0; j < g.tk; ++j) tb.push_back({d.b_kpos[j], j | 64});
+  for (int i = 0; i < g.tn; ++i) tb.push_back({d.b_npos[i], i});
+  std::sort(ta.begin(), ta.end());
+  std::sort(tb.begin(), tb.end());
+  if ((int)ta.size() > KTB || (int)tb.size() > KTB) fail(TN_ERR_UNSUPPORTED, "tile too large");
+  g.a_tbits = (int)ta.size();
+  g.b_tbits = (int)tb.size();
+  for (size_t t = 0; t < ta.size(); ++t) {
+    g.a_tpos[t] = (int8_t)ta[t].first;
+    g.a_tsel[t] = (int8_t)ta[t].second;
+  }
+  for (size_t t = 0; t < tb.size(); ++t) {
+    g.b_tpos[t] = (int8_t)tb[t].first;
+    g.b_tsel[t] = (int8_t)tb[t].second;
+  }
+  return g;
+}
+
+static void launch_gemm(const GemmArgs& g, int kid, cudaStream_t s) {
+  if (g.n_inst <= 0) return;
+  const int64_t gx = (int64_t)1 << (g.nm - g.tm);
+  const int64_t gy = (int64_t)1 << (g.nn - g.tn);
+  if (gx > 0x7fffffff || gy > 65535) fail(TN_ERR_UNSUPPORTED, "GEMM grid too large");
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)std::min<int32_t>(g.n_inst, 65535));
+  switch (kid) {
+    case K_SIMT_64x64:
+      k_cgemm_simt<64, 64, 8, 4, 4><<<grid, 256, 0, s>>>(g);
+      break;
+    case K_SIMT_128x16:
+      k_cgemm_simt<128, 16, 16, 4, 2><<<grid, 256, 0, s>>>(g);
+      break;
+    case K_SIMT_256x4:
+      k_cgemm_simt<256, 4, 16, 4, 1><<<grid, 256, 0, s>>>(g);
+      break;
+    default:
+      fail(TN_ERR_UNSUPPORTED, "kernel variant not built");
+  }
+}
+
+// ------------------------------------------------------------------ plan device state
+struct DeviceState {
+  int device = -1;
+  float2* arena = nullptr;
+  float2* leaf_data = nullptr;
+  LeafDesc* leaf_desc = nullptr;
+  ChunkParam* params = nullptr;
+  size_t params_cap = 0;
+  unsigned* counter = nullptr;
+  std::vector<GemmArgs> gemm;
+  std::vector<int> kid;
+  cudaEvent_t done = nullptr;
+  bool have_done = false;
+};
+
+static int pick_kernel(const Plan& p, const StepDesc& d) {
+  if (p.opts.precision == TN_PREC_FP32) return pick_simt(d);
+  return pick_simt(d);  // replaced by the tensor-core selection once available
+}
+
+static void ensure_device(Plan& p) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (p.dev) {
+    if (p.dev->device != dev) fail(TN_ERR_ARG, "plan was first used on another device");
+    return;
+  }
+  auto* ds = new DeviceState;
+  p.dev = ds;
+  ds->device = dev;
+  const size_t ab = std::max<size_t>(256, (size_t)p.arena_elems * sizeof(float2));
+  if (cudaMalloc(&ds->arena, ab) != cudaSuccess) {
+    cudaGetLastError();
+    fail(TN_ERR_OOM, "arena allocation of " + std::to_string(ab) + " bytes failed");
+  }
+  const size_t lb = std::max<size_t>(16, p.leaf_data.size() * sizeof(float2));
+  CK(cudaMalloc(&ds->leaf_data, lb));
+  CK(cudaMemcpy(ds->leaf_data, p.leaf_data.data(), p.leaf_data.size() * sizeof(float2),
+                cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ds->leaf_desc, std::max<size_t>(1, p.leaves.size()) * sizeof(LeafDesc)));
+  CK(cudaMemcpy(ds->leaf_desc, p.leaves.data(), p.leaves.size() * sizeof(LeafDesc),
+                cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ds->counter, sizeof(unsigned)));
+  CK(cudaEventCreateWithFlags(&ds->done, cudaEventDisableTiming));
+  // bounds of every operand inside the arena, checked once on the host
+  const int64_t ae = p.arena_elems;
+  auto in_arena = [&](int64_t off, int64_t size, int insts) {
+    return off >= 0 && off + size * (int64_t)insts <= ae;
+  };
+  for (const LeafDesc& l : p.leaves)
+    if (!in_arena(l.dst_off, (int64_t)1 << l.rank, 1 << __builtin_popcount(l.bmask)))
+      fail(TN_ERR_PLAN, "internal: leaf outside the arena");
+  for (const StepDesc& d : p.steps) {
+    if (!in_arena(d.a_off, d.a_size, 1 << __builtin_popcount(d.a_bsel)) ||
+        !in_arena(d.b_off, d.b_size, 1 << __builtin_popcount(d.b_bsel)) ||
+        !in_arena(d.c_off, d.c_size, 1 << d.nbc))
+      fail(TN_ERR_PLAN, "internal: step operand outside the arena");
+    const int kid = pick_kernel(p, d);
+    ds->kid.push_back(kid);
+    ds->gemm.push_back(make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off,
+                                 1 << d.nbc));
+  }
+  if (!in_arena(p.root.off, (int64_t)1 << p.root.rank, 1 << __builtin_popcount(p.root.bmask)))
+    fail(TN_ERR_PLAN, "internal: root outside the arena");
+}
+
+void destroy_device_state(Plan* p) {
+  if (!p || !p->dev) return;
+  DeviceState* ds = p->dev;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(ds->device);
+  if (ds->have_done) cudaEventSynchronize(ds->done);
+  cudaFree(ds->arena);
+  cudaFree(ds->leaf_data);
+  cudaFree(ds->leaf_desc);
+  cudaFree(ds->params);
+  cudaFree(ds->counter);
+  if (ds->done) cudaEventDestroy(ds->done);
+  cudaSetDevice(cur);
+  delete ds;
+  p->dev = nullptr;
+}
+
+static void run_chunk(Plan& p, double* out, cudaStream_t s) {
+  DeviceState& ds = *p.dev;
+  const int nl = (int)p.leaves.size();
+  k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
+                                                                 ds.params, ds.counter);
+  for (size_t i = 0; i < p.steps.size(); ++i) launch_gemm(ds.gemm[i], ds.kid[i], s);
+  const int64_t nout = (int64_t)1 << p.root.rank;
+  const int blocks = (int)std::min<int64_t>((nout + 255) / 256, 4096);
+  k_root_accumulate<<<blocks, 256, 0, s>>>(ds.arena, p.root, p.log2_batch, out, ds.params, ds.counter);
+  k_advance<<<1, 1, 0, s>>>(ds.counter);
+}
+
+}  // namespace tnx
+
+using namespace tnx;
+
+#define API_BEGIN \
+  try {           \
+    clear_error();
+#define API_END                        \
+  return TN_OK;                        \
+  }                                    \
+  catch (const TnError& e) {           \
+    set_error(e.msg);                  \
+    return e.code;                     \
+  }                                    \
+  catch (const std::bad_alloc&) {      \
+    set_error("host allocation failed"); \
+    return TN_ERR_OOM;                 \
+  }
+
+extern "C" tn_status tn_contract_slices(tn_plan_t* h, uint64_t first, uint64_t count,
+                                        const uint64_t* bitstrings, int32_t n_batches, double* out,
+                                        void* stream) {
+  API_BEGIN
+  if (!h || !bitstrings || !out) fail(TN_ERR_ARG, "tn_contract_slices: NULL argument");
+  Plan& p = h->plan;
+  if (p.sticky != TN_OK) fail(p.sticky, p.sticky_msg);
+  if (n_batches < 1) fail(TN_ERR_ARG, "n_batches must be >= 1");
+  const int S = (int)p.sliced.size();
+  const uint64_t total = S >= 64 ? ~0ULL : (1ULL << S);
+  if (first > total || count > total - first) fail(TN_ERR_ARG, "slice range beyond 2^S");
+  if (count == 0) return TN_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  ensure_device(p);
+  DeviceState& ds = *p.dev;
+  const int b = p.log2_batch;
+  const uint64_t step = 1ULL << b;
+  uint64_t open_mask = 0;
+  for (int q : p.open_qubits) open_mask |= 1ULL << q;
+  std::vector<ChunkParam> prm;
+  for (int i = 0; i < n_batches; ++i)
+    for (uint64_t base = (first >> b) << b; base < first + count; base += step) {
+      ChunkParam c;
+      c.slice_base = base;
+      c.valid_lo = std::max(first, base);
+      c.valid_hi = std::min(first + count, base + step);
+      c.bitstring = bitstrings[i] & ~open_mask;
+      c.out_index = i;
+      prm.push_back(c);
+    }
+  if (ds.have_done) CK(cudaStreamWaitEvent(s, ds.done, 0));
+  if (prm.size() > ds.params_cap) {
+    if (ds.params) {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaFree(ds.params));
+      ds.params = nullptr;
+    }
+    ds.params_cap = std::max<size_t>(prm.size(), 1024);
+    CK(cudaMalloc(&ds.params, ds.params_cap * sizeof(ChunkParam)));
+  }
+  CK(cudaMemcpyAsync(ds.params, prm.data(), prm.size() * sizeof(ChunkParam), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
+  for (size_t c = 0; c < prm.size(); ++c) {
+    run_chunk(p, out, s);
+    CK(cudaGetLastError());
+  }
+  CK(cudaEventRecord(ds.done, s));
+  ds.have_done = true;
+  API_END
+}
+
+extern "C" tn_status tn_plan_sync(tn_plan_t* h, void* stream) {
+  API_BEGIN
+  if (!h) fail(TN_ERR_ARG, "tn_plan_sync: NULL plan");
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (h->plan.sticky != TN_OK) fail(h->plan.sticky, h->plan.sticky_msg);
+  API_END
+}
+
+extern "C" void tn_plan_destroy(tn_plan_t* h) {
+  if (!h) return;
+  destroy_device_state(&h->plan);
+  delete h;
+}
+
+// per-device FP64 scratch of the XEB reduction
+static double* xeb_scratch(int dev) {
+  static std::mutex mu;
+  static std::unordered_map<int, double*> m;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = m.find(dev);
+  if (it != m.end()) return it->second;
+  double* p = nullptr;
+  CK(cudaMalloc(&p, sizeof(double)));
+  m[dev] = p;
+  return p;
+}
+
+extern "C" tn_status tn_xeb(const double* amps, int64_t count, int32_t n_qubits, double* xeb_out,
+                            void* stream) {
+  API_BEGIN
+  if (!amps || !xeb_out) fail(TN_ERR_ARG, "tn_xeb: NULL argument");
+  if (count < 1) fail(TN_ERR_ARG, "tn_xeb: count must be >= 1");
+  if (n_qubits < 0 || n_qubits > 1023) fail(TN_ERR_ARG, "tn_xeb: n_qubits out of range");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  double* scratch = xeb_scratch(dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  k_xeb_sum<<<1, 1024, 0, s>>>(reinterpret_cast<const double2*>(amps), count, scratch);
+  CK(cudaGetLastError());
+  double sum = 0;
+  CK(cudaMemcpyAsync(&sum, scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *xeb_out = std::ldexp(sum / (double)count, n_qubits) - 1.0;
+  API_END
+}
+
+extern "C" tn_status tn_permute(const float* in, float* out, int32_t rank, const int32_t* perm,
+                                int64_t batch, void* stream) {
+  API_BEGIN
+  if (!in || !out || (!perm && rank > 0)) fail(TN_ERR_ARG, "tn_permute: NULL argument");
+  if (rank < 0 || rank > 34) fail(TN_ERR_ARG, "tn_permute: rank must be in [0, 34]");
+  if (batch < 0) fail(TN_ERR_ARG, "tn_permute: negative batch");
+  PermArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  std::vector<char> seen(rank, 0);
+  for (int p = 0; p < rank; ++p) {
+    if (perm[p] < 0 || perm[p] >= rank || seen[perm[p]]) fail(TN_ERR_ARG, "tn_permute: not a permutation");
+    seen[perm[p]] = 1;
+    pa.src_pos[p] = (int8_t)perm[p];
+  }
+  const int64_t total = batch << rank;
+  if (total == 0) return TN_OK;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
+  k_permute_gather<<<blocks, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(in),
+                                                             reinterpret_cast<float2*>(out), rank, pa, total);
+  CK(cudaGetLastError());
+  API_END
+}
+
+extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t ar, const float* b,
+                                      const int32_t* bw, int32_t br, float* c, const int32_t* cw,
+                                      int32_t cr, int64_t batch, int32_t precision, int32_t cmult,
+                                      void* stream) {
+  API_BEGIN
+  if (!a || !b || !c || (ar && !aw) || (br && !bw) || (cr && !cw)) fail(TN_ERR_ARG, "tn_contract_pair: NULL argument");
+  if (ar < 0 || br < 0 || cr < 0 || ar > 34 || br > 34 || cr > 34) fail(TN_ERR_ARG, "tn_contract_pair: rank out of range");
+  if (batch < 1 || batch > 65535) fail(TN_ERR_ARG, "tn_contract_pair: batch must be in [1, 65535]");
+  if (precision < TN_PREC_FP32 || precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
+  if (cmult != 3 && cmult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
+  std::vector<int> A(aw, aw + ar), B(bw, bw + br), Cw(cw, cw + cr);
+  auto has = [](const std::vector<int>& v, int w) { return std::find(v.begin(), v.end(), w) != v.end(); };
+  for (size_t i = 0; i < A.size(); ++i)
+    for (size_t j = i + 1; j < A.size(); ++j)
+      if (A[i] == A[j]) fail(TN_ERR_ARG, "repeated wire in a_wires");
+  for (size_t i = 0; i < B.size(); ++i)
+    for (size_t j = i + 1; j < B.size(); ++j)
+      if (B[i] == B[j]) fail(TN_ERR_ARG, "repeated wire in b_wires");
+  StepDesc d;
+  std::memset(&d, 0, sizeof(d));
+  std::vector<int> mw, kw, nw;
+  for (int w : A) (has(B, w) ? kw : mw).push_back(w);
+  for (int w : B)
+    if (!has(A, w)) nw.push_back(w);
+  if (mw.size() + nw.size() != Cw.size()) fail(TN_ERR_ARG, "c_wires must be the uncontracted wires");
+  for (int w : mw)
+    if (!has(Cw, w)) fail(TN_ERR_ARG, "c_wires misses a wire of A");
+  for (int w : nw)
+    if (!has(Cw, w)) fail(TN_ERR_ARG, "c_wires misses a wire of B");
+  auto pos = [](const std::vector<int>& v, int w) { return (int)(std::find(v.begin(), v.end(), w) - v.begin()); };
+  d.nm = (int)mw.size();
+  d.nk = (int)kw.size();
+  d.nn = (int)nw.size();
+  for (int i = 0; i < d.nm; ++i) {
+    d.a_mpos[i] = (int8_t)pos(A, mw[i]);
+    d.c_mpos[i] = (int8_t)pos(Cw, mw[i]);
+  }
+  for (int j = 0; j < d.nk; ++j) {
+    d.a_kpos[j] = (int8_t)pos(A, kw[j]);
+    d.b_kpos[j] = (int8_t)pos(B, kw[j]);
+  }
+  for (int i = 0; i < d.nn; ++i) {
+    d.b_npos[i] = (int8_t)pos(B, nw[i]);
+    d.c_npos[i] = (int8_t)pos(Cw, nw[i]);
+  }
+  d.a_size = (int64_t)1 << ar;
+  d.b_size = (int64_t)1 << br;
+  d.c_size = (int64_t)1 << cr;
+  d.a_bsel = d.b_bsel = 0xffffffffu;
+  Plan tmp;
+  tmp.opts.precision = precision;
+  tmp.opts.complex_mult = cmult;
+  const int kid = pick_kernel(tmp, d);
+  GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
+                         reinterpret_cast<float2*>(c), (int32_t)batch);
+  launch_gemm(g, kid, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  API_END
+}

@@ -1,0 +1,1003 @@
+// Host planner: network simplification, contraction-order search, index
+// slicing, slice batching and the device step program (paper, SI TN section and
+// main text section II).  Host only: no CUDA call is made here.
+#include <algorithm>
+#include <bitset>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <limits>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <random>
+#include <unordered_map>
+
+#include "tn_internal.h"
+
+namespace tnx {
+namespace {
+
+constexpr int MAXW = 4096;
+using WS = std::bitset<MAXW>;
+constexpr double ALPHA = 32.0;   // complex MACs charged per complex64 element moved
+
+double pow2(int e) { return std::ldexp(1.0, e); }
+
+// ====================================================================== simplification
+// SI, TN section: rank-1 and rank-2 tensors are absorbed into neighbours, and
+// two tensors are pre-contracted when the result's rank is not larger than the
+// larger input's.  Ranks count planning wires only: the closed output wires
+// ("fixed") are set per batch by the leaf-select kernel and never enter a
+// per-slice tensor.
+struct Simplified {
+  std::vector<HTensor> leaves;   // wires: planning wires first, then fixed wires
+  std::vector<char> fixed;       // per network wire id
+};
+
+Simplified simplify(const Network& net, uint64_t open_mask) {
+  Simplified out;
+  const int n = net.n_qubits;
+  const int nw = (int)net.labels.size();
+  std::vector<HTensor> ts = net.gates;
+  // initial state |0> on every input wire
+  for (int q = 0; q < n; ++q) {
+    const int w = net.input_wire[q];
+    if (net.gates_per_qubit[q] == 0) {
+      HTensor t;   // a qubit with no gate: |0> sits directly on its output wire
+      t.wires = {w};
+      t.data = {cd(1, 0), cd(0, 0)};
+      ts.push_back(std::move(t));
+      continue;
+    }
+    for (auto& t : ts)
+      if (std::find(t.wires.begin(), t.wires.end(), w) != t.wires.end()) {
+        t = hfix(t, w, 0);
+        break;
+      }
+  }
+  out.fixed.assign(nw, 0);
+  for (int q = 0; q < n; ++q)
+    if (!((open_mask >> q) & 1)) out.fixed[net.output_wire[q]] = 1;
+  auto prank = [&](const HTensor& t) {
+    int r = 0;
+    for (int w : t.wires) r += !out.fixed[w];
+    return r;
+  };
+  std::vector<char> alive(ts.size(), 1);
+  auto owners = [&]() {
+    std::vector<std::vector<int>> own(nw);
+    for (size_t i = 0; i < ts.size(); ++i)
+      if (alive[i])
+        for (int w : ts[i].wires)
+          if (!out.fixed[w]) own[w].push_back((int)i);
+    return own;
+  };
+  auto n_alive = [&]() { return (int)std::count(alive.begin(), alive.end(), 1); };
+  bool changed = true;
+  while (changed && n_alive() > 1) {
+    changed = false;
+    auto own = owners();
+    // (a) absorb rank <= 2 tensors into their highest-rank neighbour
+    for (size_t i = 0; i < ts.size() && n_alive() > 1; ++i) {
+      if (!alive[i] || prank(ts[i]) > 2) continue;
+      int best = -1, best_rank = -1;
+      for (int w : ts[i].wires) {
+        if (out.fixed[w]) continue;
+        for (int j : own[w])
+          if (j != (int)i && alive[j] && prank(ts[j]) > best_rank) {
+            best = j;
+            best_rank = prank(ts[j]);
+          }
+      }
+      if (best < 0) {
+        // disconnected piece: fold it into the largest other tensor as an outer product
+        for (size_t j = 0; j < ts.size(); ++j)
+          if (j != i && alive[j] && prank(ts[j]) > best_rank) {
+            best = (int)j;
+            best_rank = prank(ts[j]);
+          }
+        if (best < 0) continue;
+      }
+      ts[best] = hcontract(ts[best], ts[i]);
+      alive[i] = 0;
+      changed = true;
+      own = owners();
+    }
+    // (b) pre-contract pairs whose result is not larger than the larger input
+    for (int w = 0; w < nw; ++w) {
+      if (own[w].size() != 2) continue;
+      const int a = own[w][0], b = own[w][1];
+      if (!alive[a] || !alive[b] || a == b) continue;
+      std::vector<int> uni;
+      int shared = 0;
+      for (int x : ts[a].wires)
+        if (!out.fixed[x]) uni.push_back(x);
+      for (int x : ts[b].wires) {
+        if (out.fixed[x]) continue;
+        if (std::find(uni.begin(), uni.end(), x) != uni.end())
+          ++shared;
+        else
+          uni.push_back(x);
+      }
+      const int rc = (int)uni.size() - shared;
+      if (rc <= std::max(prank(ts[a]), prank(ts[b]))) {
+        ts[a] = hcontract(ts[a], ts[b]);
+        alive[b] = 0;
+        changed = true;
+        own = owners();
+      }
+    }
+  }
+  for (size_t i = 0; i < ts.size(); ++i) {
+    if (!alive[i]) continue;
+    std::vector<int> order;
+    for (int w : ts[i].wires)
+      if (!out.fixed[w]) order.push_back(w);
+    for (int w : ts[i].wires)
+      if (out.fixed[w]) order.push_back(w);
+    out.leaves.push_back(hpermute(ts[i], order));
+  }
+  return out;
+}
+
+// ====================================================================== trees
+struct Tree {
+  int L = 0;
+  std::vector<std::pair<int, int>> merges;  // merge i creates node L + i
+  std::vector<WS> sets;                     // planning-wire set of each node
+};
+
+struct CostModel {
+  // cost of one pairwise step from log2 sizes: MACs + ALPHA * elements moved
+  static double step(int u, int a, int b, int c) {
+    return pow2(u) + ALPHA * (pow2(a) + pow2(b) + pow2(c));
+  }
+};
+
+double tree_cost(const Tree& t, const WS& sl) {
+  double c = 0;
+  WS keep = ~sl;
+  for (size_t i = 0; i < t.merges.size(); ++i) {
+    const WS& a = t.sets[t.merges[i].first];
+    const WS& b = t.sets[t.merges[i].second];
+    const WS& r = t.sets[t.L + i];
+    c += CostModel::step((int)((a | b) & keep).count(), (int)(a & keep).count(),
+                         (int)(b & keep).count(), (int)(r & keep).count());
+  }
+  return c;
+}
+
+// --------------------------------------------------------- exhaustive small subtrees
+// Optimal order of <= 8 nodes by dynamic programming over subsets (the SI's
+// brute-force optimisation of small subtrees).  Wires are mapped to a local
+// 128-bit mask.
+using u128 = unsigned __int128;
+static inline int pc128(u128 x) {
+  return __builtin_popcountll((uint64_t)x) + __builtin_popcountll((uint64_t)(x >> 64));
+}
+
+int dp_subtree(Tree& t, const std::vector<int>& nodes) {
+  const int k = (int)nodes.size();
+  if (k == 1) return nodes[0];
+  // local wire index
+  std::vector<int> wires;
+  for (int v : nodes)
+    for (size_t w = t.sets[v]._Find_first(); w < MAXW; w = t.sets[v]._Find_next(w))
+      if (std::find(wires.begin(), wires.end(), (int)w) == wires.end()) wires.push_back((int)w);
+  if (wires.size() > 128 || k > 10) {
+    // fall back to a left-deep chain
+    int cur = nodes[0];
+    for (int i = 1; i < k; ++i) {
+      t.merges.push_back({cur, nodes[i]});
+      t.sets.push_back(t.sets[cur] ^ t.sets[nodes[i]]);
+      cur = (int)t.sets.size() - 1;
+    }
+    return cur;
+  }
+  std::vector<u128> loc(k, 0);
+  for (int i = 0; i < k; ++i)
+    for (size_t j = 0; j < wires.size(); ++j)
+      if (t.sets[nodes[i]].test(wires[j])) loc[i] |= (u128)1 << j;
+  const int full = (1 << k) - 1;
+  std::vector<u128> legs(full + 1, 0);
+  for (int m = 1; m <= full; ++m) {
+    const int lo = __builtin_ctz(m);
+    legs[m] = legs[m & (m - 1)] ^ loc[lo];
+  }
+  std::vector<double> best(full + 1, std::numeric_limits<double>::infinity());
+  std::vector<int> split(full + 1, 0);
+  for (int i = 0; i < k; ++i) best[1 << i] = 0;
+  for (int m = 1; m <= full; ++m) {
+    if ((m & (m - 1)) == 0) continue;
+    const int lo = m & -m;
+    // enumerate submasks containing the lowest bit to avoid double counting
+    for (int s = (m - 1) & m; s > 0; s = (s - 1) & m) {
+      if (!(s & lo)) continue;
+      const int r = m ^ s;
+      const double c = best[s] + best[r] +
+                       CostModel::step(pc128(legs[s] | legs[r]), pc128(legs[s]), pc128(legs[r]),
+                                       pc128(legs[m]));
+      if (c < best[m]) {
+        best[m] = c;
+        split[m] = s;
+      }
+    }
+  }
+  std::function<int(int)> emit = [&](int m) -> int {
+    if ((m & (m - 1)) == 0) return nodes[__builtin_ctz(m)];
+    const int a = emit(split[m]);
+    const int b = emit(m ^ split[m]);
+    t.merges.push_back({a, b});
+    t.sets.push_back(t.sets[a] ^ t.sets[b]);
+    return (int)t.sets.size() - 1;
+  };
+  return emit(full);
+}
+
+// --------------------------------------------------------- recursive bisection
+// The SI partitions the network into subtrees with a hypergraph partitioner
+// before slicing and re-optimising small subtrees.  Here: balanced bisection by
+// region growing plus Fiduccia-Mattheyses refinement, minimising the number of
+// wires cut, recursively, with exhaustive search below a leaf-cluster size.
+struct Bisector {
+  const std::vector<std::vector<std::pair<int, int>>>& adj;  // leaf -> (nbr, multiplicity)
+  std::mt19937_64& rng;
+  double eps;
+  int leafmax;
+  int inits;
+
+  std::vector<char> partition(const std::vector<int>& nodes) {
+    const int n = (int)nodes.size();
+    std::unordered_map<int, int> loc;
+    for (int i = 0; i < n; ++i) loc[nodes[i]] = i;
+    std::vector<std::vector<std::pair<int, int>>> ladj(n);
+    for (int i = 0; i < n; ++i)
+      for (auto [v, m] : adj[nodes[i]]) {
+        auto it = loc.find(v);
+        if (it != loc.end()) ladj[i].push_back({it->second, m});
+      }
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    std::vector<char> best_side;
+    int best_cut = std::numeric_limits<int>::max();
+    const int lo = std::max(1, (int)std::floor(n * (0.5 - eps)));
+    const int hi = std::min(n - 1, (int)std::ceil(n * (0.5 + eps)));
+    for (int trial = 0; trial < inits; ++trial) {
+      std::vector<char> side(n, 1);
+      const int target = std::min(hi, lo + (int)(U(rng) * (hi - lo + 1)));
+      // region growing from a random seed
+      int count = 0;
+      std::vector<int> queue;
+      std::vector<char> seen(n, 0);
+      while (count < target) {
+        if (queue.empty()) {
+          std::vector<int> cand;
+          for (int i = 0; i < n; ++i)
+            if (!seen[i]) cand.push_back(i);
+          if (cand.empty()) break;
+          const int s = cand[(size_t)(U(rng) * cand.size()) % cand.size()];
+          seen[s] = 1;
+          queue.push_back(s);
+        }
+        const int v = queue.front();
+        queue.erase(queue.begin());
+        side[v] = 0;
+        ++count;
+        for (auto [u, m] : ladj[v])
+          if (!seen[u]) {
+            seen[u] = 1;
+            queue.push_back(u);
+          }
+      }
+      // FM passes
+      auto cut_of = [&]() {
+        int c = 0;
+        for (int i = 0; i < n; ++i)
+          for (auto [u, m] : ladj[i])
+            if (side[i] != side[u]) c += m;
+        return c / 2;
+      };
+      int cur = cut_of();
+      for (int pass = 0; pass < 8; ++pass) {
+        std::vector<int> gain(n, 0);
+        for (int i = 0; i < n; ++i)
+          for (auto [u, m] : ladj[i]) gain[i] += (side[i] != side[u]) ? m : -m;
+        std::vector<char> locked(n, 0);
+        int cnt0 = 0;
+        for (int i = 0; i < n; ++i) cnt0 += side[i] == 0;
+        std::vector<int> moved;
+        std::vector<int> cuts;
+        int c = cur;
+        for (int step = 0; step < n; ++step) {
+          int bv = -1;
+          double bg = -1e18;
+          for (int i = 0; i < n; ++i) {
+            if (locked[i]) continue;
+            const int c0 = cnt0 + (side[i] == 0 ? -1 : 1);
+            if (c0 < lo || c0 > hi) continue;
+            const double g = gain[i] + 1e-3 * U(rng);
+            if (g > bg) {
+              bg = g;
+              bv = i;
+            }
+          }
+          if (bv < 0) break;
+          c -= gain[bv];
+          cnt0 += side[bv] == 0 ? -1 : 1;
+          side[bv] ^= 1;
+          locked[bv] = 1;
+          gain[bv] = -gain[bv];
+          for (auto [u, m] : ladj[bv]) gain[u] += (side[u] != side[bv]) ? 2 * m : -2 * m;
+          moved.push_back(bv);
+          cuts.push_back(c);
+        }
+        int bi = -1, bc = cur;
+        for (size_t s = 0; s < cuts.size(); ++s)
+          if (cuts[s] < bc) {
+            bc = cuts[s];
+            bi = (int)s;
+          }
+        for (int s = (int)moved.size() - 1; s > bi; --s) side[moved[s]] ^= 1;
+        if (bi < 0) break;
+        cur = bc;
+      }
+      if (cur < best_cut) {
+        best_cut = cur;
+        best_side = side;
+      }
+    }
+    return best_side;
+  }
+
+  int build(Tree& t, const std::vector<int>& nodes) {
+    if ((int)nodes.size() <= leafmax) return dp_subtree(t, nodes);
+    auto side = partition(nodes);
+    std::vector<int> p0, p1;
+    for (size_t i = 0; i < nodes.size(); ++i) (side[i] ? p1 : p0).push_back(nodes[i]);
+    if (p0.empty() || p1.empty()) {
+      p0.assign(nodes.begin(), nodes.begin() + nodes.size() / 2);
+      p1.assign(nodes.begin() + nodes.size() / 2, nodes.end());
+    }
+    const int a = build(t, p0);
+    const int b = build(t, p1);
+    t.merges.push_back({a, b});
+    t.sets.push_back(t.sets[a] ^ t.sets[b]);
+    return (int)t.sets.size() - 1;
+  }
+};
+
+// --------------------------------------------------------- subtree reconfiguration
+// Re-optimise every subtree of up to 8 frontier nodes exhaustively (SI: small
+// subtrees are optimised by brute force) with the sliced wires removed.
+void reconfigure(Tree& t, const WS& sl, int passes) {
+  for (int pass = 0; pass < passes; ++pass) {
+    bool improved = false;
+    const int nm = (int)t.merges.size();
+    for (int root = t.L + nm - 1; root >= t.L; --root) {
+      // collect the frontier by expanding the costliest internal node
+      std::vector<int> frontier = {root};
+      std::vector<int> internal;
+      while ((int)frontier.size() < 8) {
+        int best = -1;
+        double bc = -1;
+        for (size_t i = 0; i < frontier.size(); ++i) {
+          const int v = frontier[i];
+          if (v < t.L) continue;
+          const auto [a, b] = t.merges[v - t.L];
+          const double c = pow2((int)((t.sets[a] | t.sets[b]) & ~sl).count());
+          if (c > bc) {
+            bc = c;
+            best = (int)i;
+          }
+        }
+        if (best < 0) break;
+        const int v = frontier[best];
+        frontier.erase(frontier.begin() + best);
+        internal.push_back(v);
+        frontier.push_back(t.merges[v - t.L].first);
+        frontier.push_back(t.merges[v - t.L].second);
+      }
+      if (frontier.size() < 3) continue;
+      double old_cost = 0;
+      for (int v : internal) {
+        const auto [a, b] = t.merges[v - t.L];
+        old_cost += CostModel::step((int)((t.sets[a] | t.sets[b]) & ~sl).count(),
+                                    (int)(t.sets[a] & ~sl).count(), (int)(t.sets[b] & ~sl).count(),
+                                    (int)(t.sets[v] & ~sl).count());
+      }
+      // exhaustive re-optimisation in a scratch tree that shares the node sets
+      Tree s;
+      s.L = 0;
+      s.sets = t.sets;
+      for (auto& w : s.sets) w &= ~sl;
+      const size_t base = s.sets.size();
+      dp_subtree(s, frontier);
+      double new_cost = 0;
+      for (size_t i = 0; i < s.merges.size(); ++i) {
+        const auto [a, b] = s.merges[i];
+        new_cost += CostModel::step((int)(s.sets[a] | s.sets[b]).count(), (int)s.sets[a].count(),
+                                    (int)s.sets[b].count(), (int)s.sets[base + i].count());
+      }
+      if (new_cost < old_cost * 0.999 && s.merges.size() == internal.size()) {
+        // rewrite: reuse the internal node ids, the subtree root keeps its id
+        std::vector<int> others;
+        for (int v : internal)
+          if (v != root) others.push_back(v);
+        std::sort(others.begin(), others.end());
+        std::unordered_map<int, int> remap;  // scratch id -> tree id
+        for (size_t i = 0; i < s.merges.size(); ++i) {
+          int a = s.merges[i].first, b = s.merges[i].second;
+          if (a >= (int)base) a = remap[a];
+          if (b >= (int)base) b = remap[b];
+          const int id = (i + 1 == s.merges.size()) ? root : others[i];
+          remap[(int)(base + i)] = id;
+          t.merges[id - t.L] = {a, b};
+          t.sets[id] = t.sets[a] ^ t.sets[b];
+        }
+        improved = true;
+      }
+    }
+    if (!improved) break;
+  }
+}
+
+// Topological order of merges (children before parents), deepest-first so that
+// the larger subtree runs before its sibling.
+std::vector<int> post_order(const Tree& t) {
+  std::vector<int> order;
+  const int root = t.L + (int)t.merges.size() - 1;
+  std::vector<std::pair<int, int>> stack = {{root, 0}};
+  while (!stack.empty()) {
+    auto& [v, state] = stack.back();
+    if (v < t.L) {
+      stack.pop_back();
+      continue;
+    }
+    if (state == 0) {
+      state = 1;
+      const auto [a, b] = t.merges[v - t.L];
+      stack.push_back({b, 0});
+      stack.push_back({a, 0});
+    } else {
+      order.push_back(v - t.L);
+      stack.pop_back();
+    }
+  }
+  return order;
+}
+
+// --------------------------------------------------------- slicing
+// Main text, section II: slice wires until every intermediate fits the bound;
+// each pick minimises the total cost 2^S * cost(per slice).
+std::vector<int> choose_slices(const Tree& t, const WS& open, int bound, int min_slices) {
+  std::vector<int> out;
+  WS sl;
+  const int nm = (int)t.merges.size();
+  while (true) {
+    int mx = 0;
+    for (const auto& s : t.sets) mx = std::max(mx, (int)(s & ~sl).count());
+    if (mx <= bound && (int)out.size() >= min_slices) break;
+    WS cand;
+    const int thresh = mx > bound ? mx : std::max(0, mx - 3);
+    for (const auto& s : t.sets)
+      if ((int)(s & ~sl).count() >= thresh) cand |= s;
+    cand &= ~sl;
+    cand &= ~open;
+    if (cand.none()) fail(TN_ERR_PLAN, "no wire left to slice (open qubits exceed the bound?)");
+    std::vector<int> ua(nm), ub(nm), uc(nm), uu(nm);
+    for (int i = 0; i < nm; ++i) {
+      const WS& a = t.sets[t.merges[i].first];
+      const WS& b = t.sets[t.merges[i].second];
+      ua[i] = (int)(a & ~sl).count();
+      ub[i] = (int)(b & ~sl).count();
+      uc[i] = (int)(t.sets[t.L + i] & ~sl).count();
+      uu[i] = (int)((a | b) & ~sl).count();
+    }
+    int best_w = -1;
+    double best_c = std::numeric_limits<double>::infinity();
+    int best_mx = 1 << 30;
+    for (size_t w = cand._Find_first(); w < MAXW; w = cand._Find_next(w)) {
+      double c = 0;
+      for (int i = 0; i < nm; ++i) {
+        const WS& a = t.sets[t.merges[i].first];
+        const WS& b = t.sets[t.merges[i].second];
+        const bool ia = a.test(w), ib = b.test(w);
+        c += CostModel::step(uu[i] - (ia || ib), ua[i] - ia, ub[i] - ib, uc[i] - t.sets[t.L + i].test(w));
+      }
+      // prefer picks that lower the maximum when over the bound
+      int nmx = 0;
+      if (mx > bound)
+        for (const auto& s : t.sets) nmx = std::max(nmx, (int)(s & ~sl).count() - (int)s.test(w));
+      if (nmx < best_mx || (nmx == best_mx && c < best_c)) {
+        best_mx = nmx;
+        best_c = c;
+        best_w = (int)w;
+      }
+    }
+    sl.set(best_w);
+    out.push_back(best_w);
+    if (out.size() > 60) fail(TN_ERR_PLAN, "slicing did not converge under 60 wires");
+  }
+  return out;
+}
+
+}  // namespace
+
+// ====================================================================== plan builder
+Plan* build_plan(const Network& net, const tn_plan_opts& o) {
+  if (o.max_log2_intermediate < 1 || o.max_log2_intermediate > 36)
+    fail(TN_ERR_ARG, "max_log2_intermediate must be in [1, 36]");
+  if (o.precision < TN_PREC_FP32 || o.precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
+  if (o.complex_mult != 3 && o.complex_mult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
+  if (o.min_log2_slices < 0 || o.min_log2_slices > 48) fail(TN_ERR_ARG, "min_log2_slices out of range");
+  const int n = net.n_qubits;
+  if (n < 64 && (o.open_mask >> n) != 0) fail(TN_ERR_ARG, "open_mask names a qubit >= n_qubits");
+  auto* P = new Plan;
+  std::unique_ptr<Plan> guard(P);
+  P->opts = o;
+  P->n_qubits = n;
+  for (int q = 0; q < n; ++q)
+    if ((o.open_mask >> q) & 1) P->open_qubits.push_back(q);
+  const int k_open = (int)P->open_qubits.size();
+  if (k_open > o.max_log2_intermediate) fail(TN_ERR_PLAN, "open qubits alone exceed the bound");
+  if (k_open > 30) fail(TN_ERR_UNSUPPORTED, "more than 30 open qubits");
+
+  Simplified S = simplify(net, o.open_mask);
+  const int L = (int)S.leaves.size();
+  P->n_leaves = L;
+
+  // planning wire numbering
+  std::vector<int> pw_of(net.labels.size(), -1);
+  std::vector<int> wire_of_pw;
+  for (const auto& lf : S.leaves)
+    for (int w : lf.wires)
+      if (!S.fixed[w] && pw_of[w] < 0) {
+        pw_of[w] = (int)wire_of_pw.size();
+        wire_of_pw.push_back(w);
+      }
+  const int W = (int)wire_of_pw.size();
+  if (W > MAXW) fail(TN_ERR_UNSUPPORTED, "network has more than 4096 wires after simplification");
+  WS open_ws;
+  for (int q : P->open_qubits)
+    if (pw_of[net.output_wire[q]] >= 0) open_ws.set(pw_of[net.output_wire[q]]);
+
+  Tree base;
+  base.L = L;
+  base.sets.resize(L);
+  for (int i = 0; i < L; ++i)
+    for (int w : S.leaves[i].wires)
+      if (!S.fixed[w]) base.sets[i].set(pw_of[w]);
+  // leaf adjacency
+  std::vector<std::vector<std::pair<int, int>>> adj(L);
+  {
+    std::vector<std::vector<int>> own(W);
+    for (int i = 0; i < L; ++i)
+      for (size_t w = base.sets[i]._Find_first(); w < MAXW; w = base.sets[i]._Find_next(w))
+        own[w].push_back(i);
+    std::vector<std::unordered_map<int, int>> m(L);
+    for (int w = 0; w < W; ++w)
+      if (own[w].size() == 2) {
+        m[own[w][0]][own[w][1]]++;
+        m[own[w][1]][own[w][0]]++;
+      }
+    for (int i = 0; i < L; ++i)
+      for (auto& [j, c] : m[i]) adj[i].push_back({j, c});
+    for (auto& v : adj) std::sort(v.begin(), v.end());
+  }
+
+  // order search: randomised recursive bisection trials, each sliced to the bound
+  const int trials = o.trials > 0 ? o.trials : 64;
+  const int bound = o.max_log2_intermediate;
+  Tree best_tree;
+  std::vector<int> best_sl;
+  double best_total = std::numeric_limits<double>::infinity();
+  std::vector<int> all(L);
+  std::iota(all.begin(), all.end(), 0);
+  for (int tr = 0; tr < trials; ++tr) {
+    std::mt19937_64 rng(o.seed * 1000003ULL + (uint64_t)tr);
+    const double eps_choices[4] = {0.05, 0.12, 0.2, 0.3};
+    Bisector bis{adj, rng, eps_choices[(tr / 2) % 4], (tr % 2) ? 6 : 8, 3};
+    Tree t = base;
+    if (L == 1) {
+      // single tensor: no merge
+    } else {
+      bis.build(t, all);
+    }
+    std::vector<int> sl = (L > 1) ? choose_slices(t, open_ws, bound, o.min_log2_slices)
+                                  : std::vector<int>{};
+    WS slw;
+    for (int w : sl) slw.set(w);
+    double total = pow2((int)sl.size()) * tree_cost(t, slw);
+    if (total < best_total) {
+      best_total = total;
+      best_tree = t;
+      best_sl = sl;
+    }
+  }
+  if (L == 1 && o.min_log2_slices > 0) fail(TN_ERR_PLAN, "a single-tensor network cannot be sliced");
+  // subtree reconfiguration with the slices in place, then re-slice if that helps
+  if (L > 2) {
+    WS slw;
+    for (int w : best_sl) slw.set(w);
+    Tree t2 = best_tree;
+    reconfigure(t2, slw, 3);
+    std::vector<int> sl2 = choose_slices(t2, open_ws, bound, o.min_log2_slices);
+    WS s2;
+    for (int w : sl2) s2.set(w);
+    const double tot2 = pow2((int)sl2.size()) * tree_cost(t2, s2);
+    if (tot2 < best_total) {
+      best_total = tot2;
+      best_tree = t2;
+      best_sl = sl2;
+    }
+  }
+  Tree& T = best_tree;
+  WS SL;
+  for (int w : best_sl) SL.set(w);
+  const int nS = (int)best_sl.size();
+  const int nm = (int)T.merges.size();
+
+  const std::vector<int> order = (nm > 0) ? post_order(T) : std::vector<int>{};
+  // dependence of every node on the sliced wires (through its subtree's leaves)
+  std::vector<WS> dep(T.sets.size());
+  for (int i = 0; i < L; ++i) dep[i] = T.sets[i] & SL;
+  for (int i : order) dep[L + i] = dep[T.merges[i].first] | dep[T.merges[i].second];
+
+  // batch bits: choose which sliced wires vary inside a chunk
+  auto chunk_cost = [&](const WS& B) {
+    double c = 0;
+    for (int i = 0; i < nm; ++i) {
+      const WS& a = T.sets[T.merges[i].first];
+      const WS& b = T.sets[T.merges[i].second];
+      const int mult = (int)(dep[L + i] & B).count();
+      c += pow2(mult) * CostModel::step((int)((a | b) & ~SL).count(), (int)(a & ~SL).count(),
+                                        (int)(b & ~SL).count(), (int)(T.sets[L + i] & ~SL).count());
+    }
+    return c;
+  };
+  std::vector<int> order_sl;  // slice bit order: batch bits first
+  {
+    WS B;
+    std::vector<int> rest = best_sl;
+    const int bmax = std::min(nS, 12);
+    for (int j = 0; j < bmax; ++j) {
+      int bw = -1;
+      double bc = std::numeric_limits<double>::infinity();
+      for (int w : rest) {
+        WS B2 = B;
+        B2.set(w);
+        const double c = chunk_cost(B2);
+        if (c < bc) {
+          bc = c;
+          bw = w;
+        }
+      }
+      B.set(bw);
+      order_sl.push_back(bw);
+      rest.erase(std::find(rest.begin(), rest.end(), bw));
+    }
+    for (int w : rest) order_sl.push_back(w);
+  }
+  std::vector<int> slice_bit(W, -1);
+  for (int j = 0; j < nS; ++j) slice_bit[order_sl[j]] = j;
+  for (int j = 0; j < nS; ++j) P->sliced.push_back(net.labels[wire_of_pw[order_sl[j]]]);
+
+  // ------------------------------------------------ step program for a given b
+  struct NodeInfo {
+    std::vector<int> wires;  // planning wires (unsliced), storage order
+    uint32_t bmask = 0;
+    int64_t off = -1;
+  };
+  auto elems_of = [](const NodeInfo& ni) {
+    return (int64_t)1 << (ni.wires.size() + __builtin_popcount(ni.bmask));
+  };
+  const int64_t cap_bytes = o.max_arena_bytes > 0 ? o.max_arena_bytes : (int64_t)96 << 30;
+  auto layout = [&](int b, std::vector<NodeInfo>& info, std::vector<StepDesc>& steps,
+                    int64_t& arena) -> bool {
+    info.assign(L + nm, NodeInfo{});
+    const uint32_t lowmask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
+    for (int i = 0; i < L; ++i) {
+      for (int w : S.leaves[i].wires)
+        if (!S.fixed[w] && !SL.test(pw_of[w])) info[i].wires.push_back(pw_of[w]);
+      for (int w : S.leaves[i].wires)
+        if (!S.fixed[w] && SL.test(pw_of[w]) && slice_bit[pw_of[w]] < b)
+          info[i].bmask |= 1u << slice_bit[pw_of[w]];
+    }
+    // best-fit arena allocator
+    std::vector<std::pair<int64_t, int64_t>> freel;  // (offset, size)
+    int64_t end = 0;
+    const int64_t AL = 64;
+    auto alloc = [&](int64_t sz) {
+      sz = (sz + AL - 1) / AL * AL;
+      int bi = -1;
+      for (size_t i = 0; i < freel.size(); ++i)
+        if (freel[i].second >= sz && (bi < 0 || freel[i].second < freel[bi].second)) bi = (int)i;
+      if (bi >= 0) {
+        const int64_t off = freel[bi].first;
+        freel[bi].first += sz;
+        freel[bi].second -= sz;
+        if (freel[bi].second == 0) freel.erase(freel.begin() + bi);
+        return off;
+      }
+      const int64_t off = end;
+      end += sz;
+      return off;
+    };
+    auto release = [&](int64_t off, int64_t sz) {
+      sz = (sz + AL - 1) / AL * AL;
+      freel.push_back({off, sz});
+      std::sort(freel.begin(), freel.end());
+      std::vector<std::pair<int64_t, int64_t>> merged;
+      for (auto& f : freel) {
+        if (!merged.empty() && merged.back().first + merged.back().second == f.first)
+          merged.back().second += f.second;
+        else
+          merged.push_back(f);
+      }
+      freel.swap(merged);
+      if (!freel.empty() && freel.back().first + freel.back().second == end) {
+        end = freel.back().first;
+        freel.pop_back();
+      }
+    };
+    int64_t peak = 0;
+    for (int i = 0; i < L; ++i) {
+      info[i].off = alloc(elems_of(info[i]));
+      peak = std::max(peak, end);
+    }
+    steps.clear();
+    for (int mi : order) {
+      const int x = T.merges[mi].first, y = T.merges[mi].second;
+      const int64_t ex = elems_of(info[x]), ey = elems_of(info[y]);
+      const bool x_is_a = ex > ey || (ex == ey && info[x].wires.size() >= info[y].wires.size());
+      const NodeInfo& A = info[x_is_a ? x : y];
+      const NodeInfo& B = info[x_is_a ? y : x];
+      NodeInfo C;
+      StepDesc d;
+      std::memset(&d, 0, sizeof(d));
+      std::vector<int> mw, kw, nw;
+      for (int w : A.wires)
+        (std::find(B.wires.begin(), B.wires.end(), w) != B.wires.end() ? kw : mw).push_back(w);
+      for (int w : B.wires)
+        if (std::find(A.wires.begin(), A.wires.end(), w) == A.wires.end()) nw.push_back(w);
+      if ((int)(mw.size() + kw.size()) > MAXR || (int)(kw.size() + nw.size()) > MAXR ||
+          (int)(mw.size() + nw.size()) > MAXR)
+        fail(TN_ERR_UNSUPPORTED, "a tensor exceeds the kernels' rank limit");
+      C.wires = mw;
+      C.wires.insert(C.wires.end(), nw.begin(), nw.end());
+      C.bmask = A.bmask | B.bmask;
+      auto pos_in = [](const std::vector<int>& ws, int w) {
+        return (int)(std::find(ws.begin(), ws.end(), w) - ws.begin());
+      };
+      d.nm = (int)mw.size();
+      d.nk = (int)kw.size();
+      d.nn = (int)nw.size();
+      for (int i = 0; i < d.nm; ++i) d.a_mpos[i] = (int8_t)pos_in(A.wires, mw[i]);
+      for (int i = 0; i < d.nk; ++i) {
+        d.a_kpos[i] = (int8_t)pos_in(A.wires, kw[i]);
+        d.b_kpos[i] = (int8_t)pos_in(B.wires, kw[i]);
+      }
+      for (int i = 0; i < d.nn; ++i) d.b_npos[i] = (int8_t)pos_in(B.wires, nw[i]);
+      for (int i = 0; i < d.nm; ++i) d.c_mpos[i] = (int8_t)i;
+      for (int i = 0; i < d.nn; ++i) d.c_npos[i] = (int8_t)(d.nm + i);
+      d.nbc = __builtin_popcount(C.bmask);
+      int t = 0;
+      for (int j = 0; j < 32; ++j)
+        if ((C.bmask >> j) & 1) {
+          if ((A.bmask >> j) & 1) d.a_bsel |= 1u << t;
+          if ((B.bmask >> j) & 1) d.b_bsel |= 1u << t;
+          ++t;
+        }
+      d.a_size = (int64_t)1 << A.wires.size();
+      d.b_size = (int64_t)1 << B.wires.size();
+      d.c_size = (int64_t)1 << C.wires.size();
+      d.a_off = A.off;
+      d.b_off = B.off;
+      C.off = alloc(elems_of(C));
+      d.c_off = C.off;
+      peak = std::max(peak, end);
+      d.kernel = -1;
+      release(A.off, elems_of(A));
+      release(B.off, elems_of(B));
+      info[L + mi] = C;
+      steps.push_back(d);
+    }
+    arena = peak;
+    (void)lowmask;
+    return peak * 8 <= cap_bytes;
+  };
+
+  std::vector<NodeInfo> info;
+  std::vector<StepDesc> steps;
+  int64_t arena = 0;
+  int b = o.log2_batch_slices > 0 ? std::min(o.log2_batch_slices, std::min(nS, 12)) : std::min(nS, 12);
+  while (true) {
+    const bool ok = layout(b, info, steps, arena);
+    if (ok) break;
+    if (b == 0) fail(TN_ERR_PLAN, "one slice does not fit the arena cap");
+    --b;
+  }
+  P->log2_batch = b;
+  P->steps = steps;
+  P->arena_elems = arena;
+
+  // leaves: source data ordered [kept planning wires, sliced wires by slice bit, closed outputs]
+  P->leaves.resize(L);
+  for (int i = 0; i < L; ++i) {
+    const HTensor& lf = S.leaves[i];
+    std::vector<int> ord, kind, idx;
+    for (int w : info[i].wires) ord.push_back(wire_of_pw[w]);
+    std::vector<std::pair<int, int>> sw;
+    for (int w : lf.wires)
+      if (!S.fixed[w] && SL.test(pw_of[w])) sw.push_back({slice_bit[pw_of[w]], w});
+    std::sort(sw.begin(), sw.end());
+    for (auto [j, w] : sw) {
+      ord.push_back(w);
+      kind.push_back(0);
+      idx.push_back(j);
+    }
+    for (int w : lf.wires)
+      if (S.fixed[w]) {
+        ord.push_back(w);
+        kind.push_back(1);
+        idx.push_back(net.labels[w].q);
+      }
+    if ((int)kind.size() > MAXFIX) fail(TN_ERR_UNSUPPORTED, "a leaf carries too many fixed wires");
+    HTensor pt = hpermute(lf, ord);
+    LeafDesc& ld = P->leaves[i];
+    std::memset(&ld, 0, sizeof(ld));
+    ld.src_off = (int64_t)P->leaf_data.size();
+    ld.dst_off = info[i].off;
+    ld.rank = (int)info[i].wires.size();
+    ld.bmask = info[i].bmask;
+    ld.nfixed = (int)kind.size();
+    for (size_t f = 0; f < kind.size(); ++f) {
+      ld.fixed_kind[f] = (int8_t)kind[f];
+      ld.fixed_index[f] = (int8_t)idx[f];
+    }
+    for (const cd& v : pt.data) P->leaf_data.push_back(std::complex<float>((float)v.real(), (float)v.imag()));
+  }
+  // root
+  const int root = (nm > 0) ? (L + order.back()) : 0;
+  const NodeInfo& R = info[root];
+  if ((int)R.wires.size() != k_open) fail(TN_ERR_PLAN, "internal: root rank differs from open qubits");
+  P->root.off = R.off;
+  P->root.rank = k_open;
+  P->root.bmask = R.bmask;
+  for (int j = 0; j < k_open; ++j) {
+    const int w = pw_of[net.output_wire[P->open_qubits[j]]];
+    const int p = (int)(std::find(R.wires.begin(), R.wires.end(), w) - R.wires.begin());
+    if (p >= (int)R.wires.size()) fail(TN_ERR_PLAN, "internal: open wire missing from the root");
+    P->root.pos_of_open[j] = (int8_t)p;
+  }
+  // statistics
+  PlanStats& st = P->stats;
+  for (int i = 0; i < L; ++i) st.log2_max = std::max(st.log2_max, (int)info[i].wires.size());
+  for (const StepDesc& d : P->steps) {
+    const double macs = pow2(d.nm + d.nk + d.nn);
+    const double el = (double)(d.a_size + d.b_size + d.c_size);
+    st.flops_slice += 8.0 * macs;
+    st.bytes_slice += 8.0 * el;
+    st.flops_chunk += 8.0 * macs * pow2(d.nbc);
+    double elc = 0;
+    elc += (double)d.c_size * pow2(d.nbc);
+    elc += (double)d.a_size * pow2(__builtin_popcount(d.a_bsel));
+    elc += (double)d.b_size * pow2(__builtin_popcount(d.b_bsel));
+    st.bytes_chunk += 8.0 * elc;
+    st.log2_max = std::max(st.log2_max, d.nm + d.nn);
+    st.khist[std::min(d.nk, 39)]++;
+  }
+  guard.release();
+  return P;
+}
+
+}  // namespace tnx
+
+using namespace tnx;
+
+extern "C" tn_status tn_plan_default_opts(tn_plan_opts* o) {
+  clear_error();
+  if (!o) {
+    set_error("tn_plan_default_opts: NULL");
+    return TN_ERR_ARG;
+  }
+  std::memset(o, 0, sizeof(*o));
+  o->open_mask = 0;
+  o->max_log2_intermediate = 30;
+  o->min_log2_slices = 0;
+  o->seed = 1;
+  o->trials = 64;
+  o->precision = TN_PREC_FP32;
+  o->complex_mult = 4;
+  o->log2_batch_slices = 0;
+  o->max_arena_bytes = (int64_t)96 << 30;
+  o->fuse_permute = 1;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan(const tn_network_t* net, const tn_plan_opts* opts, tn_plan_t** out) {
+  try {
+    clear_error();
+    if (!net || !opts || !out) fail(TN_ERR_ARG, "tn_plan: NULL argument");
+    *out = nullptr;
+    Plan* p = build_plan(net->net, *opts);
+    auto* h = new (std::nothrow) tn_plan_s;
+    if (!h) {
+      delete p;
+      fail(TN_ERR_OOM, "host allocation failed");
+    }
+    h->plan = std::move(*p);
+    delete p;
+    *out = h;
+    return TN_OK;
+  } catch (const TnError& e) {
+    set_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return TN_ERR_OOM;
+  }
+}
+
+extern "C" tn_status tn_plan_info(const tn_plan_t* h, tn_plan_stats* s) {
+  clear_error();
+  if (!h || !s) {
+    set_error("tn_plan_info: NULL argument");
+    return TN_ERR_ARG;
+  }
+  const Plan& p = h->plan;
+  std::memset(s, 0, sizeof(*s));
+  s->n_qubits = p.n_qubits;
+  s->n_open = (int)p.open_qubits.size();
+  s->n_leaves = p.n_leaves;
+  s->n_steps = (int)p.steps.size();
+  s->log2_slices = (int)p.sliced.size();
+  s->log2_batch_slices = p.log2_batch;
+  s->log2_max_intermediate = p.stats.log2_max;
+  s->precision = p.opts.precision;
+  s->flops_per_slice = p.stats.flops_slice;
+  s->bytes_per_slice = p.stats.bytes_slice;
+  s->flops_per_chunk = p.stats.flops_chunk;
+  s->bytes_per_chunk = p.stats.bytes_chunk;
+  s->arena_bytes = p.arena_elems * 8;
+  for (int i = 0; i < 40; ++i) s->k_histogram[i] = p.stats.khist[i];
+  s->complex_mult = p.opts.complex_mult;
+  s->n_kernel_launches_per_chunk = (int)p.steps.size() + 3;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_sliced_wires(const tn_plan_t* h, int32_t* qubit, int32_t* t, int32_t cap,
+                                          int32_t* count) {
+  clear_error();
+  if (!h || !count || (cap > 0 && (!qubit || !t))) {
+    set_error("tn_plan_sliced_wires: NULL argument");
+    return TN_ERR_ARG;
+  }
+  const Plan& p = h->plan;
+  *count = (int)p.sliced.size();
+  for (int j = 0; j < (int)p.sliced.size() && j < cap; ++j) {
+    qubit[j] = p.sliced[j].q;
+    t[j] = p.sliced[j].t;
+  }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_step_shape(const tn_plan_t* h, int32_t step, int32_t* lm, int32_t* lk,
+                                        int32_t* ln, int32_t* lb) {
+  clear_error();
+  if (!h || !lm || !lk || !ln || !lb) {
+    set_error("tn_plan_step_shape: NULL argument");
+    return TN_ERR_ARG;
+  }
+  const Plan& p = h->plan;
+  if (step < 0 || step >= (int)p.steps.size()) {
+    set_error("tn_plan_step_shape: step out of range");
+    return TN_ERR_ARG;
+  }
+  const StepDesc& d = p.steps[step];
+  *lm = d.nm;
+  *lk = d.nk;
+  *ln = d.nn;
+  *lb = d.nbc;
+  return TN_OK;
+}

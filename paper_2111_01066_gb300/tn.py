@@ -1,0 +1,257 @@
+"""ctypes binding of the C ABI declared in include/tn.h.
+
+Argument marshalling only: every step of the contraction runs in the library
+(host planner in C++, slices in CUDA kernels).  Device buffers are torch CUDA
+tensors, passed by data pointer; streams are torch CUDA streams.  There is no
+CPU fallback: if the shared library is missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_NAME = "libtn_gb300.so"
+LIB_PATH = os.path.join(_HERE, LIB_NAME)
+
+TN_OK = 0
+TN_ERR_ARG = -1
+TN_ERR_OOM = -2
+TN_ERR_CUDA = -3
+TN_ERR_PLAN = -4
+TN_ERR_TIMEOUT = -5
+TN_ERR_UNSUPPORTED = -6
+TN_ERR_DEVICE = -7
+
+PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2, "fp16x3": 3}
+PREC_NAME = {v: k for k, v in PREC.items()}
+
+
+class TnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tn status {status}: {msg}")
+        self.status = status
+
+
+class tn_circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32),
+                ("gate_qubits", ctypes.POINTER(ctypes.c_int32)),
+                ("gate_matrices", ctypes.POINTER(ctypes.c_double)),
+                ("gate_layer", ctypes.POINTER(ctypes.c_int32))]
+
+
+class tn_plan_opts(ctypes.Structure):
+    _fields_ = [("open_mask", ctypes.c_uint64), ("max_log2_intermediate", ctypes.c_int32),
+                ("min_log2_slices", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("trials", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("complex_mult", ctypes.c_int32), ("log2_batch_slices", ctypes.c_int32),
+                ("max_arena_bytes", ctypes.c_int64), ("fuse_permute", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class tn_plan_stats(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_open", ctypes.c_int32),
+                ("n_leaves", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+                ("log2_slices", ctypes.c_int32), ("log2_batch_slices", ctypes.c_int32),
+                ("log2_max_intermediate", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("flops_per_slice", ctypes.c_double), ("bytes_per_slice", ctypes.c_double),
+                ("flops_per_chunk", ctypes.c_double), ("bytes_per_chunk", ctypes.c_double),
+                ("arena_bytes", ctypes.c_int64), ("k_histogram", ctypes.c_int32 * 40),
+                ("complex_mult", ctypes.c_int32), ("n_kernel_launches_per_chunk", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes); every symbol include/tn.h declares
+_SIGS = {
+    "tn_last_error": (ctypes.c_char_p, []),
+    "tn_network_from_circuit": (ctypes.c_int, [ctypes.POINTER(tn_circuit), ctypes.POINTER(ctypes.c_void_p)]),
+    "tn_network_wire_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "tn_network_destroy": (None, [ctypes.c_void_p]),
+    "tn_plan_default_opts": (ctypes.c_int, [ctypes.POINTER(tn_plan_opts)]),
+    "tn_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tn_plan_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "tn_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tn_plan_stats)]),
+    "tn_plan_sliced_wires": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "tn_plan_step_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    "tn_contract_slices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "tn_plan_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tn_plan_destroy": (None, [ctypes.c_void_p]),
+    "tn_xeb": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "tn_permute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, ctypes.c_void_p]),
+    "tn_contract_pair": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                        ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load the shared library (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"{p} not built: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != TN_OK:
+        msg = load().tn_last_error()
+        raise TnError(status, msg.decode() if msg else "")
+
+
+def _i32(seq) -> ctypes.Array:
+    arr = (ctypes.c_int32 * max(1, len(seq)))()
+    for i, v in enumerate(seq):
+        arr[i] = int(v)
+    return arr
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+class Network:
+    """tn_network_from_circuit: a circuit (rqcgen.Circuit or arrays) as a tensor network."""
+
+    def __init__(self, circuit):
+        lib = load()
+        qs = np.ascontiguousarray(circuit.gate_qubits, dtype=np.int32)
+        mats = circuit.flat_matrices()
+        layers = np.ascontiguousarray(circuit.gate_layer, dtype=np.int32)
+        c = tn_circuit(circuit.n_qubits, circuit.n_gates,
+                       qs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                       mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       layers.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        h = ctypes.c_void_p()
+        _check(lib.tn_network_from_circuit(ctypes.byref(c), ctypes.byref(h)))
+        self.handle = h
+        self.n_qubits = circuit.n_qubits
+
+    def gates_per_qubit(self) -> List[int]:
+        arr = (ctypes.c_int32 * self.n_qubits)()
+        _check(load().tn_network_wire_counts(self.handle, arr, self.n_qubits))
+        return list(arr)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tn_network_destroy(self.handle)
+            self.handle = None
+
+
+def default_opts() -> tn_plan_opts:
+    o = tn_plan_opts()
+    _check(load().tn_plan_default_opts(ctypes.byref(o)))
+    return o
+
+
+class Plan:
+    """tn_plan: contraction order + slice set + device step program (host only)."""
+
+    def __init__(self, network: Network, open_mask: int = 0, max_log2_intermediate: int = 30,
+                 min_log2_slices: int = 0, precision: str = "fp32", complex_mult: int = 4,
+                 seed: int = 1, trials: int = 64, log2_batch_slices: int = 0,
+                 max_arena_bytes: int = 0, fuse_permute: int = 1):
+        lib = load()
+        o = default_opts()
+        o.open_mask = open_mask
+        o.max_log2_intermediate = max_log2_intermediate
+        o.min_log2_slices = min_log2_slices
+        o.seed = seed
+        o.trials = trials
+        o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        o.complex_mult = complex_mult
+        o.log2_batch_slices = log2_batch_slices
+        if max_arena_bytes:
+            o.max_arena_bytes = max_arena_bytes
+        o.fuse_permute = fuse_permute
+        h = ctypes.c_void_p()
+        _check(lib.tn_plan(network.handle, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+        self.network = network
+        self.open_mask = open_mask
+
+    def info(self) -> dict:
+        s = tn_plan_stats()
+        _check(load().tn_plan_info(self.handle, ctypes.byref(s)))
+        d = {name: getattr(s, name) for name, _ in tn_plan_stats._fields_}
+        d["k_histogram"] = list(s.k_histogram)
+        return d
+
+    def sliced_wires(self) -> List[Tuple[int, int]]:
+        cnt = ctypes.c_int32()
+        q = (ctypes.c_int32 * 64)()
+        t = (ctypes.c_int32 * 64)()
+        _check(load().tn_plan_sliced_wires(self.handle, q, t, 64, ctypes.byref(cnt)))
+        return [(q[j], t[j]) for j in range(cnt.value)]
+
+    def step_shapes(self) -> List[Tuple[int, int, int, int]]:
+        n = self.info()["n_steps"]
+        out = []
+        a, b, c, d = (ctypes.c_int32() for _ in range(4))
+        for i in range(n):
+            _check(load().tn_plan_step_shape(self.handle, i, ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.byref(c), ctypes.byref(d)))
+            out.append((a.value, b.value, c.value, d.value))
+        return out
+
+    def contract_slices(self, slice_first: int, slice_count: int, bitstrings: Sequence[int],
+                        out, stream=None) -> None:
+        """Add the slices' contribution to `out` (torch complex128 CUDA tensor of
+        n_batches * 2^k amplitudes)."""
+        bs = (ctypes.c_uint64 * len(bitstrings))(*[int(b) for b in bitstrings])
+        _check(load().tn_contract_slices(self.handle, slice_first, slice_count, bs, len(bitstrings),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+
+    def sync(self, stream=None) -> None:
+        _check(load().tn_plan_sync(self.handle, _stream_handle(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tn_plan_destroy(self.handle)
+            self.handle = None
+
+
+def xeb(amplitudes, n_qubits: int, stream=None) -> float:
+    """tn_xeb on a complex128 CUDA tensor."""
+    f = ctypes.c_double()
+    _check(load().tn_xeb(ctypes.c_void_p(amplitudes.data_ptr()), amplitudes.numel(), n_qubits,
+                         ctypes.byref(f), _stream_handle(stream)))
+    return f.value
+
+
+def permute(inp, out, rank: int, perm: Sequence[int], batch: int = 1, stream=None) -> None:
+    """tn_permute on complex64 CUDA tensors."""
+    _check(load().tn_permute(ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()), rank,
+                             _i32(perm), batch, _stream_handle(stream)))
+
+
+def contract_pair(a, a_wires, b, b_wires, c, c_wires, batch: int = 1, precision: str = "fp32",
+                  complex_mult: int = 4, stream=None) -> None:
+    """tn_contract_pair on complex64 CUDA tensors."""
+    p = PREC[precision] if isinstance(precision, str) else int(precision)
+    _check(load().tn_contract_pair(ctypes.c_void_p(a.data_ptr()), _i32(a_wires), len(a_wires),
+                                   ctypes.c_void_p(b.data_ptr()), _i32(b_wires), len(b_wires),
+                                   ctypes.c_void_p(c.data_ptr()), _i32(c_wires), len(c_wires),
+                                   batch, p, complex_mult, _stream_handle(stream)))

@@ -1,0 +1,110 @@
+"""CPU-only checks of the C ABI: the library loads, exports every symbol the
+header declares, validates arguments, and the host planner (tn_plan makes no
+CUDA call) produces consistent plans."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import rqcgen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_01066_gb300 import tn as _tn
+    return _tn
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "tn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(tn):
+    lib = tn.load()
+    syms = _declared_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(lib, s), f"missing export {s}"
+        assert s in tn._SIGS, f"binding lacks {s}"
+
+
+def test_network_argument_errors(tn):
+    lib = tn.load()
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.tn_network_from_circuit(None, ctypes.byref(h)) == tn.TN_ERR_ARG
+    assert b"NULL" in lib.tn_last_error()
+    bad = tn.tn_circuit(0, 0, None, None, None)
+    assert lib.tn_network_from_circuit(ctypes.byref(bad), ctypes.byref(h)) == tn.TN_ERR_ARG
+    q = (ctypes.c_int32 * 2)(0, 0)       # a gate acting twice on qubit 0
+    m = (ctypes.c_double * 32)()
+    c = tn.tn_circuit(2, 1, q, m, None)
+    assert lib.tn_network_from_circuit(ctypes.byref(c), ctypes.byref(h)) == tn.TN_ERR_ARG
+
+
+def test_plan_options_validated(tn):
+    circ, om, _ = rqcgen.config_circuit("c1")
+    net = tn.Network(circ)
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(net, open_mask=om, precision=7)
+    assert e.value.status == tn.TN_ERR_ARG
+    with pytest.raises(tn.TnError):
+        tn.Plan(net, open_mask=om, complex_mult=5)
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(net, open_mask=om, max_log2_intermediate=6)   # 12 open qubits > 2^6
+    assert e.value.status == tn.TN_ERR_PLAN
+
+
+def test_wire_counts(tn):
+    circ, _, _ = rqcgen.config_circuit("c1")
+    net = tn.Network(circ)
+    gpq = net.gates_per_qubit()
+    want = [int(np.sum((circ.gate_qubits[:, 0] == q) | (circ.gate_qubits[:, 1] == q)))
+            for q in range(circ.n_qubits)]
+    assert gpq == want
+
+
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_plan_respects_bound_and_reports(tn, name):
+    cfg = rqcgen.CONFIGS[name]
+    circ, om, _ = rqcgen.config_circuit(name)
+    net = tn.Network(circ)
+    plan = tn.Plan(net, open_mask=om, max_log2_intermediate=cfg["log2_bound"], trials=16)
+    info = plan.info()
+    assert info["n_open"] == cfg["k_open"]
+    assert info["log2_max_intermediate"] <= cfg["log2_bound"]
+    assert info["n_steps"] == info["n_leaves"] - 1
+    assert sum(info["k_histogram"]) == info["n_steps"]
+    shapes = plan.step_shapes()
+    flops = sum(8 * 2 ** (m + k + n) for m, k, n, _ in shapes)
+    assert math.isclose(flops, info["flops_per_slice"], rel_tol=1e-12)
+    for m, k, n, _ in shapes:
+        assert m + k <= cfg["log2_bound"] and k + n <= cfg["log2_bound"] and m + n <= cfg["log2_bound"]
+
+
+def test_forced_slices_and_wire_labels(tn):
+    circ, om, _ = rqcgen.config_circuit("c1")
+    net = tn.Network(circ)
+    gpq = net.gates_per_qubit()
+    plan = tn.Plan(net, open_mask=om & 0xFF, max_log2_intermediate=30, min_log2_slices=5, trials=8)
+    sl = plan.sliced_wires()
+    assert len(sl) == 5 == plan.info()["log2_slices"]
+    for q, t in sl:
+        assert 0 <= q < circ.n_qubits and 1 <= t < gpq[q], "sliced wires are internal wires"
+    assert len(set(sl)) == 5
+
+
+def test_plan_is_deterministic(tn):
+    circ, om, _ = rqcgen.config_circuit("c2")
+    net = tn.Network(circ)
+    a = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3)
+    b = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3)
+    assert a.step_shapes() == b.step_shapes() and a.sliced_wires() == b.sliced_wires()

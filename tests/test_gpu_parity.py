@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative, norm-wise over a batch): FP32 SIMT path 1e-5; every path
+must stay within the stated 1e-3 amplitude target.  Kernel-level checks use
+the same element-wise bound scaled by the operands' norms.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import rqcgen
+from oracle import pairwise
+from oracle import statevector as sv
+from oracle import xeb as oxeb
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_01066_gb300 import tn
+    torch.cuda.set_device(0)
+    return tn, torch
+
+
+def _run_plan(tn, torch, plan, first, count, bitstrings, k_open):
+    out = torch.zeros(len(bitstrings) * (2 << k_open), dtype=torch.float64, device="cuda")
+    plan.contract_slices(first, count, bitstrings, out)
+    plan.sync()
+    return out.cpu().numpy().view(np.complex128)
+
+
+def _relerr(got, want):
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+def test_c1_fp32_all_amplitudes(env):
+    tn, torch = env
+    circ, om, cb = rqcgen.config_circuit("c1")
+    want = sv.batch_amplitudes(sv.simulate(circ), circ.n_qubits, cb, om)
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=30)
+    got = _run_plan(tn, torch, plan, 0, 1, [cb], 12)
+    assert _relerr(got, want) < FP32_TOL
+
+
+def test_c1_sliced_batches_and_ragged_ranges(env):
+    """Slices summed in chunks of 2^b with ragged ends equal the full amplitudes."""
+    tn, torch = env
+    circ, _, _ = rqcgen.config_circuit("c1")
+    om = 0b111100001111
+    psi = sv.simulate(circ)
+    bits = [0b000011110000, 0b000001010000, 0b000010100000]
+    want = np.concatenate([sv.batch_amplitudes(psi, circ.n_qubits, b, om) for b in bits])
+    net = tn.Network(circ)
+    for lb in (0, 2, 3):
+        plan = tn.Plan(net, open_mask=om, max_log2_intermediate=30, min_log2_slices=5,
+                       log2_batch_slices=lb, trials=8)
+        s = plan.info()["log2_slices"]
+        assert s == 5
+        got = _run_plan(tn, torch, plan, 0, 1 << s, bits, 8)
+        assert _relerr(got, want) < FP32_TOL
+        # ragged split of the slice range, accumulated into one buffer
+        out = torch.zeros(len(bits) * (2 << 8), dtype=torch.float64, device="cuda")
+        for first, count in ((0, 3), (3, 10), (13, 1), (14, 18)):
+            plan.contract_slices(first, count, bits, out)
+        plan.sync()
+        assert _relerr(out.cpu().numpy().view(np.complex128), want) < FP32_TOL
+
+
+def test_c1_range_errors(env):
+    tn, torch = env
+    circ, om, cb = rqcgen.config_circuit("c1")
+    plan = tn.Plan(tn.Network(circ), open_mask=om & 0xFF, min_log2_slices=3, trials=4)
+    out = torch.zeros(2 << 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(tn.TnError) as e:
+        plan.contract_slices(5, 4, [cb], out)        # 5 + 4 > 2^3
+    assert e.value.status == tn.TN_ERR_ARG
+    with pytest.raises(tn.TnError):
+        plan.contract_slices(0, 1, [], out)
+    plan.contract_slices(0, 0, [cb], out)            # empty range is a no-op
+    plan.sync()
+    assert float(out.abs().max()) == 0.0
+
+
+def test_c2_fp32_against_golden(env):
+    tn, torch = env
+    from tests.golden.make_golden import read
+    want = read("c2")
+    circ, om, cb = rqcgen.config_circuit("c2")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=26)
+    n_sl = 1 << plan.info()["log2_slices"]
+    got = _run_plan(tn, torch, plan, 0, n_sl, [cb], 10)
+    assert _relerr(got, want) < FP32_TOL
+
+
+SHAPES = [  # (m bits, k bits, n bits): several tiles, ragged (smaller than a tile), degenerate
+    (0, 0, 0), (1, 0, 3), (0, 4, 0), (1, 1, 1), (3, 2, 5), (9, 5, 3), (10, 7, 7),
+    (12, 3, 2), (5, 9, 8), (13, 4, 4), (8, 6, 11), (2, 12, 2), (11, 1, 6),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("batch", [1, 3])
+def test_contract_pair_fp32(env, shape, batch):
+    tn, torch = env
+    nm, nk, nn = shape
+    rng = np.random.default_rng(hash(shape) % 1000 + batch)
+    wires = list(range(100, 100 + nm + nk + nn))
+    m_w, k_w, n_w = wires[:nm], wires[nm:nm + nk], wires[nm + nk:]
+    a_w = list(rng.permutation(m_w + k_w))
+    b_w = list(rng.permutation(k_w + n_w))
+    c_w = list(rng.permutation(m_w + n_w))
+    a = (rng.normal(size=(batch, 2 ** len(a_w))) + 1j * rng.normal(size=(batch, 2 ** len(a_w)))) / 2
+    b = (rng.normal(size=(batch, 2 ** len(b_w))) + 1j * rng.normal(size=(batch, 2 ** len(b_w)))) / 2
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    ta, tb = dev(a), dev(b)
+    tc = torch.empty((batch, 2 ** len(c_w)), dtype=torch.complex64, device="cuda")
+    tn.contract_pair(ta, a_w, tb, b_w, tc, c_w, batch=batch, precision="fp32")
+    torch.cuda.synchronize()
+    got = tc.cpu().numpy()
+    for i in range(batch):
+        want = pairwise.contract_pair(a[i], a_w, b[i], b_w, c_w)
+        scale = math.sqrt(2 ** nk) * np.sqrt(np.mean(np.abs(a[i]) ** 2) * np.mean(np.abs(b[i]) ** 2))
+        assert np.max(np.abs(got[i] - want)) <= 1e-5 * max(scale, 1e-30) * 8
+
+
+@pytest.mark.parametrize("rank", [1, 2, 5, 9, 14, 20])
+def test_permute_bit_exact(env, rank):
+    tn, torch = env
+    rng = np.random.default_rng(rank)
+    batch = 2
+    perm = list(rng.permutation(rank))
+    x = (rng.normal(size=(batch, 2 ** rank)) + 1j * rng.normal(size=(batch, 2 ** rank))).astype(np.complex64)
+    tx = torch.from_numpy(x).cuda()
+    ty = torch.empty_like(tx)
+    tn.permute(tx, ty, rank, perm, batch)
+    torch.cuda.synchronize()
+    got = ty.cpu().numpy()
+    for i in range(batch):
+        want = pairwise.permute(x[i], rank, perm).astype(np.complex64)
+        assert np.array_equal(got[i], want)
+
+
+def test_xeb_against_oracle(env):
+    tn, torch = env
+    rng = np.random.default_rng(5)
+    for n, count in ((12, 4096), (30, 1024), (53, 64), (20, 1)):
+        a = (rng.normal(size=count) + 1j * rng.normal(size=count)) * 2 ** (-n / 2)
+        t = torch.from_numpy(a).cuda()
+        f = tn.xeb(t, n)
+        want = oxeb.linear_xeb(a, n)
+        assert abs(f - want) <= 1e-12 * max(1.0, abs(want))
+    with pytest.raises(tn.TnError):
+        tn.xeb(torch.zeros(0, dtype=torch.complex128, device="cuda"), 10)

@@ -10,7 +10,7 @@ import rqcgen
 from oracle import statevector as sv
 from oracle import tensornet as tn
 
-from test_oracle_pins import _feynman_amplitude, _random_circuit
+from tests.test_oracle_pins import _feynman_amplitude, _random_circuit
 
 
 def _mutated_network(monkeypatch, mutate):
