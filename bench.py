@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the sliced tensor-network contraction on GB300.
+
+Workload (default "c3"): the 42-qubit 6x7-grid circuit with 16 cycles, its
+tree sliced into 2^12 slices with intermediates <= 2^28 complex64, all 4096
+slices contracted per step, 12 open qubits (4096 correlated amplitudes), XEB of
+the batch.  One step = tn_contract_slices over every slice + tn_xeb.
+
+value  : slices/s over the whole job, device-timed (CUDA events), inputs resident.
+e2e    : the same through the public API with host buffers: the batch's
+         bitstrings from pinned host memory in, amplitudes + XEB back to host.
+Also reported: complex TFLOP/s, the FP32 SIMT path on the same plan, relative
+amplitude and XEB error against the oracle's stored amplitudes, the roofline of
+the dominant kernel, SM clocks sampled during the timed region, and the oracle
+timed on the host cores (cpu_baseline).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU (one process per GPU via torchrun): each rank contracts every slice
+for its own bitstring batch (independent problems, weak scaling), no collective
+on the data path; a barrier and a max over ranks bracket the timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import rqcgen  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
+
+
+# ------------------------------------------------------------------ multi-process helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def batch_bits_for_rank(name: str, rank: int) -> int:
+    """Closed bits of the batch a rank contracts: rank 0 takes the workload's own
+    bitstring, rank r > 0 an independent one drawn from (seed, stream r + 1)."""
+    circ, om, cb = rqcgen.config_circuit(name)
+    if rank == 0:
+        return cb
+    return rqcgen.random_bits(circ.n_qubits, rqcgen.CONFIGS[name]["seed"], stream=rank + 1) & ~om
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import rqcgen
+from oracle import tensornet
+circ, om, cb = rqcgen.config_circuit({name!r})
+net = tensornet.CircuitNetwork(circ, cb, om)
+t0 = time.time()
+merges, extra = net.plan([], max_log2={maxlog!r}, method="bisect", trials={trials!r})
+plan_s = time.time() - t0
+budget = {budget!r}
+done, t_run = 0, 0.0
+while t_run < budget and done < (1 << len(extra)):
+    values = {{leg: (done >> j) & 1 for j, leg in enumerate(extra)}}
+    t1 = time.time()
+    net._run(merges, values)
+    t_run += time.time() - t1
+    done += 1
+print(json.dumps({{"sub_networks": 1 << len(extra), "timed": done, "seconds": t_run, "plan_s": plan_s}}))
+"""
+
+
+def oracle_timing(name: str, budget_s: float) -> dict:
+    """Time the FP64 oracle on a bounded sample: the oracle contracts the whole
+    batch as 2^E sub-networks of its own (its sub-slicing); `timed` of them are
+    run within the budget and the full-batch time is extrapolated."""
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, maxlog=26, trials=4, budget=budget_s)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=3600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip()[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    full = d["seconds"] / d["timed"] * d["sub_networks"]
+    return {"full_batch_seconds": full, "timed_sub_networks": d["timed"], "sub_networks": d["sub_networks"],
+            "seconds": d["seconds"]}
+
+
+def cores_used() -> int:
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ main
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(rqcgen.CONFIGS))
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--compare-fp32", type=int, default=1)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    name = args.workload
+    cfg = rqcgen.CONFIGS[name]
+    circ, om, _ = rqcgen.config_circuit(name)
+    n_slices = None
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        t = oracle_timing(name, args.cpu_budget)
+        total_slices = 1 << cfg["log2_slices"]
+        steps = []
+        if "error" not in t:
+            steps = [t["full_batch_seconds"]]
+        value = total_slices / t["full_batch_seconds"] if steps else None
+        line = {"impl": "reference", "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": 0,
+                "steps": 1, "warmup": 0, "ms_per_step": (steps[0] * 1e3 if steps else None),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": f"{name}: {circ.n_qubits}q {cfg['rows']}x{cfg['cols']} "
+                                                            f"d={cfg['cycles']}, 2^{cfg['log2_slices']} slices, "
+                                                            f"{cfg['k_open']} open qubits"},
+                "cpu_baseline": {"value": value, "unit": "slices/s", "cores": cores_used(), "kind": "oracle",
+                                 "sample": f"{t.get('timed_sub_networks')} of {t.get('sub_networks')} oracle "
+                                           f"sub-networks of the full batch, extrapolated"},
+                "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        if "error" in t:
+            line["unavailable"] = "oracle failed: " + t["error"]
+        print(json.dumps(line))
+        return 0
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    from paper_2111_01066_gb300 import tn
+    tn.load()
+
+    prec = args.precision if args.precision != "auto" else "fp32"
+    bits = batch_bits_for_rank(name, rank)
+    net = tn.Network(circ)
+    plan_kw = dict(open_mask=om, max_log2_intermediate=cfg["log2_bound"], min_log2_slices=cfg["log2_slices"])
+    t_plan = time.time()
+    plan = tn.Plan(net, precision=prec, **plan_kw)
+    t_plan = time.time() - t_plan
+    info = plan.info()
+    n_slices = 1 << info["log2_slices"]
+    k_open = info["n_open"]
+    n_chunks = max(1, n_slices >> info["log2_batch_slices"])
+    out = torch.zeros(2 << k_open, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p, o):
+        o.zero_()
+        p.contract_slices(0, n_slices, [bits], o, stream)
+        return tn.xeb(o.view(torch.complex128), circ.n_qubits, stream)
+
+    def timed(p, o, k, w):
+        for _ in range(w):
+            step(p, o)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            step(p, o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times
+
+    # untimed first call: device state + warm-up
+    step(plan, out)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = timed(plan, out, args.steps, args.warmup)
+    clk = clocks.stop()
+    barrier(world)
+    ms = statistics.mean(times)
+    ms_max = max_over_ranks(ms, world, dev)
+    total_units = n_slices * world
+    value = total_units / (ms_max / 1e3)
+    amps = out.cpu().numpy().view(np.complex128).copy()
+    f_xeb = tn.xeb(out.view(torch.complex128), circ.n_qubits)
+
+    # e2e: host bitstrings in, host amplitudes + XEB out, wall clock
+    host_amps = torch.empty(2 << k_open, dtype=torch.float64, pin_memory=True)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out.zero_()
+        plan.contract_slices(0, n_slices, [bits], out, stream)
+        host_amps.copy_(out, non_blocking=True)
+        tn.xeb(out.view(torch.complex128), circ.n_qubits, stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), world, dev)
+
+    # FP32 SIMT path on the same workload
+    fp32 = None
+    if args.compare_fp32 and prec != "fp32":
+        plan32 = tn.Plan(net, precision="fp32", **plan_kw)
+        out32 = torch.zeros_like(out)
+        step(plan32, out32)
+        t32 = timed(plan32, out32, min(3, args.steps), 1)
+        ms32 = max_over_ranks(statistics.mean(t32), world, dev)
+        fp32 = {"value": total_units / (ms32 / 1e3), "ms_per_step": ms32}
+
+    # roofline of the dominant kernel: per-step device times on the same stream
+    st = plan.step_times(reps=3, stream=stream)
+    shapes = plan.step_shapes()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+    i_dom = max(range(len(st)), key=lambda i: st[i])
+    m, k, n_, b = shapes[i_dom]
+    flops_dom = 8.0 * 2 ** (m + k + n_ + b)
+    ms_dom = st[i_dom]
+    sm_clock_ghz = 1.92  # FP32 peak clock assumption, see the design doc
+    fp32_peak_tf = 152 * 128 * 2 * sm_clock_ghz / 1e3
+    roof = {"bound": "alu", "achieved": flops_dom / (ms_dom / 1e3) / 1e12, "peak": fp32_peak_tf,
+            "unit": "TFLOP/s", "traffic": None, "step": i_dom, "shape_log2_mknb": [m, k, n_, b],
+            "share_of_step_time": ms_dom / sum(st)}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    # error against the oracle's stored amplitudes, when present
+    err = None
+    gold_path = os.path.join(ROOT, "tests", "golden", f"{name}_amplitudes.txt")
+    if rank == 0 and os.path.exists(gold_path):
+        from tests.golden.make_golden import read
+        want = read(name)
+        if want.size == amps.size:
+            from oracle import xeb as oxeb
+            err = {"rel_amp_err": float(np.linalg.norm(amps - want) / np.linalg.norm(want)),
+                   "xeb_err": abs(f_xeb - oxeb.linear_xeb(want, circ.n_qubits))}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_budget > 0:
+        t = oracle_timing(name, args.cpu_budget)
+        if "error" not in t:
+            cpu = {"value": n_slices / t["full_batch_seconds"], "unit": "slices/s", "cores": cores_used(),
+                   "kind": "oracle",
+                   "sample": f"{t['timed_sub_networks']} of {t['sub_networks']} oracle sub-networks of the "
+                             f"full {n_slices}-slice batch ({t['seconds']:.1f} s), extrapolated"}
+        else:
+            cpu = {"value": None, "unit": "slices/s", "cores": cores_used(), "kind": "oracle",
+                   "sample": "oracle failed: " + t["error"][-200:]}
+
+    if rank == 0:
+        line = {
+            "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3",
+                                           "fp16x3": "fp16x3"}[prec],
+            "data": "synthetic",
+            "config": {"workload": f"{name}: {circ.n_qubits}-qubit {cfg['rows']}x{cfg['cols']} grid, "
+                                   f"{cfg['cycles']} cycles, 2^{info['log2_slices']} slices (<=2^"
+                                   f"{cfg['log2_bound']} per slice), {k_open} open qubits",
+                       "precision": prec, "complex_mult": info["complex_mult"],
+                       "slices_per_step": n_slices, "chunks_per_step": n_chunks,
+                       "log2_batch_slices": info["log2_batch_slices"], "l2": "flushed between steps "
+                       "(512 MiB write); intermediates also exceed L2"},
+            "complex_tflops": info["flops_per_chunk"] * n_chunks * world / (ms_max / 1e3) / 1e12,
+            "complex_tflops_per_slice_basis": info["flops_per_slice"] * total_units / (ms_max / 1e3) / 1e12,
+            "plan": {"flops_per_slice": info["flops_per_slice"], "flops_per_chunk": info["flops_per_chunk"],
+                     "bytes_per_chunk": info["bytes_per_chunk"], "n_steps": info["n_steps"],
+                     "log2_max_intermediate": info["log2_max_intermediate"], "arena_gib": info["arena_bytes"] / 2**30,
+                     "plan_seconds": t_plan},
+            "fp32_path": fp32,
+            "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,
+            "error_vs_oracle": err,
+            "xeb": f_xeb,
+            "roofline": roof,
+            "clocks": clk,
+            "e2e": {"value": total_units / e2e_s, "unit": "slices/s", "h2d_bytes_per_step": 8 + 40 * n_chunks,
+                    "d2h_bytes_per_step": (16 << k_open) + 8},
+            "gpu_launches": args.steps * (n_chunks * info["n_kernel_launches_per_chunk"] + 1),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,6 +178,13 @@ tn_status tn_contract_slices(tn_plan_t* plan, uint64_t slice_first, uint64_t sli
                              const uint64_t* open_bitstrings, int32_t n_batches,
                              double* out_amplitudes, void* stream);
 
+/* Device time of every step's kernel: after the plan's device state exists
+ * (one tn_contract_slices call), launches each step's GEMM `reps` times on
+ * `stream` between CUDA events, on the arena contents of the last chunk, and
+ * writes the mean milliseconds per launch into ms_out[n_steps] (host array).
+ * Used for plan reports and roofline measurements; synchronises `stream`. */
+tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, void* stream);
+
 /* Wait for the plan's work on `stream` and return its sticky device error, if any. */
 tn_status tn_plan_sync(tn_plan_t* plan, void* stream);
 

@@ -76,12 +76,12 @@ k_cgemm_simt(const GemmArgs g) {
 
   const int nkc = 1 << (g.nk - g.tk);
   for (int inst = blockIdx.z; inst < g.n_inst; inst += gridDim.z) {
-    const float2* A = g.A + (int64_t)pext_u32((uint32_t)inst, g.a_bsel) * g.a_size +
+    const float2* A = g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) +
                       deposit_hi(blockIdx.x, g.a_mpos, g.tm, g.nm);
-    const float2* B = g.B + (int64_t)pext_u32((uint32_t)inst, g.b_bsel) * g.b_size +
+    const float2* B = g.B + inst_offset(inst, g.b_istride, g.b_bpos, g.nb) +
                       deposit_hi(blockIdx.y, g.b_npos, g.tn, g.nn);
-    float2* C = g.C + (int64_t)inst * g.c_size + deposit_hi(blockIdx.x, g.c_mpos, g.tm, g.nm) +
-                deposit_hi(blockIdx.y, g.c_npos, g.tn, g.nn);
+    float2* C = g.C + inst_offset(inst, g.c_istride, g.c_bpos, g.nb) +
+                deposit_hi(blockIdx.x, g.c_mpos, g.tm, g.nm) + deposit_hi(blockIdx.y, g.c_npos, g.tn, g.nn);
     float2 acc[RM][RN];
 #pragma unroll
     for (int i = 0; i < RM; ++i)

@@ -12,6 +12,7 @@
 
 #include "k_misc.cuh"
 #include "k_simt.cuh"
+#include "k_tc.cuh"
 #include "kernels_common.cuh"
 #include "tn_internal.h"
 
@@ -28,13 +29,14 @@ enum KernelId {
   K_SIMT_64x64 = 0,   // TM 64, TN 64, TK 8
   K_SIMT_128x16 = 1,  // TM 128, TN 16, TK 16
   K_SIMT_256x4 = 2,   // TM 256, TN 4, TK 16
-  K_TC = 3,           // tcgen05 (tile 128 x TN, see k_tc.cuh)
+  K_TC_TF32 = 3,      // tcgen05 kind::tf32, tile 128 x (<=128 complex), k chunk 16
+  K_TC_BF16X3 = 4,    // tcgen05 kind::f16 bf16 hi/lo split
   K_COUNT
 };
 struct KernelCfg {
   int tm, tn, tk;  // log2 tile extents
 };
-static const KernelCfg kCfg[K_COUNT] = {{6, 6, 3}, {7, 4, 4}, {8, 2, 4}, {7, 5, 5}};
+static const KernelCfg kCfg[K_COUNT] = {{6, 6, 3}, {7, 4, 4}, {8, 2, 4}, {7, 7, 4}, {7, 7, 4}};
 
 static int pick_simt(const StepDesc& d) {
   if (d.nn >= 5 && d.nm >= 5) return K_SIMT_64x64;
@@ -42,23 +44,36 @@ static int pick_simt(const StepDesc& d) {
   return K_SIMT_256x4;
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
 // Tile decode tables: the tile's bits in ascending memory position.
 static GemmArgs make_args(const StepDesc& d, int kid, const float2* A, const float2* B, float2* C,
-                          int32_t n_inst) {
+                          int32_t n_inst, int64_t a_istride = 0, int64_t b_istride = 0,
+                          int64_t c_istride = 0) {
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   g.A = A;
   g.B = B;
   g.C = C;
-  g.a_size = d.a_size;
-  g.b_size = d.b_size;
-  g.c_size = d.c_size;
-  g.a_bsel = d.a_bsel;
-  g.b_bsel = d.b_bsel;
+  g.a_istride = a_istride;
+  g.b_istride = b_istride;
+  g.c_istride = c_istride;
   g.n_inst = n_inst;
+  g.nb = d.nb;
   g.nm = d.nm;
   g.nk = d.nk;
   g.nn = d.nn;
+  std::memcpy(g.a_bpos, d.a_bpos, KMAXB);
+  std::memcpy(g.b_bpos, d.b_bpos, KMAXB);
+  std::memcpy(g.c_bpos, d.c_bpos, KMAXB);
   const KernelCfg& k = kCfg[kid];
   g.tm = std::min(k.tm, d.nm);
   g.tk = std::min(k.tk, d.nk);
@@ -90,7 +105,7 @@ static GemmArgs make_args(const StepDesc& d, int kid, const float2* A, const flo
   return g;
 }
 
-static void launch_gemm(const GemmArgs& g, int kid, cudaStream_t s) {
+static void launch_simt(const GemmArgs& g, int kid, cudaStream_t s) {
   if (g.n_inst <= 0) return;
   const int64_t gx = (int64_t)1 << (g.nm - g.tm);
   const int64_t gy = (int64_t)1 << (g.nn - g.tn);
@@ -111,6 +126,70 @@ static void launch_gemm(const GemmArgs& g, int kid, cudaStream_t s) {
   }
 }
 
+// One step ready to launch: GEMM arguments, tensor-core tiling, B' workspace size.
+struct StepLaunch {
+  int kid = 0;
+  GemmArgs g;
+  TcArgs tc;
+  int64_t ws_bytes = 0;
+  int smem = 0;
+};
+
+static bool is_tc(int kid) { return kid == K_TC_TF32 || kid == K_TC_BF16X3; }
+
+static StepLaunch make_launch(const GemmArgs& g, int kid) {
+  StepLaunch L;
+  L.kid = kid;
+  L.g = g;
+  std::memset(&L.tc, 0, sizeof(L.tc));
+  if (!is_tc(kid)) return L;
+  TcArgs& t = L.tc;
+  t.g = g;
+  t.tnb = g.tn;
+  t.tn_c = std::max(8, 1 << g.tn);
+  t.n_mt = 1 << (g.nm - g.tm);
+  t.n_nt = 1 << (g.nn - g.tn);
+  t.n_kc = 1 << (g.nk - g.tk);
+  t.n_tiles = (int64_t)g.n_inst * t.n_mt * t.n_nt;
+  const int esz = kid == K_TC_TF32 ? 4 : 2, npl = kid == K_TC_TF32 ? 1 : 2;
+  const int b_plane = tc_plane_bytes(2 * t.tn_c, esz);
+  const int a_plane = tc_plane_bytes(TC_M, esz);
+  L.ws_bytes = (int64_t)g.n_inst * t.n_nt * t.n_kc * npl * b_plane;
+  L.smem = std::max(TC_STAGES * npl * (a_plane + b_plane) + 4096, TC_MIN_SMEM);
+  return L;
+}
+
+static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s) {
+  if (!is_tc(L.kid)) {
+    launch_simt(L.g, L.kid, s);
+    return;
+  }
+  TcArgs t = L.tc;
+  t.bimg = ws;
+  t.err = err;
+  if (t.n_tiles <= 0) return;
+  const int64_t prep_total = (int64_t)t.g.n_inst * t.n_nt * t.n_kc * TC_TK * t.tn_c;
+  const int pblocks = (int)std::min<int64_t>((prep_total + 255) / 256, (int64_t)sm_count() * 16);
+  const int grid = (int)std::min<int64_t>(t.n_tiles, sm_count());
+  if (L.kid == K_TC_TF32) {
+    k_tc_prep_b<TC_TF32><<<pblocks, 256, 0, s>>>(t);
+    static bool attr = false;
+    if (!attr) {
+      CK(cudaFuncSetAttribute(k_cgemm_tc<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      attr = true;
+    }
+    k_cgemm_tc<TC_TF32><<<grid, TC_THREADS, L.smem, s>>>(t);
+  } else {
+    k_tc_prep_b<TC_BF16X3><<<pblocks, 256, 0, s>>>(t);
+    static bool attr = false;
+    if (!attr) {
+      CK(cudaFuncSetAttribute(k_cgemm_tc<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      attr = true;
+    }
+    k_cgemm_tc<TC_BF16X3><<<grid, TC_THREADS, L.smem, s>>>(t);
+  }
+}
+
 // ------------------------------------------------------------------ plan device state
 struct DeviceState {
   int device = -1;
@@ -120,15 +199,21 @@ struct DeviceState {
   ChunkParam* params = nullptr;
   size_t params_cap = 0;
   unsigned* counter = nullptr;
-  std::vector<GemmArgs> gemm;
-  std::vector<int> kid;
+  int32_t* err = nullptr;
+  uint8_t* ws = nullptr;
+  std::vector<StepLaunch> launches;
   cudaEvent_t done = nullptr;
   bool have_done = false;
 };
 
-static int pick_kernel(const Plan& p, const StepDesc& d) {
-  if (p.opts.precision == TN_PREC_FP32) return pick_simt(d);
-  return pick_simt(d);  // replaced by the tensor-core selection once available
+// Tensor-core kernels for every step with enough work in the TF32 / BF16X3
+// modes; tiny steps (and the FP32 mode) on the CUDA cores.
+static int pick_kernel(int precision, const StepDesc& d) {
+  if (precision == TN_PREC_FP32) return pick_simt(d);
+  if (precision == TN_PREC_FP16X3) fail(TN_ERR_UNSUPPORTED, "FP16X3 is not built");
+  const int work = d.nm + d.nk + d.nn + d.nb;
+  if (work < 20 || d.nm < 4) return pick_simt(d);
+  return precision == TN_PREC_TF32 ? K_TC_TF32 : K_TC_BF16X3;
 }
 
 static void ensure_device(Plan& p) {
@@ -154,6 +239,8 @@ static void ensure_device(Plan& p) {
   CK(cudaMemcpy(ds->leaf_desc, p.leaves.data(), p.leaves.size() * sizeof(LeafDesc),
                 cudaMemcpyHostToDevice));
   CK(cudaMalloc(&ds->counter, sizeof(unsigned)));
+  CK(cudaMalloc(&ds->err, sizeof(int32_t)));
+  CK(cudaMemset(ds->err, 0, sizeof(int32_t)));
   CK(cudaEventCreateWithFlags(&ds->done, cudaEventDisableTiming));
   // bounds of every operand inside the arena, checked once on the host
   const int64_t ae = p.arena_elems;
@@ -164,14 +251,31 @@ static void ensure_device(Plan& p) {
     if (!in_arena(l.dst_off, (int64_t)1 << l.rank, 1 << __builtin_popcount(l.bmask)))
       fail(TN_ERR_PLAN, "internal: leaf outside the arena");
   for (const StepDesc& d : p.steps) {
-    if (!in_arena(d.a_off, d.a_size, 1 << __builtin_popcount(d.a_bsel)) ||
-        !in_arena(d.b_off, d.b_size, 1 << __builtin_popcount(d.b_bsel)) ||
-        !in_arena(d.c_off, d.c_size, 1 << d.nbc))
-      fail(TN_ERR_PLAN, "internal: step operand outside the arena");
-    const int kid = pick_kernel(p, d);
-    ds->kid.push_back(kid);
-    ds->gemm.push_back(make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off,
-                                 1 << d.nbc));
+    // every bit position must address inside the operand's own extent
+    auto span_ok = [](const int8_t* pos, int n, int64_t elems) {
+      for (int i = 0; i < n; ++i)
+        if (pos[i] < 0 || ((int64_t)1 << pos[i]) >= elems) return false;
+      return true;
+    };
+    const bool ok = in_arena(d.a_off, d.a_elems, 1) && in_arena(d.b_off, d.b_elems, 1) &&
+                    in_arena(d.c_off, d.c_elems, 1) && span_ok(d.a_mpos, d.nm, d.a_elems) &&
+                    span_ok(d.a_kpos, d.nk, d.a_elems) && span_ok(d.b_kpos, d.nk, d.b_elems) &&
+                    span_ok(d.b_npos, d.nn, d.b_elems) && span_ok(d.c_mpos, d.nm, d.c_elems) &&
+                    span_ok(d.c_npos, d.nn, d.c_elems) && span_ok(d.a_bpos, d.nb, d.a_elems) &&
+                    span_ok(d.b_bpos, d.nb, d.b_elems) && span_ok(d.c_bpos, d.nb, d.c_elems) &&
+                    ((int64_t)1 << (d.nm + d.nk + d.nb)) == d.a_elems &&
+                    ((int64_t)1 << (d.nk + d.nn + d.nb)) == d.b_elems &&
+                    ((int64_t)1 << (d.nm + d.nn + d.nb)) == d.c_elems;
+    if (!ok) fail(TN_ERR_PLAN, "internal: step operand outside its extent");
+    const int kid = pick_kernel(p.opts.precision, d);
+    ds->launches.push_back(make_launch(
+        make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off, 1 << d.nb), kid));
+  }
+  int64_t ws = 16;
+  for (const StepLaunch& L : ds->launches) ws = std::max(ws, L.ws_bytes);
+  if (cudaMalloc(&ds->ws, (size_t)ws) != cudaSuccess) {
+    cudaGetLastError();
+    fail(TN_ERR_OOM, "workspace allocation of " + std::to_string(ws) + " bytes failed");
   }
   if (!in_arena(p.root.off, (int64_t)1 << p.root.rank, 1 << __builtin_popcount(p.root.bmask)))
     fail(TN_ERR_PLAN, "internal: root outside the arena");
@@ -189,6 +293,8 @@ void destroy_device_state(Plan* p) {
   cudaFree(ds->leaf_desc);
   cudaFree(ds->params);
   cudaFree(ds->counter);
+  cudaFree(ds->err);
+  cudaFree(ds->ws);
   if (ds->done) cudaEventDestroy(ds->done);
   cudaSetDevice(cur);
   delete ds;
@@ -200,7 +306,7 @@ static void run_chunk(Plan& p, double* out, cudaStream_t s) {
   const int nl = (int)p.leaves.size();
   k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
                                                                  ds.params, ds.counter);
-  for (size_t i = 0; i < p.steps.size(); ++i) launch_gemm(ds.gemm[i], ds.kid[i], s);
+  for (size_t i = 0; i < p.steps.size(); ++i) launch_step(ds.launches[i], ds.ws, ds.err, s);
   const int64_t nout = (int64_t)1 << p.root.rank;
   const int blocks = (int)std::min<int64_t>((nout + 255) / 256, 4096);
   k_root_accumulate<<<blocks, 256, 0, s>>>(ds.arena, p.root, p.log2_batch, out, ds.params, ds.counter);
@@ -277,10 +383,47 @@ extern "C" tn_status tn_contract_slices(tn_plan_t* h, uint64_t first, uint64_t c
   API_END
 }
 
+extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_out, void* stream) {
+  API_BEGIN
+  if (!h || !ms_out) fail(TN_ERR_ARG, "tn_plan_step_times: NULL argument");
+  if (reps < 1) fail(TN_ERR_ARG, "tn_plan_step_times: reps must be >= 1");
+  Plan& p = h->plan;
+  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_step_times: run tn_contract_slices first");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceState& ds = *p.dev;
+  if (ds.have_done) CK(cudaStreamWaitEvent(s, ds.done, 0));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    launch_step(ds.launches[i], ds.ws, ds.err, s);  // warm-up
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) launch_step(ds.launches[i], ds.ws, ds.err, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms_out[i] = (double)ms / reps;
+  }
+  CK(cudaGetLastError());
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  API_END
+}
+
 extern "C" tn_status tn_plan_sync(tn_plan_t* h, void* stream) {
   API_BEGIN
   if (!h) fail(TN_ERR_ARG, "tn_plan_sync: NULL plan");
   CK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (h->plan.dev && h->plan.sticky == TN_OK) {
+    int32_t e = 0;
+    CK(cudaMemcpy(&e, h->plan.dev->err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+      h->plan.sticky = e;
+      h->plan.sticky_msg = "a device kernel reported error " + std::to_string(e) +
+                           " (bounded wait expired or device check failed)";
+    }
+  }
   if (h->plan.sticky != TN_OK) fail(h->plan.sticky, h->plan.sticky_msg);
   API_END
 }
@@ -291,17 +434,27 @@ extern "C" void tn_plan_destroy(tn_plan_t* h) {
   delete h;
 }
 
-// per-device FP64 scratch of the XEB reduction
-static double* xeb_scratch(int dev) {
+// Per-device scratch of the calls that have no plan: the XEB sum, the error
+// word and the B' workspace of tn_contract_pair.
+struct Scratch {
+  double* xeb = nullptr;
+  int32_t* err = nullptr;
+  uint8_t* ws = nullptr;
+  int64_t ws_bytes = 0;
+};
+static Scratch& scratch_for_device() {
   static std::mutex mu;
-  static std::unordered_map<int, double*> m;
+  static std::unordered_map<int, Scratch> m;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
-  auto it = m.find(dev);
-  if (it != m.end()) return it->second;
-  double* p = nullptr;
-  CK(cudaMalloc(&p, sizeof(double)));
-  m[dev] = p;
-  return p;
+  Scratch& s = m[dev];
+  if (!s.xeb) {
+    CK(cudaMalloc(&s.xeb, sizeof(double)));
+    CK(cudaMalloc(&s.err, sizeof(int32_t)));
+    CK(cudaMemset(s.err, 0, sizeof(int32_t)));
+  }
+  return s;
 }
 
 extern "C" tn_status tn_xeb(const double* amps, int64_t count, int32_t n_qubits, double* xeb_out,
@@ -310,9 +463,7 @@ extern "C" tn_status tn_xeb(const double* amps, int64_t count, int32_t n_qubits,
   if (!amps || !xeb_out) fail(TN_ERR_ARG, "tn_xeb: NULL argument");
   if (count < 1) fail(TN_ERR_ARG, "tn_xeb: count must be >= 1");
   if (n_qubits < 0 || n_qubits > 1023) fail(TN_ERR_ARG, "tn_xeb: n_qubits out of range");
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  double* scratch = xeb_scratch(dev);
+  double* scratch = scratch_for_device().xeb;
   cudaStream_t s = (cudaStream_t)stream;
   k_xeb_sum<<<1, 1024, 0, s>>>(reinterpret_cast<const double2*>(amps), count, scratch);
   CK(cudaGetLastError());
@@ -391,17 +542,23 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
     d.b_npos[i] = (int8_t)pos(B, nw[i]);
     d.c_npos[i] = (int8_t)pos(Cw, nw[i]);
   }
-  d.a_size = (int64_t)1 << ar;
-  d.b_size = (int64_t)1 << br;
-  d.c_size = (int64_t)1 << cr;
-  d.a_bsel = d.b_bsel = 0xffffffffu;
-  Plan tmp;
-  tmp.opts.precision = precision;
-  tmp.opts.complex_mult = cmult;
-  const int kid = pick_kernel(tmp, d);
+  d.a_elems = (int64_t)1 << ar;
+  d.b_elems = (int64_t)1 << br;
+  d.c_elems = (int64_t)1 << cr;
+  d.nb = 0;
+  const int kid = pick_kernel(precision, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
-                         reinterpret_cast<float2*>(c), (int32_t)batch);
-  launch_gemm(g, kid, (cudaStream_t)stream);
+                         reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
+  StepLaunch L = make_launch(g, kid);
+  Scratch& sc = scratch_for_device();
+  if (L.ws_bytes > sc.ws_bytes) {
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (sc.ws) CK(cudaFree(sc.ws));
+    sc.ws = nullptr;
+    CK(cudaMalloc(&sc.ws, (size_t)L.ws_bytes));
+    sc.ws_bytes = L.ws_bytes;
+  }
+  launch_step(L, sc.ws, sc.err, (cudaStream_t)stream);
   CK(cudaGetLastError());
   API_END
 }

@@ -50,21 +50,25 @@ struct Network {
 };
 
 // ------------------------------------------------------------------ plan
-constexpr int MAXR = 40;   // bits per tensor index tracked by a step descriptor
+constexpr int MAXR = 48;   // bits per tensor index tracked by a step descriptor
 constexpr int MAXFIX = 24; // fixed (sliced or closed-output) wires per leaf
 
 // One pairwise contraction C[m, n] = sum_k A[m, k] B[k, n] over a batch of
-// instances (SI, Eq. (2)).  Element offsets of an operand are gathered from its
-// bit positions: the m-th row of A starts at sum_i bit_i(m) 2^{a_mpos[i]} etc.
+// instances (SI, Eq. (2)).  Every index is a bit of an element offset: the
+// m-th row of A starts at sum_i bit_i(m) 2^{a_mpos[i]} etc.  Positions at or
+// above an operand's rank address its batch instances (slices of the chunk);
+// batch bits carried by only one operand are folded into that operand's m or n
+// bits, so only bits shared by A and B remain true batch bits (nb).
+constexpr int MAXB = 16;
 struct StepDesc {
-  int64_t a_off, b_off, c_off;     // arena offsets in complex64 elements
-  int64_t a_size, b_size, c_size;  // elements per batch instance (2^rank)
-  int32_t nm, nk, nn;              // log2 of M, K, N
-  int32_t nbc;                     // batch bits of C (instances = 2^nbc)
-  uint32_t a_bsel, b_bsel;         // which of C's batch bits A / B carry
-  int32_t kernel;                  // kernel variant chosen by the planner
-  int32_t pad_;
+  int64_t a_off, b_off, c_off;        // arena offsets in complex64 elements
+  int64_t a_elems, b_elems, c_elems;  // elements of each operand over all its instances
+  int32_t nm, nk, nn, nb;             // log2 of M, K, N and of the instance count
+  int32_t nm_wires, nn_wires;         // m / n bits that are wires (the rest are batch bits)
+  int32_t rank_a, rank_b, rank_c;     // per-slice ranks
+  int32_t kernel;                     // kernel variant chosen by the executor
   int8_t a_mpos[MAXR], a_kpos[MAXR], b_kpos[MAXR], b_npos[MAXR], c_mpos[MAXR], c_npos[MAXR];
+  int8_t a_bpos[MAXB], b_bpos[MAXB], c_bpos[MAXB];
 };
 
 // One leaf tensor materialised per chunk by the leaf-select kernel.

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <bitset>
 #include <cmath>
+#include <array>
 #include <cstring>
 #include <functional>
 #include <limits>
@@ -760,41 +761,63 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
         (std::find(B.wires.begin(), B.wires.end(), w) != B.wires.end() ? kw : mw).push_back(w);
       for (int w : B.wires)
         if (std::find(A.wires.begin(), A.wires.end(), w) == A.wires.end()) nw.push_back(w);
-      if ((int)(mw.size() + kw.size()) > MAXR || (int)(kw.size() + nw.size()) > MAXR ||
-          (int)(mw.size() + nw.size()) > MAXR)
-        fail(TN_ERR_UNSUPPORTED, "a tensor exceeds the kernels' rank limit");
       C.wires = mw;
       C.wires.insert(C.wires.end(), nw.begin(), nw.end());
       C.bmask = A.bmask | B.bmask;
       auto pos_in = [](const std::vector<int>& ws, int w) {
         return (int)(std::find(ws.begin(), ws.end(), w) - ws.begin());
       };
-      d.nm = (int)mw.size();
+      // storage position of batch bit j in a node: rank + its index among the node's batch bits
+      auto bpos = [](const NodeInfo& x, int j) {
+        return (int)x.wires.size() + __builtin_popcount(x.bmask & ((1u << j) - 1u));
+      };
+      const int ra = (int)A.wires.size(), rb = (int)B.wires.size(), rc = (int)C.wires.size();
+      std::vector<std::pair<int, int>> mb, nb;  // (pos in operand, pos in C)
+      std::vector<std::array<int, 3>> bb;       // shared batch bits (pos A, pos B, pos C)
+      for (int w : mw) mb.push_back({pos_in(A.wires, w), pos_in(C.wires, w)});
+      for (int w : nw) nb.push_back({pos_in(B.wires, w), pos_in(C.wires, w)});
+      for (int j = 0; j < 32; ++j) {
+        const bool ia = (A.bmask >> j) & 1, ib = (B.bmask >> j) & 1;
+        if (ia && ib) bb.push_back({bpos(A, j), bpos(B, j), bpos(C, j)});
+        else if (ia) mb.push_back({bpos(A, j), bpos(C, j)});
+        else if (ib) nb.push_back({bpos(B, j), bpos(C, j)});
+      }
+      if ((int)(mb.size() + kw.size()) > MAXR || (int)(kw.size() + nb.size()) > MAXR ||
+          (int)(mb.size() + nb.size()) > MAXR || (int)bb.size() > MAXB)
+        fail(TN_ERR_UNSUPPORTED, "a tensor exceeds the kernels' rank limit");
+      d.nm = (int)mb.size();
       d.nk = (int)kw.size();
-      d.nn = (int)nw.size();
-      for (int i = 0; i < d.nm; ++i) d.a_mpos[i] = (int8_t)pos_in(A.wires, mw[i]);
+      d.nn = (int)nb.size();
+      d.nb = (int)bb.size();
+      d.nm_wires = (int)mw.size();
+      d.nn_wires = (int)nw.size();
+      d.rank_a = ra;
+      d.rank_b = rb;
+      d.rank_c = rc;
+      for (int i = 0; i < d.nm; ++i) {
+        d.a_mpos[i] = (int8_t)mb[i].first;
+        d.c_mpos[i] = (int8_t)mb[i].second;
+      }
       for (int i = 0; i < d.nk; ++i) {
         d.a_kpos[i] = (int8_t)pos_in(A.wires, kw[i]);
         d.b_kpos[i] = (int8_t)pos_in(B.wires, kw[i]);
       }
-      for (int i = 0; i < d.nn; ++i) d.b_npos[i] = (int8_t)pos_in(B.wires, nw[i]);
-      for (int i = 0; i < d.nm; ++i) d.c_mpos[i] = (int8_t)i;
-      for (int i = 0; i < d.nn; ++i) d.c_npos[i] = (int8_t)(d.nm + i);
-      d.nbc = __builtin_popcount(C.bmask);
-      int t = 0;
-      for (int j = 0; j < 32; ++j)
-        if ((C.bmask >> j) & 1) {
-          if ((A.bmask >> j) & 1) d.a_bsel |= 1u << t;
-          if ((B.bmask >> j) & 1) d.b_bsel |= 1u << t;
-          ++t;
-        }
-      d.a_size = (int64_t)1 << A.wires.size();
-      d.b_size = (int64_t)1 << B.wires.size();
-      d.c_size = (int64_t)1 << C.wires.size();
+      for (int i = 0; i < d.nn; ++i) {
+        d.b_npos[i] = (int8_t)nb[i].first;
+        d.c_npos[i] = (int8_t)nb[i].second;
+      }
+      for (int i = 0; i < d.nb; ++i) {
+        d.a_bpos[i] = (int8_t)bb[i][0];
+        d.b_bpos[i] = (int8_t)bb[i][1];
+        d.c_bpos[i] = (int8_t)bb[i][2];
+      }
+      d.a_elems = elems_of(A);
+      d.b_elems = elems_of(B);
       d.a_off = A.off;
       d.b_off = B.off;
       C.off = alloc(elems_of(C));
       d.c_off = C.off;
+      d.c_elems = elems_of(C);
       peak = std::max(peak, end);
       d.kernel = -1;
       release(A.off, elems_of(A));
@@ -874,17 +897,11 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   PlanStats& st = P->stats;
   for (int i = 0; i < L; ++i) st.log2_max = std::max(st.log2_max, (int)info[i].wires.size());
   for (const StepDesc& d : P->steps) {
-    const double macs = pow2(d.nm + d.nk + d.nn);
-    const double el = (double)(d.a_size + d.b_size + d.c_size);
-    st.flops_slice += 8.0 * macs;
-    st.bytes_slice += 8.0 * el;
-    st.flops_chunk += 8.0 * macs * pow2(d.nbc);
-    double elc = 0;
-    elc += (double)d.c_size * pow2(d.nbc);
-    elc += (double)d.a_size * pow2(__builtin_popcount(d.a_bsel));
-    elc += (double)d.b_size * pow2(__builtin_popcount(d.b_bsel));
-    st.bytes_chunk += 8.0 * elc;
-    st.log2_max = std::max(st.log2_max, d.nm + d.nn);
+    st.flops_slice += 8.0 * pow2(d.nm_wires + d.nk + d.nn_wires);
+    st.bytes_slice += 8.0 * (pow2(d.rank_a) + pow2(d.rank_b) + pow2(d.rank_c));
+    st.flops_chunk += 8.0 * pow2(d.nm + d.nk + d.nn + d.nb);
+    st.bytes_chunk += 8.0 * (double)(d.a_elems + d.b_elems + d.c_elems);
+    st.log2_max = std::max(st.log2_max, d.rank_c);
     st.khist[std::min(d.nk, 39)]++;
   }
   guard.release();
@@ -998,6 +1015,6 @@ extern "C" tn_status tn_plan_step_shape(const tn_plan_t* h, int32_t step, int32_
   *lm = d.nm;
   *lk = d.nk;
   *ln = d.nn;
-  *lb = d.nbc;
+  *lb = d.nb;
   return TN_OK;
 }

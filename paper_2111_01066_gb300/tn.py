@@ -80,6 +80,8 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p]),
     "tn_plan_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tn_plan_step_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p]),
     "tn_plan_destroy": (None, [ctypes.c_void_p]),
     "tn_xeb": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -223,6 +225,13 @@ class Plan:
         bs = (ctypes.c_uint64 * len(bitstrings))(*[int(b) for b in bitstrings])
         _check(load().tn_contract_slices(self.handle, slice_first, slice_count, bs, len(bitstrings),
                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+
+    def step_times(self, reps: int = 3, stream=None) -> List[float]:
+        """Mean device milliseconds per launch of every step's kernel."""
+        n = self.info()["n_steps"]
+        arr = (ctypes.c_double * max(1, n))()
+        _check(load().tn_plan_step_times(self.handle, reps, arr, _stream_handle(stream)))
+        return list(arr)[:n]
 
     def sync(self, stream=None) -> None:
         _check(load().tn_plan_sync(self.handle, _stream_handle(stream)))
