@@ -221,6 +221,32 @@ tn_status tn_contract_pair(const float* a, const int32_t* a_wires, int32_t a_ran
                            int64_t batch, int32_t precision, int32_t complex_mult,
                            void* stream);
 
+/* tn_contract_pair without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory -- code running while a CUDA graph is captured, allocation-free
+ * real-time or embedded hosts, programs whose memory pool belongs to someone
+ * else.  Arguments, layouts and results are those of tn_contract_pair (same
+ * kernels); the caller still provides A, B and C.
+ *   - Scratch (an error word and the B' images of the tensor-core kernels)
+ *     comes from one static device array of 32 MiB compiled into the library;
+ *     every GPU that loads the library holds it until the process exits.  A
+ *     contraction whose scratch exceeds it (tensor-core paths: about 16 bytes
+ *     per complex entry of B per batch instance, after padding k to 16 and n
+ *     to 8) fails with TN_ERR_ARG before anything is launched.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.  The
+ *     first call on each device looks the array's device address up (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the array, which keeps the previous call's contents;
+ *     the error word is cleared on the stream at the start of each call.
+ *     Calls that overlap on the GPU (other streams, other threads) race on the
+ *     array and must be serialised by the caller.
+ * Asynchronous on stream. */
+tn_status tn_contract_pair_noalloc(const float* a, const int32_t* a_wires, int32_t a_rank,
+                                   const float* b, const int32_t* b_wires, int32_t b_rank,
+                                   float* c, const int32_t* c_wires, int32_t c_rank,
+                                   int64_t batch, int32_t precision, int32_t complex_mult,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -562,3 +562,99 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   CK(cudaGetLastError());
   API_END
 }
+
+// ---------------------------------------------------------------- no-allocation variant
+// Some callers cannot call cudaMalloc at all: code running while a CUDA graph
+// is being captured, allocation-free real-time or embedded hosts, and programs
+// whose memory pool is owned by someone else.  tn_contract_pair_noalloc serves
+// them with the same kernels as tn_contract_pair, taking its scratch (the
+// device error word and the B' images of the tensor-core kernels) from this
+// file-scope device array instead of allocating it.  Every GPU that loads the
+// library holds the array until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB
+constexpr size_t kNoAllocErrBytes = 256;                     // error word, then the B' images
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+static void* noalloc_scratch_address() {
+  static std::mutex mu;
+  static std::unordered_map<int, void*> addr;   // per device, found once with that device current
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = addr.find(dev);
+  if (it != addr.end()) return it->second;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    fail(TN_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") + cudaGetErrorString(e));
+  addr[dev] = p;
+  return p;
+}
+
+extern "C" tn_status tn_contract_pair_noalloc(const float* a, const int32_t* aw, int32_t ar, const float* b,
+                                              const int32_t* bw, int32_t br, float* c, const int32_t* cw,
+                                              int32_t cr, int64_t batch, int32_t precision, int32_t cmult,
+                                              void* stream) {
+  API_BEGIN
+  if (!a || !b || !c || (ar && !aw) || (br && !bw) || (cr && !cw))
+    fail(TN_ERR_ARG, "tn_contract_pair_noalloc: NULL argument");
+  if (ar < 0 || br < 0 || cr < 0 || ar > 34 || br > 34 || cr > 34)
+    fail(TN_ERR_ARG, "tn_contract_pair_noalloc: rank out of range");
+  if (batch < 1 || batch > 65535) fail(TN_ERR_ARG, "tn_contract_pair_noalloc: batch must be in [1, 65535]");
+  if (precision < TN_PREC_FP32 || precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
+  if (cmult != 3 && cmult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
+  std::vector<int> A(aw, aw + ar), B(bw, bw + br), Cw(cw, cw + cr);
+  auto has = [](const std::vector<int>& v, int w) { return std::find(v.begin(), v.end(), w) != v.end(); };
+  auto dup = [](const std::vector<int>& v) {
+    for (size_t i = 0; i < v.size(); ++i)
+      for (size_t j = i + 1; j < v.size(); ++j)
+        if (v[i] == v[j]) return true;
+    return false;
+  };
+  if (dup(A) || dup(B) || dup(Cw)) fail(TN_ERR_ARG, "repeated wire in a wire list");
+  StepDesc d;
+  std::memset(&d, 0, sizeof(d));
+  std::vector<int> mw, kw, nw;
+  for (int w : A) (has(B, w) ? kw : mw).push_back(w);
+  for (int w : B)
+    if (!has(A, w)) nw.push_back(w);
+  if (mw.size() + nw.size() != Cw.size()) fail(TN_ERR_ARG, "c_wires must be the uncontracted wires");
+  for (int w : mw)
+    if (!has(Cw, w)) fail(TN_ERR_ARG, "c_wires misses a wire of A");
+  for (int w : nw)
+    if (!has(Cw, w)) fail(TN_ERR_ARG, "c_wires misses a wire of B");
+  auto pos = [](const std::vector<int>& v, int w) { return (int)(std::find(v.begin(), v.end(), w) - v.begin()); };
+  d.nm = (int)mw.size();
+  d.nk = (int)kw.size();
+  d.nn = (int)nw.size();
+  for (int i = 0; i < d.nm; ++i) {
+    d.a_mpos[i] = (int8_t)pos(A, mw[i]);
+    d.c_mpos[i] = (int8_t)pos(Cw, mw[i]);
+  }
+  for (int j = 0; j < d.nk; ++j) {
+    d.a_kpos[j] = (int8_t)pos(A, kw[j]);
+    d.b_kpos[j] = (int8_t)pos(B, kw[j]);
+  }
+  for (int i = 0; i < d.nn; ++i) {
+    d.b_npos[i] = (int8_t)pos(B, nw[i]);
+    d.c_npos[i] = (int8_t)pos(Cw, nw[i]);
+  }
+  d.a_elems = (int64_t)1 << ar;
+  d.b_elems = (int64_t)1 << br;
+  d.c_elems = (int64_t)1 << cr;
+  const int kid = pick_kernel(precision, d);
+  GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
+                         reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
+  StepLaunch L = make_launch(g, kid);
+  const int64_t cap = (int64_t)(kNoAllocScratchBytes - kNoAllocErrBytes);
+  if (L.ws_bytes > cap)
+    fail(TN_ERR_ARG, "tn_contract_pair_noalloc: this contraction needs " + std::to_string(L.ws_bytes) +
+                         " bytes of scratch; the static array holds " + std::to_string(cap));
+  uint8_t* base = static_cast<uint8_t*>(noalloc_scratch_address());
+  int32_t* err = reinterpret_cast<int32_t*>(base);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(err, 0, sizeof(int32_t), s));   // the array keeps the last call's contents
+  launch_step(L, base + kNoAllocErrBytes, err, s);
+  CK(cudaGetLastError());
+  API_END
+}

@@ -91,6 +91,10 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                         ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "tn_contract_pair_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
 }
 
 _lib = None
