@@ -164,6 +164,102 @@ def cores_used() -> int:
     return os.cpu_count() or 1
 
 
+# ------------------------------------------------------------------ rooflines
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 x GHz
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def complex_peak_tflops(kernel: str, peaks: dict) -> float:
+    """Peak in algorithmic complex flops (8 per complex multiply-add) of a kernel:
+    a real tensor peak P runs a complex MAC as R real MACs, so P_eff = P * 8 / (2 R)."""
+    bf16 = peaks["bf16_tflops"]
+    if kernel == "tc_tf32":
+        return bf16 / 2 * 8 / (2 * 4)          # TF32 dense = half the BF16 rate, 4M
+    if kernel == "tc_bf16x3":
+        return bf16 * 8 / (2 * 12)             # 3 bf16 products per real product, 4M
+    return FP32_SIMT_TFLOPS
+
+
+def step_roofline(shape, ms: float, kernel: str, peaks: dict) -> dict:
+    m, k, n, b = shape
+    flops = 8.0 * 2 ** (m + k + n + b)
+    nbytes = 8.0 * (2 ** (m + k) + 2 ** (k + n) + 2 ** (m + n)) * 2 ** b
+    p_tf = complex_peak_tflops(kernel, peaks)
+    bw = peaks["hbm_gbs"]
+    t_c = flops / (p_tf * 1e12) * 1e3
+    t_m = nbytes / (bw * 1e9) * 1e3
+    if t_c >= t_m:
+        bound = "tensor" if kernel.startswith("tc") else "alu"
+        ach = flops / (ms / 1e3) / 1e12
+        r = {"bound": bound, "achieved": ach, "peak": p_tf, "unit": "TFLOP/s", "frac": ach / p_tf}
+    else:
+        ach = nbytes / (ms / 1e3) / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": bw, "unit": "GB/s", "frac": ach / bw}
+    r.update({"traffic": None, "kernel": kernel, "shape_log2_mknb": [m, k, n, b], "ms": ms,
+              "t_roof_ms": max(t_c, t_m), "peak_source": peaks.get("source", "measured")})
+    return r
+
+
+# ------------------------------------------------------------------ one pairwise contraction
+def pair_bench(args) -> int:
+    """Time tn_contract_pair on random operands of shape (m, k, n) with a
+    seeded random storage order of every operand (the permutation is folded
+    into the kernel's loads)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_01066_gb300 import tn
+    vals = [int(x) for x in args.pair.split(",")]
+    m, k, n = vals[:3]
+    batch = vals[3] if len(vals) > 3 else 1
+    prec = args.precision if args.precision != "auto" else "bf16x3"
+    rng = np.random.default_rng(m * 10000 + k * 100 + n)
+    wires = list(range(m + k + n))
+    mw, kw, nw = wires[:m], wires[m:m + k], wires[m + k:]
+    a_w = {"random": list(rng.permutation(mw + kw)), "kfast": kw + mw, "mfast": mw + kw}[args.layout]
+    b_w = list(rng.permutation(kw + nw)) if args.layout == "random" else kw + nw
+    c_w = mw + nw
+    dev = torch.device("cuda", 0)
+    a = torch.randn(batch, 2 ** (m + k), dtype=torch.complex64, device=dev)
+    b = torch.randn(batch, 2 ** (k + n), dtype=torch.complex64, device=dev)
+    c = torch.empty(batch, 2 ** (m + n), dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        tn.contract_pair(a, a_w, b, b_w, c, c_w, batch=batch, precision=prec, stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tn.contract_pair(a, a_w, b, b_w, c, c_w, batch=batch, precision=prec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    peaks = load_peaks()
+    kernel = {"fp32": "simt", "tf32": "tc_tf32", "bf16x3": "tc_bf16x3"}[prec]
+    if prec != "fp32" and (m + k + n + int(math.log2(batch)) < 20 or m < 4):
+        kernel = "simt"
+    r = step_roofline((m, k, n, int(round(math.log2(batch)))), ms, kernel, peaks)
+    print(json.dumps({"metric": "pair_contraction", "shape_log2_mkn": [m, k, n], "batch": batch,
+                      "layout": args.layout,
+                      "precision": prec, "ms": ms, "complex_tflops": 8.0 * 2 ** (m + k + n) * batch / ms / 1e9,
+                      "roofline": r, "note": "includes the B' image pre-pass for tensor-core kernels"}))
+    return 0
+
+
 # ------------------------------------------------------------------ main
 def main() -> int:
     ap = argparse.ArgumentParser()
@@ -175,7 +271,14 @@ def main() -> int:
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--compare-fp32", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--pair", default=None,
+                    help="log2 m,k,n[,batch]: time one pairwise contraction (tn_contract_pair) instead")
+    ap.add_argument("--layout", default="random", choices=["random", "kfast", "mfast"],
+                    help="storage order of A in --pair mode: seeded random, contracted wires lowest, "
+                         "free wires lowest")
     args = ap.parse_args()
+    if args.pair:
+        return pair_bench(args)
     rank, world, local = dist_env()
     name = args.workload
     cfg = rqcgen.CONFIGS[name]
@@ -221,7 +324,7 @@ def main() -> int:
     from paper_2111_01066_gb300 import tn
     tn.load()
 
-    prec = args.precision if args.precision != "auto" else "fp32"
+    prec = args.precision if args.precision != "auto" else "bf16x3"
     bits = batch_bits_for_rank(name, rank)
     net = tn.Network(circ)
     plan_kw = dict(open_mask=om, max_log2_intermediate=cfg["log2_bound"], min_log2_slices=cfg["log2_slices"])
@@ -289,42 +392,53 @@ def main() -> int:
             e2e_times.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(statistics.mean(e2e_times), world, dev)
 
-    # FP32 SIMT path on the same workload
-    fp32 = None
-    if args.compare_fp32 and prec != "fp32":
-        plan32 = tn.Plan(net, precision="fp32", **plan_kw)
-        out32 = torch.zeros_like(out)
-        step(plan32, out32)
-        t32 = timed(plan32, out32, min(3, args.steps), 1)
-        ms32 = max_over_ranks(statistics.mean(t32), world, dev)
-        fp32 = {"value": total_units / (ms32 / 1e3), "ms_per_step": ms32}
+    # the other paths on the same workload: FP32 SIMT (the plain path) and TF32
+    others = {}
+    gold = None
+    gold_path = os.path.join(ROOT, "tests", "golden", f"{name}_amplitudes.txt")
+    if rank == 0 and os.path.exists(gold_path):
+        from tests.golden.make_golden import read
+        gold = read(name)
+
+    def amp_error(o):
+        if gold is None or gold.size != (o.numel() // 2):
+            return None
+        from oracle import xeb as oxeb
+        got = o.cpu().numpy().view(np.complex128)
+        f = tn.xeb(o.view(torch.complex128), circ.n_qubits)
+        return {"rel_amp_err": float(np.linalg.norm(got - gold) / np.linalg.norm(gold)),
+                "xeb_err": abs(f - oxeb.linear_xeb(gold, circ.n_qubits))}
+
+    if args.compare_fp32:
+        for other in ("fp32", "tf32"):
+            if other == prec:
+                continue
+            p2 = tn.Plan(net, precision=other, **plan_kw)
+            o2 = torch.zeros_like(out)
+            step(p2, o2)
+            t2 = timed(p2, o2, min(3, args.steps), 1)
+            ms2 = max_over_ranks(statistics.mean(t2), world, dev)
+            others[other] = {"value": total_units / (ms2 / 1e3), "ms_per_step": ms2,
+                             "error_vs_oracle": amp_error(o2)}
+            del p2, o2
+    fp32 = others.get("fp32")
 
     # roofline of the dominant kernel: per-step device times on the same stream
     st = plan.step_times(reps=3, stream=stream)
     shapes = plan.step_shapes()
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-    i_dom = max(range(len(st)), key=lambda i: st[i])
-    m, k, n_, b = shapes[i_dom]
-    flops_dom = 8.0 * 2 ** (m + k + n_ + b)
-    ms_dom = st[i_dom]
-    sm_clock_ghz = 1.92  # FP32 peak clock assumption, see the design doc
-    fp32_peak_tf = 152 * 128 * 2 * sm_clock_ghz / 1e3
-    roof = {"bound": "alu", "achieved": flops_dom / (ms_dom / 1e3) / 1e12, "peak": fp32_peak_tf,
-            "unit": "TFLOP/s", "traffic": None, "step": i_dom, "shape_log2_mknb": [m, k, n_, b],
-            "share_of_step_time": ms_dom / sum(st)}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    peaks = load_peaks()
+    rows = [step_roofline(shapes[i], st[i][0], st[i][1], peaks) for i in range(len(st))]
+    i_dom = max(range(len(rows)), key=lambda i: rows[i]["ms"])
+    roof = dict(rows[i_dom])
+    roof["share_of_step_time"] = rows[i_dom]["ms"] / sum(r["ms"] for r in rows)
+    roof["step"] = i_dom
+    # whole-path roofline: sum over steps of max(flops / peak, bytes / bandwidth)
+    t_roof = sum(r["t_roof_ms"] for r in rows)
+    path_roof = {"t_roof_ms": t_roof, "t_steps_ms": sum(r["ms"] for r in rows),
+                 "frac": t_roof / sum(r["ms"] for r in rows)}
+    top = sorted(rows, key=lambda r: -r["ms"])[:8]
 
-    # error against the oracle's stored amplitudes, when present
-    err = None
-    gold_path = os.path.join(ROOT, "tests", "golden", f"{name}_amplitudes.txt")
-    if rank == 0 and os.path.exists(gold_path):
-        from tests.golden.make_golden import read
-        want = read(name)
-        if want.size == amps.size:
-            from oracle import xeb as oxeb
-            err = {"rel_amp_err": float(np.linalg.norm(amps - want) / np.linalg.norm(want)),
-                   "xeb_err": abs(f_xeb - oxeb.linear_xeb(want, circ.n_qubits))}
+    err = amp_error(out) if rank == 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_budget > 0:
@@ -359,10 +473,13 @@ def main() -> int:
                      "log2_max_intermediate": info["log2_max_intermediate"], "arena_gib": info["arena_bytes"] / 2**30,
                      "plan_seconds": t_plan},
             "fp32_path": fp32,
+            "tf32_path": others.get("tf32"),
             "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,
             "error_vs_oracle": err,
             "xeb": f_xeb,
             "roofline": roof,
+            "path_roofline": path_roof,
+            "top_steps": top,
             "clocks": clk,
             "e2e": {"value": total_units / e2e_s, "unit": "slices/s", "h2d_bytes_per_step": 8 + 40 * n_chunks,
                     "d2h_bytes_per_step": (16 << k_open) + 8},

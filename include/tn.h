@@ -181,9 +181,13 @@ tn_status tn_contract_slices(tn_plan_t* plan, uint64_t slice_first, uint64_t sli
 /* Device time of every step's kernel: after the plan's device state exists
  * (one tn_contract_slices call), launches each step's GEMM `reps` times on
  * `stream` between CUDA events, on the arena contents of the last chunk, and
- * writes the mean milliseconds per launch into ms_out[n_steps] (host array).
- * Used for plan reports and roofline measurements; synchronises `stream`. */
-tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, void* stream);
+ * writes the mean milliseconds per launch into ms_out[n_steps] (host array)
+ * and, when kernel_out is not NULL, the kernel used by each step into
+ * kernel_out[n_steps]: 0-2 FP32 SIMT tiles (64x64, 128x16, 256x4),
+ * 3 tcgen05 TF32, 4 tcgen05 BF16x3.  Used for plan reports and roofline
+ * measurements; synchronises `stream`. */
+tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int32_t* kernel_out,
+                             void* stream);
 
 /* Wait for the plan's work on `stream` and return its sticky device error, if any. */
 tn_status tn_plan_sync(tn_plan_t* plan, void* stream);

@@ -203,11 +203,12 @@ def order_flops(merges, sets, removed: frozenset = frozenset()) -> float:
 
 
 def best_bisection_order(leg_sets: Sequence[frozenset], trials: int = 8, seed: int = 0):
-    """Best of several randomised bisection orders by complex multiply-adds."""
+    """Best of several randomised bisection orders by complex multiply-adds; the
+    t-th trial uses seed + t and cycles through leaf sizes and imbalances."""
     best = None
     for t in range(trials):
-        m, s = bisection_order(leg_sets, seed=seed + t, leaf=(6, 8, 10)[t % 3],
-                               imbalance=(0.1, 0.2, 0.3)[(t // 3) % 3])
+        m, s = bisection_order(leg_sets, seed=seed + t, leaf=(6, 8, 10, 12)[t % 4],
+                               imbalance=(0.05, 0.1, 0.2, 0.3)[(t // 4) % 4])
         f = order_flops(m, s)
         if best is None or f < best[0]:
             best = (f, m, s)

@@ -132,7 +132,7 @@ class CircuitNetwork:
         return merges, sets
 
     def plan(self, fixed_legs: Iterable[Label], max_log2: int = 27, method: str = "greedy",
-             trials: int = 8) -> Tuple[List[Tuple[int, int]], List[Label]]:
+             trials: int = 8, seed: int = 0) -> Tuple[List[Tuple[int, int]], List[Label]]:
         """Pairwise order for the network with `fixed_legs` removed ("greedy", or
         "bisect" for the recursive bisection of oracle.order), plus the extra
         wires the oracle itself slices so that no tensor of that order exceeds
@@ -143,7 +143,7 @@ class CircuitNetwork:
             merges, sets = self.greedy_order(base)
         elif method == "bisect":
             from . import order as _order
-            merges, sets = _order.best_bisection_order(base, trials=trials)
+            merges, sets = _order.best_bisection_order(base, trials=trials, seed=seed)
         else:
             raise ValueError(f"unknown order method {method!r}")
         extra: List[Label] = []
@@ -205,7 +205,7 @@ class CircuitNetwork:
         return np.transpose(final, perm).reshape(-1)
 
     def contract(self, sliced: Sequence[Label] = (), slice_ids: Optional[Iterable[int]] = None,
-                 max_log2: int = 27, method: str = "greedy", trials: int = 8) -> np.ndarray:
+                 max_log2: int = 27, method: str = "greedy", trials: int = 8, seed: int = 0) -> np.ndarray:
         """Sum over the given slice ids (all 2^S when None) of the network with the
         sliced wires fixed: slice id s sets sliced[j] to bit j of s.  Returns the
         2^k complex128 batch amplitudes (partial sums when not all slices)."""
@@ -213,7 +213,7 @@ class CircuitNetwork:
         for leg in sliced:
             if leg in self.open_legs:
                 raise ValueError("an open output wire cannot be sliced")
-        merges, extra = self.plan(sliced, max_log2, method, trials)
+        merges, extra = self.plan(sliced, max_log2, method, trials, seed)
         if slice_ids is None:
             slice_ids = range(1 << len(sliced))
         total = np.zeros(1 << len(self.open_legs), dtype=np.complex128)
@@ -229,7 +229,7 @@ class CircuitNetwork:
 
 def batch_amplitudes(circuit, closed_bits: int, open_mask: int, sliced: Sequence[Label] = (),
                      slice_ids: Optional[Iterable[int]] = None, max_log2: int = 27,
-                     method: str = "greedy", trials: int = 8) -> np.ndarray:
+                     method: str = "greedy", trials: int = 8, seed: int = 0) -> np.ndarray:
     """Convenience wrapper: amplitudes (or a slice subset's partial sum) of one batch."""
     return CircuitNetwork(circuit, closed_bits, open_mask).contract(sliced, slice_ids, max_log2,
-                                                                    method, trials)
+                                                                    method, trials, seed)

@@ -22,11 +22,15 @@
 // Roles (416 threads, one CTA per SM, persistent over tiles):
 //   warps 0-3  epilogue: TMEM -> registers -> C (lane = tile row)
 //   warp  4    TMEM allocation; lane 0 issues tcgen05.mma and commits
-//   warps 5-12 loaders: A gathers + B' bulk copy per pipeline stage
+//   warps 5-12 loaders: A gathers + B' bulk copy per pipeline stage, or, when
+//              A is fetched by TMA in BF16X3 mode, the fp32 -> hi/lo converters
+//   warp  13   TMA producer: when A is stored as [contracted..., free...] its
+//              tiles are fetched by one tensor-map load per stage
 // Every mbarrier wait is bounded by a globaltimer deadline; on expiry the
 // kernel records TN_ERR_TIMEOUT in *err, every role leaves its loop, and the
 // CTA frees its TMEM and returns.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -37,13 +41,14 @@ namespace tnx {
 constexpr int TC_M = 128;
 constexpr int TC_TK = 16;            // complex k per pipeline stage
 constexpr int TC_KP = 2 * TC_TK;     // real K' per stage
-constexpr int TC_STAGES = 4;
+constexpr int TC_MAX_STAGES = 4;
 constexpr int TC_EPI_WARPS = 4;
 constexpr int TC_MMA_WARP = 4;
 constexpr int TC_LOAD_WARPS = 8;
 constexpr int TC_LOAD_THREADS = TC_LOAD_WARPS * 32;
-constexpr int TC_THREADS = (TC_EPI_WARPS + 1 + TC_LOAD_WARPS) * 32;
-constexpr int TC_AE = TC_M * TC_TK / TC_LOAD_THREADS;    // A elements per loader thread per stage
+constexpr int TC_PROD_WARP = TC_EPI_WARPS + 1 + TC_LOAD_WARPS;   // TMA producer
+constexpr int TC_THREADS = (TC_PROD_WARP + 1) * 32;
+constexpr int TC_RAW_BYTES = TC_M * TC_KP * 4;                     // fp32 A tile (TMA staging)
 constexpr int TC_TMEM_COLS = 512;
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;           // 4 s per wait
 constexpr int TC_MIN_SMEM = 120 * 1024;                  // keeps one CTA per SM
@@ -63,13 +68,20 @@ struct TcT<TC_BF16X3> {
 
 // bytes of one operand plane per stage: rows x 32 real elements
 __host__ __device__ constexpr int tc_plane_bytes(int rows, int esz) { return rows * TC_KP * esz; }
-// 16-byte chunks per row of one plane, and the stride between 8-row groups
-__host__ __device__ constexpr int tc_cpr(int esz) { return TC_KP * esz / 16; }
-__host__ __device__ constexpr int tc_sbo(int esz) { return tc_cpr(esz) * 128; }
-// byte offset of real element (row, kp) inside a K-major no-swizzle plane
+// Each plane row holds the stage's 32 real K' elements: 128 bytes for TF32,
+// 64 bytes for BF16.  Planes use the tensor cores' K-major swizzled layouts
+// (128-byte swizzle for 128-byte rows, 64-byte swizzle for 64-byte rows): row r
+// of an 8-row group sits at r * rowbytes and its 16-byte chunk c at chunk
+// position c ^ s(r), s(r) = r % 8 (128B) or (r / 2) % 4 (64B).  Writes of one
+// chunk by 8 consecutive rows, and of all chunks of one row, are both free of
+// bank conflicts.
+__host__ __device__ constexpr int tc_rowbytes(int esz) { return TC_KP * esz; }
+__host__ __device__ constexpr int tc_sbo(int esz) { return 8 * tc_rowbytes(esz); }
 __host__ __device__ inline int tc_elem_off(int row, int kp, int esz) {
   const int byte = kp * esz;
-  return (row >> 3) * tc_sbo(esz) + (byte >> 4) * 128 + (row & 7) * 16 + (byte & 15);
+  const int c = byte >> 4;
+  const int sw = esz == 4 ? (row & 7) : ((row >> 1) & 3);
+  return (row >> 3) * tc_sbo(esz) + (row & 7) * tc_rowbytes(esz) + ((c ^ sw) << 4) + (byte & 15);
 }
 
 struct TcArgs {
@@ -80,7 +92,21 @@ struct TcArgs {
   int32_t n_mt, n_nt, n_kc;
   int64_t n_tiles;
   int32_t* err;
+  int32_t a_tma;         // 1: A tiles by tensor-map loads (A stored as [k..., m...])
+  int32_t nst;           // pipeline stages
+  int32_t stage_bytes;   // bytes per stage: A planes, B' planes, fp32 staging
+  int32_t raw_off;       // offset of the fp32 staging tile in a stage (BF16X3 + TMA)
+  int32_t full_count;    // arrivals expected on a stage's "full" barrier
+  int32_t nmw;           // m bits that are tensor-map rows (contiguous after the k bits)
+  int32_t hi_shift;      // storage position where tensor-map dimension 2 starts
+  int64_t c2_inst_mul;   // dimension-2 step per linear instance (tn_contract_pair batches)
+  // epilogue write-back order: the 9 bits of a warp's 32-row x 16-column output
+  // block sorted by their storage position in C (sel = index | 64 for columns)
+  int32_t epi_ok;
+  int8_t epi_sel[9], epi_pos[9];
 };
+constexpr int TC_EPI_STRIDE = 17;                                  // staging row stride (float2)
+constexpr int TC_EPI_BYTES = TC_EPI_WARPS * 32 * TC_EPI_STRIDE * 8;  // epilogue staging
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -127,6 +153,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile 
     }
   }
 }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(a),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+      : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -155,13 +194,17 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
 }
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor, K-major swizzled: start address, leading
+// byte offset (unused for swizzled K-major, encoded as 16 B), stride byte
+// offset between 8-row groups, descriptor version 1, layout type (2 = 128-byte
+// swizzle, 4 = 64-byte swizzle)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, uint32_t layout) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+  d |= (uint64_t)1 << 16;
   d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)layout << 61;
   return d;
 }
 template <int MODE>
@@ -203,92 +246,127 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
 }
 
 // ------------------------------------------------------------------ B' images
-// One thread per complex B entry of every (instance, n tile, k chunk) block;
-// writes its 2x2 real form (split into hi/lo for BF16X3) at its place in the
-// block's shared-memory image.  Padding (k or n beyond the operand) is zero.
+// One thread per 16-byte chunk of every (instance, n tile, k chunk) block:
+// reads the complex B entries the chunk covers and writes their 2x2 real form
+// (split into hi/lo planes for BF16X3) in the block's shared-memory image.
+// Threads run in memory order of the image, so the writes are contiguous.
+// Padding (k or n beyond the operand) is zero.
 template <int MODE>
 __global__ void k_tc_prep_b(const TcArgs a) {
   using T = TcT<MODE>;
+  constexpr int KPC = 16 / (2 * T::ESZ);        // complex k per 16-byte chunk (2 or 4)
+  constexpr int CPR = TC_KP * T::ESZ / 16;      // chunks per row (8 or 4)
   const GemmArgs& g = a.g;
   const int ncp = 2 * a.tn_c;
   const int plane = tc_plane_bytes(ncp, T::ESZ);
   const int64_t block_bytes = (int64_t)T::NPL * plane;
-  const int per_block = TC_TK * a.tn_c;
+  const int per_block = ncp * CPR;              // chunks per plane
   const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
   const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int e = (int)(idx % per_block);
+    const int q = (int)(idx % per_block);
     const int64_t blk = idx / per_block;
+    // q in image order: row within the 8-row group fastest, then chunk, then group
+    const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
+    const int row = rg * 8 + rlo;
+    const int t = row & 1, nl = row >> 1;
     const int kc = (int)(blk % a.n_kc);
     const int nt = (int)((blk / a.n_kc) % a.n_nt);
     const int inst = (int)(blk / ((int64_t)a.n_kc * a.n_nt));
-    const int kl = e % TC_TK, nl = e / TC_TK;
-    float2 b = make_float2(0.f, 0.f);
-    if (kl < tkv && nl < tnv) {
-      const int64_t off = inst_offset(inst, g.b_istride, g.b_bpos, g.nb) +
-                          deposit_hi((uint64_t)kl, g.b_kpos, 0, g.tk) +
-                          deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk) +
-                          deposit_hi((uint64_t)nl, g.b_npos, 0, a.tnb) +
-                          deposit_hi((uint64_t)nt, g.b_npos, a.tnb, g.nn);
-      b = g.B[off];
+    float vals[2 * KPC];
+    const bool n_ok = nl < tnv;
+    int64_t base = 0;
+    if (n_ok)
+      base = inst_offset(inst, g.b_istride, g.b_bpos, g.nb) + deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk) +
+             deposit_hi((uint64_t)nl, g.b_npos, 0, a.tnb) + deposit_hi((uint64_t)nt, g.b_npos, a.tnb, g.nn);
+#pragma unroll
+    for (int i = 0; i < KPC; ++i) {
+      const int kl = c * KPC + i;
+      float2 b = make_float2(0.f, 0.f);
+      if (n_ok && kl < tkv) b = g.B[base + deposit_hi((uint64_t)kl, g.b_kpos, 0, g.tk)];
+      // row (n, t), columns (k, u): t = 0 -> (Re, -Im), t = 1 -> (Im, Re)
+      vals[2 * i] = t ? b.y : b.x;
+      vals[2 * i + 1] = t ? b.x : -b.y;
     }
-    uint8_t* base = const_cast<uint8_t*>(a.bimg) + blk * block_bytes;
-    // rows (n, t), columns (k, u)
-    const float v[2][2] = {{b.x, -b.y}, {b.y, b.x}};
-    for (int t = 0; t < 2; ++t)
-      for (int u = 0; u < 2; ++u) {
-        const int row = 2 * nl + t, kp = 2 * kl + u;
-        const int off = tc_elem_off(row, kp, T::ESZ);
-        if constexpr (MODE == TC_TF32) {
-          uint32_t bits;
-          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(bits) : "f"(v[t][u]));
-          *reinterpret_cast<uint32_t*>(base + off) = bits;
-        } else {
-          const __nv_bfloat16 hi = __float2bfloat16_rn(v[t][u]);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(v[t][u] - __bfloat162float(hi));
-          *reinterpret_cast<__nv_bfloat16*>(base + off) = hi;
-          *reinterpret_cast<__nv_bfloat16*>(base + plane + off) = lo;
-        }
+    uint8_t* dst = const_cast<uint8_t*>(a.bimg) + blk * block_bytes + tc_elem_off(row, c * KPC * 2, T::ESZ);
+    if constexpr (MODE == TC_TF32) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"(vals[i]));
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(vals[2 * i], vals[2 * i + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(vals[2 * i] - hf.x, vals[2 * i + 1] - hf.y);
+        hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[i] = *reinterpret_cast<const uint32_t*>(&l);
       }
+      *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(dst + plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
   }
 }
 
 // ------------------------------------------------------------------ the GEMM
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constant__ TcArgs a,
+                                                              const __grid_constant__ CUtensorMap tma_a) {
   using T = TcT<MODE>;
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  extern __shared__ __align__(1024) uint8_t smem_dyn[];
+  // swizzle atoms need 1024-byte aligned stage buffers
+  uint8_t* smem_raw = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
   const GemmArgs& g = a.g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncp = 2 * a.tn_c;                                   // N'
   const int a_plane = tc_plane_bytes(TC_M, T::ESZ);
   const int b_plane = tc_plane_bytes(ncp, T::ESZ);
-  const int stage_bytes = T::NPL * (a_plane + b_plane);
+  const int stage_bytes = a.stage_bytes;
+  const int nst = a.nst;
   uint8_t* stages = smem_raw;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + TC_STAGES * stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + nst * stage_bytes);
   uint64_t* full = bars;
-  uint64_t* empty = bars + TC_STAGES;
-  uint64_t* tfull = bars + 2 * TC_STAGES;
-  uint64_t* tempty = bars + 2 * TC_STAGES + 2;
-  uint64_t* fin = bars + 2 * TC_STAGES + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
+  uint64_t* empty = bars + TC_MAX_STAGES;
+  uint64_t* rawfull = bars + 2 * TC_MAX_STAGES;
+  uint64_t* tfull = bars + 3 * TC_MAX_STAGES;
+  uint64_t* tempty = bars + 3 * TC_MAX_STAGES + 2;
+  uint64_t* fin = bars + 3 * TC_MAX_STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TC_MAX_STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int64_t* offCm = reinterpret_cast<int64_t*>(tmem_slot + 4);
+  float2* epi_stage = reinterpret_cast<float2*>(smem_raw + nst * stage_bytes + 4096);
+  int64_t* epi_off = offCm + 2 * TC_M;                  // [16]: offsets of e bits 5-8
+  int* epi_rj = reinterpret_cast<int*>(epi_off + 16);   // [16]: (row << 8) | column of e bits 5-8
   int64_t* offCn = offCm + TC_M;
 
   // zero every stage once: padding rows / columns are never written again
-  for (int i = threadIdx.x; i < TC_STAGES * stage_bytes / 16; i += blockDim.x)
+  for (int i = threadIdx.x; i < nst * stage_bytes / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(stages)[i] = make_uint4(0, 0, 0, 0);
   const int tmv = 1 << g.tm, tnv = 1 << a.tnb;
   for (int r = threadIdx.x; r < TC_M; r += blockDim.x)
     offCm[r] = r < tmv ? deposit_hi((uint64_t)r, g.c_mpos, 0, g.tm) : 0;
   for (int c = threadIdx.x; c < 128; c += blockDim.x)
     offCn[c] = c < tnv ? deposit_hi((uint64_t)c, g.c_npos, 0, a.tnb) : 0;
+  if (threadIdx.x < 16 && a.epi_ok) {
+    int rj = 0;
+    int64_t off = 0;
+    for (int t = 5; t < 9; ++t)
+      if ((threadIdx.x >> (t - 5)) & 1) {
+        const int sl = a.epi_sel[t];
+        rj |= (sl & 64) ? (1 << (sl & 63)) : (1 << ((sl & 63) + 8));
+        off += (int64_t)1 << a.epi_pos[t];
+      }
+    epi_rj[threadIdx.x] = rj;
+    epi_off[threadIdx.x] = off;
+  }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
-      mbar_init(smem_u32(&full[s]), TC_LOAD_THREADS);
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(smem_u32(&full[s]), a.full_count);
       mbar_init(smem_u32(&empty[s]), 1);
+      mbar_init(smem_u32(&rawfull[s]), 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&tfull[i]), 1);
@@ -311,92 +389,265 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const TcArgs a) {
   const uint32_t tmem_base = *tmem_slot;
   const int kc_n = a.n_kc;
 
-  if (warp >= TC_MMA_WARP + 1) {
-    // ---------------------------------------------------------------- loaders
-    const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
-    // decode this thread's tile elements once: (smem offset, gmem offset)
-    int sm_off[TC_AE];
-    int64_t gm_off[TC_AE];
-    const int a_elems = 1 << g.a_tbits;
-#pragma unroll
-    for (int j = 0; j < TC_AE; ++j) {
-      const int e = lt + j * TC_LOAD_THREADS;
-      sm_off[j] = -1;
-      gm_off[j] = 0;
-      if (e < a_elems) {
-        int r = 0, c = 0;
-        int64_t off = 0;
-        for (int t = 0; t < g.a_tbits; ++t)
-          if ((e >> t) & 1) {
-            const int s = g.a_tsel[t];
-            if (s & 64) c |= 1 << (s & 63); else r |= 1 << (s & 63);
-            off += (int64_t)1 << g.a_tpos[t];
+  if (warp == TC_PROD_WARP) {
+    // ---------------------------------------------------------------- TMA producer
+    if (a.a_tma && lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tma_a)) : "memory");
+      int stage = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+        const int nt = (int)(tile % a.n_nt);
+        const int64_t rest = tile / a.n_nt;
+        const int mt = (int)(rest % a.n_mt);
+        const int inst = (int)(rest / a.n_mt);
+        // tensor-map coordinates of the tile: rows from the m bits after the
+        // first tm, dimension 2 from the remaining m bits and the instance bits
+        const int c1 = (mt & ((1 << (a.nmw - g.tm)) - 1)) << g.tm;
+        int64_t c2 = (int64_t)inst * a.c2_inst_mul;
+        for (int i = a.nmw; i < g.nm; ++i)
+          if ((mt >> (i - g.tm)) & 1) c2 += (int64_t)1 << (g.a_mpos[i] - a.hi_shift);
+        for (int j = 0; j < g.nb; ++j)
+          if ((inst >> j) & 1) c2 += (int64_t)1 << (g.a_bpos[j] - a.hi_shift);
+        const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * (int64_t)(T::NPL * b_plane);
+        for (int kc = 0; kc < kc_n; ++kc) {
+          if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
+          uint8_t* sa = stages + stage * stage_bytes;
+          uint8_t* sb = sa + T::NPL * a_plane;
+          const uint32_t fb = smem_u32(&full[stage]);
+          const uint8_t* bsrc = bt + (int64_t)kc * (T::NPL * b_plane);
+          if constexpr (MODE == TC_TF32) {
+            mbar_arrive_expect_tx(fb, (uint32_t)(TC_RAW_BYTES + T::NPL * b_plane));
+            bulk_g2s(smem_u32(sb), bsrc, T::NPL * b_plane, fb);
+            tma_load_3d(smem_u32(sa), &tma_a, kc * TC_KP, c1, (int)c2, fb);
+          } else {
+            // B' first, so that the converters cannot complete "full" before it is expected
+            mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
+            bulk_g2s(smem_u32(sb), bsrc, T::NPL * b_plane, fb);
+            const uint32_t rb = smem_u32(&rawfull[stage]);
+            mbar_arrive_expect_tx(rb, (uint32_t)TC_RAW_BYTES);
+            tma_load_3d(smem_u32(sa + a.raw_off), &tma_a, kc * TC_KP, c1, (int)c2, rb);
           }
-        sm_off[j] = tc_elem_off(r, 2 * c, T::ESZ);
-        gm_off[j] = off;
+          if (++stage == nst) {
+            stage = 0;
+            ph ^= 1;
+          }
+        }
       }
     }
-    int stage = 0;
-    uint32_t ph = 0;
-    bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-      const int nt = (int)(tile % a.n_nt);
+    __syncwarp();
+  } else if (warp >= TC_MMA_WARP + 1 && a.a_tma) {
+    // ---------------------------------------------------------------- converters (BF16X3 + TMA)
+    if constexpr (MODE != TC_TF32) {
+      const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
+      constexpr int NCH = TC_M * (TC_KP * T::ESZ / 16) / TC_LOAD_THREADS;
+      int stage = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+        for (int kc = 0; kc < kc_n; ++kc) {
+          if (!mbar_wait(smem_u32(&rawfull[stage]), ph, abort_flag, a.err)) { ok = false; break; }
+          uint8_t* sa = stages + stage * stage_bytes;
+          const uint8_t* raw = sa + a.raw_off;
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            const int q = lt + j * TC_LOAD_THREADS;
+            const int row = q % TC_M, c = q / TC_M;     // 16-byte output chunk: 4 complex
+            const float4 x0 = *reinterpret_cast<const float4*>(raw + tc_elem_off(row, 8 * c, 4));
+            const float4 x1 = *reinterpret_cast<const float4*>(raw + tc_elem_off(row, 8 * c + 4, 4));
+            const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(xs[2 * i], xs[2 * i + 1]);
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(xs[2 * i] - hf.x, xs[2 * i + 1] - hf.y);
+              hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+              lo[i] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+            const int off = tc_elem_off(row, 8 * c, T::ESZ);
+            *reinterpret_cast<uint4*>(sa + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(sa + a_plane + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
+          fence_proxy_async();
+          mbar_arrive(smem_u32(&full[stage]));
+          if (++stage == nst) {
+            stage = 0;
+            ph ^= 1;
+          }
+        }
+      }
+    }
+  } else if (warp >= TC_MMA_WARP + 1) {
+    // ---------------------------------------------------------------- loaders
+    // Thread lt owns tile row (lt % 128) and every other 16-byte chunk of it, so
+    // the 32 lanes of a warp write 32 consecutive rows: four whole 8 x 16-byte
+    // core matrices, free of bank conflicts whatever A's storage order.  A chunk
+    // holds KPC consecutive complex k (2 for TF32, 4 for BF16); when the lowest
+    // k bit is memory position 0 those are contiguous in global memory too.
+    constexpr int KPC = 16 / (2 * T::ESZ);
+    constexpr int CPR = TC_KP * T::ESZ / 16;      // 16-byte chunks per row
+    constexpr int NCH = TC_M * CPR / TC_LOAD_THREADS;  // chunks per thread per stage
+    const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
+    const int tkv = 1 << g.tk;
+    const bool kadj = g.nk > 0 && g.a_kpos[0] == 0;
+    // lanes walk the k chunks of a row when A's lowest memory bit is a k bit,
+    // else they walk rows; either way the swizzled stores are conflict-free
+    const bool klanes = kadj;
+    int64_t goff[NCH][KPC];   // offset of each complex of each chunk, -1 = padding
+    int soff[NCH];
+    bool cok[NCH];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int q = lt + j * TC_LOAD_THREADS;
+      const int row = klanes ? q / CPR : q % TC_M;
+      const int c = klanes ? q % CPR : q / TC_M;
+      cok[j] = row < (1 << g.tm);
+      soff[j] = tc_elem_off(row, c * KPC * 2, T::ESZ);
+      const int64_t roff = deposit_hi((uint64_t)row, g.a_mpos, 0, g.tm);
+#pragma unroll
+      for (int i = 0; i < KPC; ++i) {
+        const int k = c * KPC + i;
+        goff[j][i] = (cok[j] && k < tkv) ? roff + deposit_hi((uint64_t)k, g.a_kpos, 0, g.tk) : -1;
+      }
+    }
+    auto tile_base = [&](int64_t tile) -> const float2* {
       const int64_t rest = tile / a.n_nt;
       const int mt = (int)(rest % a.n_mt);
       const int inst = (int)(rest / a.n_mt);
-      const float2* A = g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) +
-                        deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
-      const uint8_t* bsrc = a.bimg + ((int64_t)inst * a.n_nt + nt) * (int64_t)kc_n * (T::NPL * b_plane);
-      for (int kc = 0; kc < kc_n; ++kc) {
-        const float2* Ak = A + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
+      return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) + deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
+    };
+    auto b_src = [&](int64_t tile, int kc) -> const uint8_t* {
+      const int nt = (int)(tile % a.n_nt);
+      const int inst = (int)(tile / a.n_nt / a.n_mt);
+      return a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n + kc) * (int64_t)(T::NPL * b_plane);
+    };
+    int stage = 0;
+    uint32_t ph = 0;
+    if constexpr (MODE == TC_TF32) {
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+        const float2* At = tile_base(tile);
+        const uint8_t* bt = b_src(tile, 0);
+        for (int kc = 0; kc < kc_n; ++kc) {
+          const float2* Ak = At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
+          uint8_t* sa = stages + stage * stage_bytes;
+          uint8_t* sb = sa + T::NPL * a_plane;
+          const uint32_t fb = smem_u32(&full[stage]);
+          if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
+          if (lt == 0) {
+            mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
+            bulk_g2s(smem_u32(sb), bt + (int64_t)kc * (T::NPL * b_plane), T::NPL * b_plane, fb);
+          }
+          {
+            const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+              if (!cok[j]) continue;
+              if (v16 && goff[j][1] >= 0) {
+                cp_async16(smem_u32(sa + soff[j]), Ak + goff[j][0]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < KPC; ++i)
+                  if (goff[j][i] >= 0) cp_async8(smem_u32(sa + soff[j] + 8 * i), Ak + goff[j][i]);
+              }
+            }
+          }
+          cp_async_arrive_noinc(fb);
+          if (++stage == nst) {
+            stage = 0;
+            ph ^= 1;
+          }
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+      // BF16X3: the next stage's loads are in flight in registers while the
+      // current one is split into hi/lo and stored
+      float4 v0[NCH][KPC / 2], v1[NCH][KPC / 2];
+      auto issue = [&](float4(&v)[NCH][KPC / 2], const float2* Ak) {
+        const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
+#pragma unroll
+        for (int j = 0; j < NCH; ++j)
+#pragma unroll
+          for (int h = 0; h < KPC / 2; ++h) {
+            const int64_t o0 = goff[j][2 * h], o1 = goff[j][2 * h + 1];
+            if (v16 && o1 >= 0) {
+              v[j][h] = __ldg(reinterpret_cast<const float4*>(Ak + o0));
+            } else {
+              const float2 x = o0 >= 0 ? __ldg(Ak + o0) : make_float2(0.f, 0.f);
+              const float2 y = o1 >= 0 ? __ldg(Ak + o1) : make_float2(0.f, 0.f);
+              v[j][h] = make_float4(x.x, x.y, y.x, y.y);
+            }
+          }
+      };
+      int64_t tile = blockIdx.x;
+      int kc = 0;
+      const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
+      const float2* An = At;     // base of the tile of the prefetched stage
+      auto body = [&](float4(&vc)[NCH][KPC / 2], float4(&vn)[NCH][KPC / 2]) -> bool {
+        int64_t ntile = tile;
+        int nkc = kc + 1;
+        if (nkc == kc_n) {
+          nkc = 0;
+          ntile += gridDim.x;
+          if (ntile < a.n_tiles) An = tile_base(ntile);
+        }
+        if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
         uint8_t* sa = stages + stage * stage_bytes;
         uint8_t* sb = sa + T::NPL * a_plane;
         const uint32_t fb = smem_u32(&full[stage]);
-        if constexpr (MODE == TC_TF32) {
-          if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
-          if (lt == 0) {
-            mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
-            bulk_g2s(smem_u32(sb), bsrc + (int64_t)kc * (T::NPL * b_plane), T::NPL * b_plane, fb);
-          }
-#pragma unroll
-          for (int j = 0; j < TC_AE; ++j)
-            if (sm_off[j] >= 0) cp_async8(smem_u32(sa + sm_off[j]), Ak + gm_off[j]);
-          cp_async_arrive_noinc(fb);
-        } else {
-          float2 v[TC_AE];
-#pragma unroll
-          for (int j = 0; j < TC_AE; ++j)
-            if (sm_off[j] >= 0) v[j] = __ldg(Ak + gm_off[j]);
-          if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
-          if (lt == 0) {
-            mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
-            bulk_g2s(smem_u32(sb), bsrc + (int64_t)kc * (T::NPL * b_plane), T::NPL * b_plane, fb);
-          }
-#pragma unroll
-          for (int j = 0; j < TC_AE; ++j)
-            if (sm_off[j] >= 0) {
-              const __nv_bfloat162 hi = __floats2bfloat162_rn(v[j].x, v[j].y);
-              const float2 hf = __bfloat1622float2(hi);
-              const __nv_bfloat162 lo = __floats2bfloat162_rn(v[j].x - hf.x, v[j].y - hf.y);
-              *reinterpret_cast<__nv_bfloat162*>(sa + sm_off[j]) = hi;
-              *reinterpret_cast<__nv_bfloat162*>(sa + a_plane + sm_off[j]) = lo;
-            }
-          fence_proxy_async();
-          mbar_arrive(fb);
+        if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) return false;
+        if (lt == 0) {
+          mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
+          bulk_g2s(smem_u32(sb), b_src(tile, kc), T::NPL * b_plane, fb);
         }
-        if (++stage == TC_STAGES) {
+        {
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            if (!cok[j]) continue;
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int h = 0; h < KPC / 2; ++h) {
+              const float4 x = vc[j][h];
+              const __nv_bfloat162 h0 = __floats2bfloat162_rn(x.x, x.y);
+              const __nv_bfloat162 h1 = __floats2bfloat162_rn(x.z, x.w);
+              const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+              const __nv_bfloat162 l0 = __floats2bfloat162_rn(x.x - f0.x, x.y - f0.y);
+              const __nv_bfloat162 l1 = __floats2bfloat162_rn(x.z - f1.x, x.w - f1.y);
+              hi[2 * h] = *reinterpret_cast<const uint32_t*>(&h0);
+              hi[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&h1);
+              lo[2 * h] = *reinterpret_cast<const uint32_t*>(&l0);
+              lo[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&l1);
+            }
+            *reinterpret_cast<uint4*>(sa + soff[j]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(sa + a_plane + soff[j]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
+        }
+        fence_proxy_async();
+        mbar_arrive(fb);
+        if (++stage == nst) {
           stage = 0;
           ph ^= 1;
         }
+        if (ntile != tile) At = An;
+        tile = ntile;
+        kc = nkc;
+        return true;
+      };
+      if (tile < a.n_tiles) issue(v0, At);
+      while (tile < a.n_tiles) {
+        if (!body(v0, v1) || tile >= a.n_tiles) break;
+        if (!body(v1, v0)) break;
       }
     }
-    if constexpr (MODE == TC_TF32) asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == TC_MMA_WARP) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
       const uint32_t idesc = (1u << 4) | ((uint32_t)T::FMT << 7) | ((uint32_t)T::FMT << 10) |
                              ((uint32_t)(ncp >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
       const uint32_t sbo = tc_sbo(T::ESZ);
+      const uint32_t lay = T::ESZ == 4 ? 2u : 4u;
       int stage = 0;
       uint32_t ph = 0;
       int64_t it = 0;
@@ -415,20 +666,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const TcArgs a) {
           const uint32_t sb = sa + T::NPL * a_plane;
 #pragma unroll
           for (int j = 0; j < TC_KP * T::ESZ / 32; ++j) {
-            const uint32_t koff = (uint32_t)j * 256u;
+            // one MMA K step = 32 bytes of every row: advance inside the swizzle atom
+            const uint32_t koff = (uint32_t)j * 32u;
             const uint32_t first = (kc > 0 || j > 0) ? 1u : 0u;
-            const uint64_t ad = smem_desc(sa + koff, 128, sbo);
-            const uint64_t bd = smem_desc(sb + koff, 128, sbo);
+            const uint64_t ad = smem_desc(sa + koff, sbo, lay);
+            const uint64_t bd = smem_desc(sb + koff, sbo, lay);
             tc_mma<MODE>(d_tmem, ad, bd, idesc, first);
             if constexpr (MODE == TC_BF16X3) {
-              const uint64_t bdl = smem_desc(sb + b_plane + koff, 128, sbo);
-              const uint64_t adl = smem_desc(sa + a_plane + koff, 128, sbo);
+              const uint64_t bdl = smem_desc(sb + b_plane + koff, sbo, lay);
+              const uint64_t adl = smem_desc(sa + a_plane + koff, sbo, lay);
               tc_mma<MODE>(d_tmem, ad, bdl, idesc, 1u);
               tc_mma<MODE>(d_tmem, adl, bd, idesc, 1u);
             }
           }
           tc_commit(smem_u32(&empty[stage]));
-          if (++stage == TC_STAGES) {
+          if (++stage == nst) {
             stage = 0;
             ph ^= 1;
           }
@@ -444,6 +696,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const TcArgs a) {
   } else {
     // ---------------------------------------------------------------- epilogue
     const int row = warp * 32 + lane;
+    // write-back decode: e = lane + 32 i; lane bits are e bits 0-4, i bits 5-8
+    int epi_rj_l = 0;
+    int64_t epi_off_l = 0;
+    if (a.epi_ok)
+      for (int t = 0; t < 5; ++t)
+        if ((lane >> t) & 1) {
+          const int sl = a.epi_sel[t];
+          epi_rj_l |= (sl & 64) ? (1 << (sl & 63)) : (1 << ((sl & 63) + 8));
+          epi_off_l += (int64_t)1 << a.epi_pos[t];
+        }
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
       const int acc = (int)(it & 1);
@@ -462,7 +724,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const TcArgs a) {
       for (int c0 = 0; c0 < ncp; c0 += 32) {
         float v[32];
         tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * ncp + c0), v);
-        if (row_ok) {
+        if (a.epi_ok) {
+          // stage the warp's 32 x 16 block, then write it in C's memory order:
+          // element e = lane + 32 i has its bits on C's lowest positions first
+          float2* stg = epi_stage + warp * 32 * TC_EPI_STRIDE;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) stg[lane * TC_EPI_STRIDE + j] = make_float2(v[2 * j], v[2 * j + 1]);
+          __syncwarp();
+          if (warp * 32 < tmv && c0 / 2 < tnv) {
+            float2* base = C + offCm[warp * 32] + offCn[c0 / 2] + epi_off_l;
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+              const int rj = epi_rj_l | epi_rj[i];
+              base[epi_off[i]] = stg[(rj >> 8) * TC_EPI_STRIDE + (rj & 255)];
+            }
+          }
+          __syncwarp();
+        } else if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int n = c0 / 2 + j;

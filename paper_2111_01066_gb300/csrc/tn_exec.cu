@@ -1,5 +1,7 @@
 // Device executor: the slice loop of a plan on one GPU, the XEB reduction, and
 // the standalone kernel entry points of the C ABI.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -126,22 +128,75 @@ static void launch_simt(const GemmArgs& g, int kid, cudaStream_t s) {
   }
 }
 
-// One step ready to launch: GEMM arguments, tensor-core tiling, B' workspace size.
+// One step ready to launch: GEMM arguments, tensor-core tiling, B' workspace
+// size, and the tensor map of A when its tiles are fetched by TMA.
 struct StepLaunch {
   int kid = 0;
   GemmArgs g;
   TcArgs tc;
+  alignas(64) CUtensorMap tma;
   int64_t ws_bytes = 0;
   int smem = 0;
 };
 
 static bool is_tc(int kid) { return kid == K_TC_TF32 || kid == K_TC_BF16X3; }
 
-static StepLaunch make_launch(const GemmArgs& g, int kid) {
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// A can be fetched by TMA when it is stored as [its k bits in order, then at
+// least 128 rows of m bits in order]: a row-major matrix per dimension-2 index.
+// a_bits = log2 of A's elements over one linear instance; n_lin = linear instances.
+static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
+  const GemmArgs& g = L.g;
+  TcArgs& t = L.tc;
+  t.a_tma = 0;
+  if (g.nk < 4 || g.tm != 7 || (reinterpret_cast<uintptr_t>(g.A) & 15)) return;
+  for (int j = 0; j < g.nk; ++j)
+    if (g.a_kpos[j] != j) return;
+  int nmw = 0;
+  while (nmw < g.nm && g.a_mpos[nmw] == g.nk + nmw) ++nmw;
+  if (nmw < 7) return;
+  const int hi_shift = g.nk + nmw;
+  if (a_bits < hi_shift) return;
+  const uint64_t dim2 = ((uint64_t)1 << (a_bits - hi_shift)) * (uint64_t)n_lin;
+  if (dim2 > ((uint64_t)1 << 31)) return;
+  auto enc = tensor_map_encoder();
+  if (!enc) return;
+  cuuint64_t dims[3] = {(cuuint64_t)2 << g.nk, (cuuint64_t)1 << nmw, (cuuint64_t)dim2};
+  cuuint64_t strides[2] = {((cuuint64_t)1 << g.nk) * 8, ((cuuint64_t)1 << hi_shift) * 8};
+  cuuint32_t box[3] = {(cuuint32_t)TC_KP, (cuuint32_t)TC_M, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(&L.tma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(g.A), dims, strides, box,
+                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return;
+  t.a_tma = 1;
+  t.nmw = nmw;
+  t.hi_shift = hi_shift;
+  t.c2_inst_mul = n_lin > 1 ? ((int64_t)1 << (a_bits - hi_shift)) : 0;
+}
+
+static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_lin) {
   StepLaunch L;
   L.kid = kid;
   L.g = g;
   std::memset(&L.tc, 0, sizeof(L.tc));
+  std::memset(&L.tma, 0, sizeof(L.tma));
   if (!is_tc(kid)) return L;
   TcArgs& t = L.tc;
   t.g = g;
@@ -155,7 +210,27 @@ static StepLaunch make_launch(const GemmArgs& g, int kid) {
   const int b_plane = tc_plane_bytes(2 * t.tn_c, esz);
   const int a_plane = tc_plane_bytes(TC_M, esz);
   L.ws_bytes = (int64_t)g.n_inst * t.n_nt * t.n_kc * npl * b_plane;
-  L.smem = std::max(TC_STAGES * npl * (a_plane + b_plane) + 4096, TC_MIN_SMEM);
+  setup_tma(L, a_bits, n_lin);
+  const bool staging = t.a_tma && kid == K_TC_BF16X3;
+  t.stage_bytes = npl * (a_plane + b_plane) + (staging ? TC_RAW_BYTES : 0);
+  t.raw_off = npl * (a_plane + b_plane);
+  t.nst = std::min(TC_MAX_STAGES, (220 * 1024 - 4096 - TC_EPI_BYTES) / t.stage_bytes);
+  t.full_count = t.a_tma ? (kid == K_TC_TF32 ? 1 : TC_LOAD_THREADS) : TC_LOAD_THREADS;
+  L.smem = std::max(t.nst * t.stage_bytes + 4096 + TC_EPI_BYTES + 1024, TC_MIN_SMEM);
+  // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
+  t.epi_ok = 0;
+  if (g.tm >= 5 && g.tn >= 4) {
+    std::vector<std::pair<int, int>> bits;
+    for (int i = 0; i < 5; ++i) bits.push_back({g.c_mpos[i], i});
+    for (int j = 0; j < 4; ++j) bits.push_back({g.c_npos[j], j | 64});
+    std::sort(bits.begin(), bits.end());
+    for (int t2 = 0; t2 < 9; ++t2) {
+      t.epi_pos[t2] = (int8_t)bits[t2].first;
+      t.epi_sel[t2] = (int8_t)bits[t2].second;
+    }
+    // rows already contiguous at C's lowest position: direct per-column stores coalesce
+    t.epi_ok = (bits[0].second & 64) ? 1 : 0;
+  }
   return L;
 }
 
@@ -178,7 +253,7 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
       CK(cudaFuncSetAttribute(k_cgemm_tc<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
       attr = true;
     }
-    k_cgemm_tc<TC_TF32><<<grid, TC_THREADS, L.smem, s>>>(t);
+    k_cgemm_tc<TC_TF32><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
   } else {
     k_tc_prep_b<TC_BF16X3><<<pblocks, 256, 0, s>>>(t);
     static bool attr = false;
@@ -186,7 +261,7 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
       CK(cudaFuncSetAttribute(k_cgemm_tc<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
       attr = true;
     }
-    k_cgemm_tc<TC_BF16X3><<<grid, TC_THREADS, L.smem, s>>>(t);
+    k_cgemm_tc<TC_BF16X3><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
   }
 }
 
@@ -269,7 +344,8 @@ static void ensure_device(Plan& p) {
     if (!ok) fail(TN_ERR_PLAN, "internal: step operand outside its extent");
     const int kid = pick_kernel(p.opts.precision, d);
     ds->launches.push_back(make_launch(
-        make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off, 1 << d.nb), kid));
+        make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off, 1 << d.nb), kid,
+        64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1));
   }
   int64_t ws = 16;
   for (const StepLaunch& L : ds->launches) ws = std::max(ws, L.ws_bytes);
@@ -383,7 +459,8 @@ extern "C" tn_status tn_contract_slices(tn_plan_t* h, uint64_t first, uint64_t c
   API_END
 }
 
-extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_out, void* stream) {
+extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_out, int32_t* kernel_out,
+                                        void* stream) {
   API_BEGIN
   if (!h || !ms_out) fail(TN_ERR_ARG, "tn_plan_step_times: NULL argument");
   if (reps < 1) fail(TN_ERR_ARG, "tn_plan_step_times: reps must be >= 1");
@@ -404,6 +481,7 @@ extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_o
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, e0, e1));
     ms_out[i] = (double)ms / reps;
+    if (kernel_out) kernel_out[i] = ds.launches[i].kid;
   }
   CK(cudaGetLastError());
   cudaEventDestroy(e0);
@@ -549,7 +627,7 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   const int kid = pick_kernel(precision, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                          reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
-  StepLaunch L = make_launch(g, kid);
+  StepLaunch L = make_launch(g, kid, ar, batch);
   Scratch& sc = scratch_for_device();
   if (L.ws_bytes > sc.ws_bytes) {
     CK(cudaStreamSynchronize((cudaStream_t)stream));
@@ -645,7 +723,7 @@ extern "C" tn_status tn_contract_pair_noalloc(const float* a, const int32_t* aw,
   const int kid = pick_kernel(precision, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                          reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
-  StepLaunch L = make_launch(g, kid);
+  StepLaunch L = make_launch(g, kid, ar, batch);
   const int64_t cap = (int64_t)(kNoAllocScratchBytes - kNoAllocErrBytes);
   if (L.ws_bytes > cap)
     fail(TN_ERR_ARG, "tn_contract_pair_noalloc: this contraction needs " + std::to_string(L.ws_bytes) +

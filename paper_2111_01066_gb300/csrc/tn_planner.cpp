@@ -7,6 +7,7 @@
 #include <array>
 #include <cstring>
 #include <functional>
+#include <iterator>
 #include <limits>
 #include <memory>
 #include <new>
@@ -693,6 +694,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
     return (int64_t)1 << (ni.wires.size() + __builtin_popcount(ni.bmask));
   };
   const int64_t cap_bytes = o.max_arena_bytes > 0 ? o.max_arena_bytes : (int64_t)96 << 30;
+  std::vector<std::vector<int>> node_order;   // storage order wanted by each node's consumer
   auto layout = [&](int b, std::vector<NodeInfo>& info, std::vector<StepDesc>& steps,
                     int64_t& arena) -> bool {
     info.assign(L + nm, NodeInfo{});
@@ -703,6 +705,44 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       for (int w : S.leaves[i].wires)
         if (!S.fixed[w] && SL.test(pw_of[w]) && slice_bit[pw_of[w]] < b)
           info[i].bmask |= 1u << slice_bit[pw_of[w]];
+    }
+    // Layout pass (SI figure S7a: C is written in the index order its consumer
+    // wants).  Every tensor that a step streams as its large operand A is stored
+    // as [the wires that step contracts..., its free wires...], i.e. as a plain
+    // row-major matrix of rows = free indices, so the GEMM can fetch its tiles
+    // with the tensor memory accelerator.  Other tensors keep the order they are
+    // produced in.
+    {
+      std::vector<std::vector<int>> wset(L + nm);
+      std::vector<uint32_t> bm(L + nm, 0);
+      for (int i = 0; i < L; ++i) {
+        wset[i] = info[i].wires;
+        std::sort(wset[i].begin(), wset[i].end());
+        bm[i] = info[i].bmask;
+      }
+      std::vector<std::vector<int>> want(L + nm);
+      for (int mi : order) {
+        const int x = T.merges[mi].first, y = T.merges[mi].second;
+        std::vector<int> u;
+        std::set_symmetric_difference(wset[x].begin(), wset[x].end(), wset[y].begin(), wset[y].end(),
+                                      std::back_inserter(u));
+        wset[L + mi] = u;
+        bm[L + mi] = bm[x] | bm[y];
+        const int64_t ex = (int64_t)1 << (wset[x].size() + __builtin_popcount(bm[x]));
+        const int64_t ey = (int64_t)1 << (wset[y].size() + __builtin_popcount(bm[y]));
+        const bool x_is_a = ex > ey || (ex == ey && wset[x].size() >= wset[y].size());
+        const int a = x_is_a ? x : y, bb = x_is_a ? y : x;
+        std::vector<int> k, m;
+        std::set_intersection(wset[a].begin(), wset[a].end(), wset[bb].begin(), wset[bb].end(),
+                              std::back_inserter(k));
+        std::set_difference(wset[a].begin(), wset[a].end(), wset[bb].begin(), wset[bb].end(),
+                            std::back_inserter(m));
+        want[a] = k;
+        want[a].insert(want[a].end(), m.begin(), m.end());
+      }
+      for (int i = 0; i < L; ++i)
+        if (!want[i].empty()) info[i].wires = want[i];
+      node_order.swap(want);
     }
     // best-fit arena allocator
     std::vector<std::pair<int64_t, int64_t>> freel;  // (offset, size)
@@ -763,6 +803,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
         if (std::find(A.wires.begin(), A.wires.end(), w) == A.wires.end()) nw.push_back(w);
       C.wires = mw;
       C.wires.insert(C.wires.end(), nw.begin(), nw.end());
+      if (!node_order[L + mi].empty()) C.wires = node_order[L + mi];
       C.bmask = A.bmask | B.bmask;
       auto pos_in = [](const std::vector<int>& ws, int w) {
         return (int)(std::find(ws.begin(), ws.end(), w) - ws.begin());

@@ -81,7 +81,7 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p]),
     "tn_plan_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "tn_plan_step_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
-                                          ctypes.c_void_p]),
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "tn_plan_destroy": (None, [ctypes.c_void_p]),
     "tn_xeb": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
@@ -230,12 +230,15 @@ class Plan:
         _check(load().tn_contract_slices(self.handle, slice_first, slice_count, bs, len(bitstrings),
                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
 
-    def step_times(self, reps: int = 3, stream=None) -> List[float]:
-        """Mean device milliseconds per launch of every step's kernel."""
+    KERNELS = {0: "simt64x64", 1: "simt128x16", 2: "simt256x4", 3: "tc_tf32", 4: "tc_bf16x3"}
+
+    def step_times(self, reps: int = 3, stream=None) -> List[Tuple[float, str]]:
+        """(mean device milliseconds per launch, kernel name) of every step."""
         n = self.info()["n_steps"]
         arr = (ctypes.c_double * max(1, n))()
-        _check(load().tn_plan_step_times(self.handle, reps, arr, _stream_handle(stream)))
-        return list(arr)[:n]
+        kid = (ctypes.c_int32 * max(1, n))()
+        _check(load().tn_plan_step_times(self.handle, reps, arr, kid, _stream_handle(stream)))
+        return [(arr[i], self.KERNELS.get(kid[i], str(kid[i]))) for i in range(n)]
 
     def sync(self, stream=None) -> None:
         _check(load().tn_plan_sync(self.handle, _stream_handle(stream)))
