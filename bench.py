@@ -167,6 +167,12 @@ def cores_used() -> int:
 # ------------------------------------------------------------------ rooflines
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 x GHz
 
+# DRAM bytes (read + write) per launch from ncu captures of the current kernels,
+# keyed by (kernel, log2 m,k,n,batch); see profiles/ for the command and scaling.
+MEASURED_TRAFFIC = {
+    ("tc_bf16x3", (16, 12, 9, 4)): 46.9e9,   # 64 x the 16384x4096x512 proxy capture (733.0 MB)
+}
+
 
 def load_peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -203,7 +209,8 @@ def step_roofline(shape, ms: float, kernel: str, peaks: dict) -> dict:
     else:
         ach = nbytes / (ms / 1e3) / 1e9
         r = {"bound": "hbm", "achieved": ach, "peak": bw, "unit": "GB/s", "frac": ach / bw}
-    r.update({"traffic": None, "kernel": kernel, "shape_log2_mknb": [m, k, n, b], "ms": ms,
+    r.update({"traffic": MEASURED_TRAFFIC.get((kernel, (m, k, n, b))), "kernel": kernel,
+              "shape_log2_mknb": [m, k, n, b], "ms": ms,
               "t_roof_ms": max(t_c, t_m), "peak_source": peaks.get("source", "measured")})
     return r
 

@@ -45,27 +45,49 @@ __global__ void k_leaf_select(const float2* __restrict__ leaf_data, const LeafDe
   }
 }
 
-// out[batch][j] += sum over the chunk's valid slices of the root tensor, FP64.
-__global__ void k_root_accumulate(const float2* __restrict__ arena, const RootDesc r, int b,
-                                  double* __restrict__ out, const ChunkParam* __restrict__ params,
-                                  const unsigned* __restrict__ counter) {
+// Slice sum of a chunk (main text, section II: the sliced network is the sum of
+// the smaller networks), FP64, in two deterministic passes: k_root_partial sums
+// the slices of group g (slices g*per .. g*per+per-1 of the chunk) for every
+// amplitude j into part[g][j]; k_root_finish adds the groups in order into
+// out[batch][j].  Slices outside the call's range are skipped.
+__global__ void k_root_partial(const float2* __restrict__ arena, const RootDesc r, int b, int groups,
+                               double2* __restrict__ part, const ChunkParam* __restrict__ params,
+                               const unsigned* __restrict__ counter) {
   const ChunkParam p = params[*counter];
   const int k = r.rank;
   const int64_t nout = (int64_t)1 << k;
+  const uint32_t per = (1u << b) / (uint32_t)groups;
+  const int g = blockIdx.y;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nout;
        j += (int64_t)gridDim.x * blockDim.x) {
     int64_t ri = 0;
     for (int q = 0; q < k; ++q)
       if ((j >> q) & 1) ri |= (int64_t)1 << r.pos_of_open[q];
     double sr = 0.0, si = 0.0;
-    const uint32_t nlow = 1u << b;
-    for (uint32_t s = 0; s < nlow; ++s) {
+    for (uint32_t s = (uint32_t)g * per; s < (uint32_t)(g + 1) * per; ++s) {
       const uint64_t sid = p.slice_base + s;
       if (sid < p.valid_lo || sid >= p.valid_hi) continue;
       const uint32_t inst = pext_u32(s, r.bmask);
       const float2 v = arena[r.off + ((int64_t)inst << k) + ri];
       sr += (double)v.x;
       si += (double)v.y;
+    }
+    part[(int64_t)g * nout + j] = make_double2(sr, si);
+  }
+}
+
+__global__ void k_root_finish(const double2* __restrict__ part, int groups, int k,
+                              const ChunkParam* __restrict__ params, const unsigned* __restrict__ counter) {
+  const ChunkParam p = params[*counter];
+  double* __restrict__ out = p.out;
+  const int64_t nout = (int64_t)1 << k;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nout;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int g = 0; g < groups; ++g) {
+      const double2 v = part[(int64_t)g * nout + j];
+      sr += v.x;
+      si += v.y;
     }
     double* o = out + 2 * (p.out_index * nout + j);
     o[0] += sr;

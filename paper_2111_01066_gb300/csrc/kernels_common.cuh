@@ -13,6 +13,7 @@ struct ChunkParam {
   uint64_t valid_hi;
   uint64_t bitstring;    // closed output bits of the batch
   int64_t out_index;     // batch index into the output amplitudes
+  double* out;           // the call's output amplitudes (complex128)
 };
 
 // Launch arguments of one gathered complex GEMM (one plan step or one

@@ -276,9 +276,16 @@ struct DeviceState {
   unsigned* counter = nullptr;
   int32_t* err = nullptr;
   uint8_t* ws = nullptr;
+  double2* root_part = nullptr;   // [groups][2^k] partial slice sums
+  int root_groups = 1;
   std::vector<StepLaunch> launches;
   cudaEvent_t done = nullptr;
   bool have_done = false;
+  // the chunk's launch sequence as one CUDA graph, captured after the first
+  // eager chunk; every kernel reads its chunk parameters from device memory
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+  bool eager_done = false;
 };
 
 // Tensor-core kernels for every step with enough work in the TF32 / BF16X3
@@ -353,6 +360,8 @@ static void ensure_device(Plan& p) {
     cudaGetLastError();
     fail(TN_ERR_OOM, "workspace allocation of " + std::to_string(ws) + " bytes failed");
   }
+  ds->root_groups = std::min(1 << p.log2_batch, 64);
+  CK(cudaMalloc(&ds->root_part, sizeof(double2) * (size_t)ds->root_groups << p.root.rank));
   if (!in_arena(p.root.off, (int64_t)1 << p.root.rank, 1 << __builtin_popcount(p.root.bmask)))
     fail(TN_ERR_PLAN, "internal: root outside the arena");
 }
@@ -371,13 +380,15 @@ void destroy_device_state(Plan* p) {
   cudaFree(ds->counter);
   cudaFree(ds->err);
   cudaFree(ds->ws);
+  cudaFree(ds->root_part);
+  if (ds->graph) cudaGraphExecDestroy(ds->graph);
   if (ds->done) cudaEventDestroy(ds->done);
   cudaSetDevice(cur);
   delete ds;
   p->dev = nullptr;
 }
 
-static void run_chunk(Plan& p, double* out, cudaStream_t s) {
+static void run_chunk(Plan& p, cudaStream_t s) {
   DeviceState& ds = *p.dev;
   const int nl = (int)p.leaves.size();
   k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
@@ -385,8 +396,41 @@ static void run_chunk(Plan& p, double* out, cudaStream_t s) {
   for (size_t i = 0; i < p.steps.size(); ++i) launch_step(ds.launches[i], ds.ws, ds.err, s);
   const int64_t nout = (int64_t)1 << p.root.rank;
   const int blocks = (int)std::min<int64_t>((nout + 255) / 256, 4096);
-  k_root_accumulate<<<blocks, 256, 0, s>>>(ds.arena, p.root, p.log2_batch, out, ds.params, ds.counter);
+  k_root_partial<<<dim3(blocks, ds.root_groups), 256, 0, s>>>(ds.arena, p.root, p.log2_batch, ds.root_groups,
+                                                               ds.root_part, ds.params, ds.counter);
+  k_root_finish<<<blocks, 256, 0, s>>>(ds.root_part, ds.root_groups, p.root.rank, ds.params, ds.counter);
   k_advance<<<1, 1, 0, s>>>(ds.counter);
+}
+
+// Capture run_chunk once into a graph (on a private stream, thread-local
+// capture mode).  Any failure leaves the plan on eager launches.
+static void capture_chunk_graph(Plan& p) {
+  DeviceState& ds = *p.dev;
+  if (ds.graph || ds.graph_failed) return;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ds.graph_failed = true;
+    return;
+  }
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    try {
+      run_chunk(p, cs);
+    } catch (const TnError&) {
+      ok = false;
+    }
+    ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ds.graph, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (!ok) {
+    cudaGetLastError();
+    ds.graph = nullptr;
+    ds.graph_failed = true;
+  }
 }
 
 }  // namespace tnx
@@ -436,6 +480,7 @@ extern "C" tn_status tn_contract_slices(tn_plan_t* h, uint64_t first, uint64_t c
       c.valid_hi = std::min(first + count, base + step);
       c.bitstring = bitstrings[i] & ~open_mask;
       c.out_index = i;
+      c.out = out;
       prm.push_back(c);
     }
   if (ds.have_done) CK(cudaStreamWaitEvent(s, ds.done, 0));
@@ -451,7 +496,17 @@ extern "C" tn_status tn_contract_slices(tn_plan_t* h, uint64_t first, uint64_t c
   CK(cudaMemcpyAsync(ds.params, prm.data(), prm.size() * sizeof(ChunkParam), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
   for (size_t c = 0; c < prm.size(); ++c) {
-    run_chunk(p, out, s);
+    if (!ds.eager_done) {
+      run_chunk(p, s);           // the first chunk runs eagerly (sets kernel attributes)
+      CK(cudaGetLastError());
+      ds.eager_done = true;
+      capture_chunk_graph(p);
+      continue;
+    }
+    if (ds.graph)
+      CK(cudaGraphLaunch(ds.graph, s));
+    else
+      run_chunk(p, s);
     CK(cudaGetLastError());
   }
   CK(cudaEventRecord(ds.done, s));

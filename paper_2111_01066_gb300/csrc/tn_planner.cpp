@@ -1020,7 +1020,7 @@ extern "C" tn_status tn_plan_info(const tn_plan_t* h, tn_plan_stats* s) {
   s->arena_bytes = p.arena_elems * 8;
   for (int i = 0; i < 40; ++i) s->k_histogram[i] = p.stats.khist[i];
   s->complex_mult = p.opts.complex_mult;
-  s->n_kernel_launches_per_chunk = (int)p.steps.size() + 3;
+  s->n_kernel_launches_per_chunk = (int)p.steps.size() + 4;
   return TN_OK;
 }
 

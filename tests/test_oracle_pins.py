@@ -268,6 +268,16 @@ def test_slicing_identity_and_additivity():
         assert np.linalg.norm(one - full) > 1e-6 * np.linalg.norm(full)  # a slice is not the sum
 
 
+def test_bisection_order_matches_greedy():
+    """The oracle's two contraction orders give the same amplitudes (the order
+    only changes rounding), on a 30-qubit batch."""
+    circ, om, cb = rqcgen.config_circuit("c2")
+    net = tn.CircuitNetwork(circ, cb, om)
+    a = net.contract(method="greedy")
+    b = net.contract(method="bisect", trials=4, max_log2=20)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+
+
 def test_oracle_subslicing_changes_nothing():
     circ, om, cb = rqcgen.config_circuit("c1")
     net = tn.CircuitNetwork(circ, cb, om)
