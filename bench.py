@@ -39,6 +39,16 @@ import rqcgen  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
 
+# per workload: slices contracted per step (None: all) and slices per chunk (0: planner's choice)
+WORKLOAD_RUN = {
+    "c1": dict(step_slices=None, log2_batch=0),
+    "c2": dict(step_slices=None, log2_batch=0),
+    "c3": dict(step_slices=None, log2_batch=0),
+    # 2^20+ slices: one seeded aligned block of 1024 slices per step; every slice
+    # has the same cost, so the full task's time is T_block * 2^S / 1024
+    "c5": dict(step_slices=1024, log2_batch=10, trials=128, arena_gib=160),
+}
+
 
 # ------------------------------------------------------------------ multi-process helpers
 def dist_env():
@@ -267,6 +277,92 @@ def pair_bench(args) -> int:
     return 0
 
 
+# ------------------------------------------------------------------ kernel sweep
+def _event_ms(fn, reps, flush, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def sweep_bench(args) -> int:
+    """Kernel sweep: every (m, k, n) in {2^4, 2^6, ..., 2^14}^3 whose operands stay
+    within 2^30 complex elements, in FP32, TF32 and BF16x3 (A stored [k, m] so
+    tensor-core runs fetch it by TMA), or random permutations of rank 20..30
+    (8 seeded permutations per rank plus the full reversal).  One JSON line per
+    case goes to --sweep-out; stdout gets a summary line."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2111_01066_gb300 import tn
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    peaks = load_peaks()
+    rows = []
+    if args.sweep == "gemm":
+        sizes = [4, 6, 8, 10, 12, 14]
+        for m in sizes:
+            for k in sizes:
+                for n in sizes:
+                    if m + k > 30 or k + n > 30 or m + n > 30:
+                        continue
+                    mw, kw, nw = list(range(m)), list(range(m, m + k)), list(range(m + k, m + k + n))
+                    a = torch.randn(2 ** (m + k), dtype=torch.complex64, device=dev)
+                    b = torch.randn(2 ** (k + n), dtype=torch.complex64, device=dev)
+                    c = torch.empty(2 ** (m + n), dtype=torch.complex64, device=dev)
+                    for prec in ("fp32", "tf32", "bf16x3"):
+                        fn = lambda: tn.contract_pair(a, kw + mw, b, kw + nw, c, mw + nw, precision=prec,
+                                                      stream=stream)
+                        ms = _event_ms(fn, 2, flush, stream)
+                        kern = {"fp32": "simt", "tf32": "tc_tf32", "bf16x3": "tc_bf16x3"}[prec]
+                        if prec != "fp32" and (m + k + n < 20 or m < 4):
+                            kern = "simt"
+                        r = step_roofline((m, k, n, 0), ms, kern, peaks)
+                        rows.append({"case": "gemm", "mkn_log2": [m, k, n], "precision": prec, "ms": ms,
+                                     "complex_tflops": 8.0 * 2 ** (m + k + n) / ms / 1e9, "bound": r["bound"],
+                                     "frac": r["frac"], "kernel": kern})
+                    del a, b, c
+    else:
+        rng = np.random.default_rng(4)
+        for rank in (20, 22, 24, 26, 28, 30):
+            x = torch.randn(2 ** rank, dtype=torch.complex64, device=dev)
+            y = torch.empty_like(x)
+            perms = [list(rng.permutation(rank)) for _ in range(8)] + [list(range(rank - 1, -1, -1))]
+            for i, perm in enumerate(perms):
+                ms = _event_ms(lambda: tn.permute(x, y, rank, perm, 1, stream), 3, flush, stream)
+                gbs = 16.0 * 2 ** rank / ms / 1e6
+                rows.append({"case": "permute", "rank": rank, "perm": i if i < 8 else "reverse", "ms": ms,
+                             "gbs": gbs, "frac": gbs / peaks["hbm_gbs"]})
+            del x, y
+    if args.sweep_out:
+        with open(args.sweep_out, "w") as f:
+            for r in rows:
+                f.write(json.dumps(r) + "\n")
+    fr = [r["frac"] for r in rows]
+    summ = {"metric": f"{args.sweep}_sweep", "cases": len(rows), "frac_median": statistics.median(fr),
+            "frac_min": min(fr), "frac_max": max(fr)}
+    if args.sweep == "gemm":
+        for prec in ("fp32", "tf32", "bf16x3"):
+            big = [r for r in rows if r["precision"] == prec and sum(r["mkn_log2"]) >= 30]
+            if big:
+                summ[f"{prec}_median_frac_large"] = statistics.median(r["frac"] for r in big)
+                summ[f"{prec}_max_tflops"] = max(r["complex_tflops"] for r in big)
+    print(json.dumps(summ))
+    return 0
+
+
 # ------------------------------------------------------------------ main
 def main() -> int:
     ap = argparse.ArgumentParser()
@@ -278,14 +374,20 @@ def main() -> int:
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--compare-fp32", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--autotune", type=int, default=1, help="tune kernels per step before timing")
     ap.add_argument("--pair", default=None,
                     help="log2 m,k,n[,batch]: time one pairwise contraction (tn_contract_pair) instead")
+    ap.add_argument("--sweep", default=None, choices=["gemm", "permute"],
+                    help="kernel sweep: complex GEMMs m,k,n in 2^4..2^14 (3 precisions) or rank-20..30 permutations")
+    ap.add_argument("--sweep-out", default=None, help="file for the sweep's per-case JSON lines")
     ap.add_argument("--layout", default="random", choices=["random", "kfast", "mfast"],
                     help="storage order of A in --pair mode: seeded random, contracted wires lowest, "
                          "free wires lowest")
     args = ap.parse_args()
     if args.pair:
         return pair_bench(args)
+    if args.sweep:
+        return sweep_bench(args)
     rank, world, local = dist_env()
     name = args.workload
     cfg = rqcgen.CONFIGS[name]
@@ -334,12 +436,21 @@ def main() -> int:
     prec = args.precision if args.precision != "auto" else "bf16x3"
     bits = batch_bits_for_rank(name, rank)
     net = tn.Network(circ)
-    plan_kw = dict(open_mask=om, max_log2_intermediate=cfg["log2_bound"], min_log2_slices=cfg["log2_slices"])
+    run = WORKLOAD_RUN[name]
+    plan_kw = dict(open_mask=om, max_log2_intermediate=cfg["log2_bound"], min_log2_slices=cfg["log2_slices"],
+                   log2_batch_slices=run["log2_batch"], trials=run.get("trials", 64),
+                   max_arena_bytes=int(run.get("arena_gib", 96)) << 30)
     t_plan = time.time()
     plan = tn.Plan(net, precision=prec, **plan_kw)
     t_plan = time.time() - t_plan
     info = plan.info()
-    n_slices = 1 << info["log2_slices"]
+    all_slices = 1 << info["log2_slices"]
+    n_slices = all_slices if run["step_slices"] is None else min(all_slices, run["step_slices"])
+    first = 0
+    if n_slices < all_slices:
+        import numpy as _np
+        blocks = all_slices // n_slices
+        first = int(_np.random.default_rng([cfg["seed"], 13]).integers(blocks)) * n_slices
     k_open = info["n_open"]
     n_chunks = max(1, n_slices >> info["log2_batch_slices"])
     out = torch.zeros(2 << k_open, dtype=torch.float64, device=dev)
@@ -348,7 +459,7 @@ def main() -> int:
 
     def step(p, o):
         o.zero_()
-        p.contract_slices(0, n_slices, [bits], o, stream)
+        p.contract_slices(first, n_slices, [bits], o, stream)
         return tn.xeb(o.view(torch.complex128), circ.n_qubits, stream)
 
     def timed(p, o, k, w):
@@ -368,9 +479,15 @@ def main() -> int:
             times.append(e0.elapsed_time(e1))
         return times
 
-    # untimed first call: device state + warm-up
+    # untimed first call: device state + warm-up; then the per-step autotuner
     step(plan, out)
     torch.cuda.synchronize()
+    t_tune = time.time()
+    if args.autotune:
+        plan.autotune(reps=2, stream=stream)
+        step(plan, out)
+        torch.cuda.synchronize()
+    t_tune = time.time() - t_tune
     barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
@@ -391,7 +508,7 @@ def main() -> int:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out.zero_()
-        plan.contract_slices(0, n_slices, [bits], out, stream)
+        plan.contract_slices(first, n_slices, [bits], out, stream)
         host_amps.copy_(out, non_blocking=True)
         tn.xeb(out.view(torch.complex128), circ.n_qubits, stream)
         torch.cuda.synchronize()
@@ -408,7 +525,7 @@ def main() -> int:
         gold = read(name)
 
     def amp_error(o):
-        if gold is None or gold.size != (o.numel() // 2):
+        if gold is None or gold.size != (o.numel() // 2) or n_slices != all_slices:
             return None
         from oracle import xeb as oxeb
         got = o.cpu().numpy().view(np.complex128)
@@ -423,6 +540,10 @@ def main() -> int:
             p2 = tn.Plan(net, precision=other, **plan_kw)
             o2 = torch.zeros_like(out)
             step(p2, o2)
+            if args.autotune:
+                p2.autotune(reps=1, stream=stream)
+                o2.zero_()
+                step(p2, o2)
             t2 = timed(p2, o2, min(3, args.steps), 1)
             ms2 = max_over_ranks(statistics.mean(t2), world, dev)
             others[other] = {"value": total_units / (ms2 / 1e3), "ms_per_step": ms2,
@@ -470,7 +591,8 @@ def main() -> int:
                                    f"{cfg['cycles']} cycles, 2^{info['log2_slices']} slices (<=2^"
                                    f"{cfg['log2_bound']} per slice), {k_open} open qubits",
                        "precision": prec, "complex_mult": info["complex_mult"],
-                       "slices_per_step": n_slices, "chunks_per_step": n_chunks,
+                       "slices_per_step": n_slices, "chunks_per_step": n_chunks, "slice_first": first,
+                       "slices_total": all_slices,
                        "log2_batch_slices": info["log2_batch_slices"], "l2": "flushed between steps "
                        "(512 MiB write); intermediates also exceed L2"},
             "complex_tflops": info["flops_per_chunk"] * n_chunks * world / (ms_max / 1e3) / 1e12,
@@ -478,7 +600,8 @@ def main() -> int:
             "plan": {"flops_per_slice": info["flops_per_slice"], "flops_per_chunk": info["flops_per_chunk"],
                      "bytes_per_chunk": info["bytes_per_chunk"], "n_steps": info["n_steps"],
                      "log2_max_intermediate": info["log2_max_intermediate"], "arena_gib": info["arena_bytes"] / 2**30,
-                     "plan_seconds": t_plan},
+                     "plan_seconds": t_plan, "autotune_seconds": t_tune if args.autotune else None},
+            "extrapolated_full_task_s": all_slices / value * world if n_slices < all_slices else None,
             "fp32_path": fp32,
             "tf32_path": others.get("tf32"),
             "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,

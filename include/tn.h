@@ -108,15 +108,21 @@ typedef struct tn_plan_opts {
     uint64_t seed;                   /* seeds the randomised order search */
     int32_t  trials;                 /* order-search trials (<= 0: default) */
     int32_t  precision;              /* TN_PREC_* */
-    int32_t  complex_mult;           /* 4 (4M) or 3 (3M) real products per complex product */
+    int32_t  complex_mult;           /* 4 (4M); 3 (3M) is reserved: TN_ERR_UNSUPPORTED in this build */
     int32_t  log2_batch_slices;      /* slices contracted together per chunk (<= 0: auto) */
     int64_t  max_arena_bytes;        /* device arena cap for one chunk (<= 0: 96 GiB) */
     int32_t  fuse_permute;           /* 1: permutes folded into operand gathers; 0: explicit permute pass */
-    int32_t  reserved;
+    int32_t  n_forced_slices;        /* wires the caller slices (0: the planner chooses them all) */
+    const int32_t* forced_slice_qubit;  /* [n_forced_slices]: wire (qubit, t) of slice bit j, host */
+    const int32_t* forced_slice_t;      /* internal wires only: 1 <= t < gates on that qubit */
 } tn_plan_opts;
 
 /* Fill opts with defaults: no open qubits, bound 2^30, no forced slices, seed 1,
- * 64 trials, FP32, 4M, automatic batch, 96 GiB arena, fused permutes. */
+ * 64 trials, FP32, 4M, automatic batch, 96 GiB arena, fused permutes.
+ * Forced slices: the given wires take slice bits 0..n_forced_slices-1 (in the
+ * given order) and the planner orders the rest of the network around them,
+ * adding further slices only if the bound needs them; chunks then hold one
+ * slice each.  TN_ERR_ARG for a wire that is not an internal wire. */
 tn_status tn_plan_default_opts(tn_plan_opts* opts);
 
 /* Find a contraction order and a slice set (SI, TN section: pairwise order as
@@ -189,6 +195,14 @@ tn_status tn_contract_slices(tn_plan_t* plan, uint64_t slice_first, uint64_t sli
 tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int32_t* kernel_out,
                              void* stream);
 
+/* Autotuner (after one tn_contract_slices call): times candidate kernels for
+ * every step in place on `stream` -- tensor-core tiles of 32, 64 or 128
+ * complex columns in the TF32 / BF16X3 modes, and the three CUDA-core tilings
+ * for steps under 50 us or in the FP32 mode -- each `reps` times, and keeps the
+ * fastest for later calls.  Synchronises `stream`; the arena contents are
+ * overwritten (the next call recomputes them). */
+tn_status tn_plan_autotune(tn_plan_t* plan, int32_t reps, void* stream);
+
 /* Wait for the plan's work on `stream` and return its sticky device error, if any. */
 tn_status tn_plan_sync(tn_plan_t* plan, void* stream);
 
@@ -224,6 +238,15 @@ tn_status tn_contract_pair(const float* a, const int32_t* a_wires, int32_t a_ran
                            float* c, const int32_t* c_wires, int32_t c_rank,
                            int64_t batch, int32_t precision, int32_t complex_mult,
                            void* stream);
+
+/* Self-test of the bounded device waits that every tensor-core kernel uses:
+ * launches one thread that waits on an mbarrier nothing ever arrives on, with
+ * a limit of wait_ms milliseconds (1..5000), and writes the device error word
+ * the kernel left into *device_status: TN_ERR_TIMEOUT when the wait gave up as
+ * designed.  The kernel returns normally and the context stays usable.  The
+ * paper has no counterpart (failure handling of this implementation).
+ * Synchronises `stream`. */
+tn_status tn_selftest_bounded_wait(int32_t wait_ms, int32_t* device_status, void* stream);
 
 /* tn_contract_pair without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device

@@ -117,10 +117,17 @@ __global__ void k_xeb_sum(const double2* __restrict__ a, int64_t n, double* __re
 
 struct PermArgs {
   int8_t src_pos[KMAXR];  // output bit p <- input bit src_pos[p]
+  // tiled variant: the tile's bits (input positions), in input order; for each
+  // tile bit its output position; the non-tile bits (input order) and theirs
+  int32_t nt;             // tile bits (<= 10)
+  int8_t t_in[10], t_out[10];
+  int32_t nr;             // remaining bits
+  int8_t r_in[KMAXR], r_out[KMAXR];
+  int32_t t_out_order[10];  // tile bits sorted by output position (indices into t_*)
 };
 
 // Standalone permutation: one thread per output element (coalesced writes,
-// gathered reads), used by tn_permute and the unfused path.
+// gathered reads); used for small ranks.
 __global__ void k_permute_gather(const float2* __restrict__ in, float2* __restrict__ out, int rank,
                                  const PermArgs pa, int64_t total) {
   const int64_t mask = ((int64_t)1 << rank) - 1;
@@ -131,6 +138,47 @@ __global__ void k_permute_gather(const float2* __restrict__ in, float2* __restri
     for (int p = 0; p < rank; ++p)
       if ((o >> p) & 1) src |= (int64_t)1 << pa.src_pos[p];
     out[idx] = __ldg(in + (idx - o) + src);
+  }
+}
+
+// Tiled permutation (SI Eq. (2) as a standalone pass): a tile holds every
+// combination of the input's 5 lowest bits and of the input bits that feed the
+// output's 5 lowest positions (<= 10 bits, <= 1024 complex).  Threads read the
+// tile in input order (contiguous runs) into shared memory and write it back in
+// output order (contiguous runs); the remaining bits select the tile.
+__global__ void __launch_bounds__(256) k_permute_tiled(const float2* __restrict__ in, float2* __restrict__ out,
+                                                       int rank, const PermArgs pa, int64_t n_tiles_per_inst,
+                                                       int64_t n_inst) {
+  __shared__ float2 tile[1024];
+  const int tsz = 1 << pa.nt;
+  for (int64_t t = blockIdx.x; t < n_tiles_per_inst * n_inst; t += gridDim.x) {
+    const int64_t inst = t / n_tiles_per_inst;
+    const int64_t r = t % n_tiles_per_inst;
+    int64_t ib = inst << rank, ob = inst << rank;
+    for (int q = 0; q < pa.nr; ++q)
+      if ((r >> q) & 1) {
+        ib += (int64_t)1 << pa.r_in[q];
+        ob += (int64_t)1 << pa.r_out[q];
+      }
+    for (int e = threadIdx.x; e < tsz; e += blockDim.x) {   // e: tile bits in input order
+      int64_t off = 0;
+      for (int q = 0; q < pa.nt; ++q)
+        if ((e >> q) & 1) off += (int64_t)1 << pa.t_in[q];
+      tile[e] = __ldg(in + ib + off);
+    }
+    __syncthreads();
+    for (int f = threadIdx.x; f < tsz; f += blockDim.x) {   // f: tile bits in output order
+      int e = 0;
+      int64_t off = 0;
+      for (int q = 0; q < pa.nt; ++q)
+        if ((f >> q) & 1) {
+          const int i = pa.t_out_order[q];
+          e |= 1 << i;
+          off += (int64_t)1 << pa.t_out[i];
+        }
+      out[ob + off] = tile[e];
+    }
+    __syncthreads();
   }
 }
 

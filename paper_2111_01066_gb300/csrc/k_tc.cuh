@@ -137,20 +137,35 @@ __device__ __forceinline__ uint64_t gtimer() {
   return t;
 }
 // Bounded wait: true when the phase completed, false on abort or deadline.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
-                                          int32_t* err) {
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int32_t* err,
+                                          uint64_t limit_ns = TC_WAIT_NS) {
   if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = gtimer();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(a, parity)) return true;
     if ((i & 255) == 0) {
       if (*abort_flag) return false;
-      if (gtimer() - t0 > TC_WAIT_NS) {
+      if (gtimer() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicExch(err, TN_ERR_TIMEOUT);
         return false;
       }
     }
+  }
+}
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// ever arrives on; the wait must give up after limit_ns and record the timeout.
+__global__ void k_selftest_wait(int32_t* err, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = mbar_wait(smem_u32(&bar), 0, &abort_flag, err, limit_ns);
+    if (ok) atomicExch(err, 1);
   }
 }
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t bytes) {

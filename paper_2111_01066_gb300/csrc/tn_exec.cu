@@ -59,7 +59,7 @@ static int sm_count() {
 // Tile decode tables: the tile's bits in ascending memory position.
 static GemmArgs make_args(const StepDesc& d, int kid, const float2* A, const float2* B, float2* C,
                           int32_t n_inst, int64_t a_istride = 0, int64_t b_istride = 0,
-                          int64_t c_istride = 0) {
+                          int64_t c_istride = 0, int tn_log = -1) {
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   g.A = A;
@@ -79,7 +79,7 @@ static GemmArgs make_args(const StepDesc& d, int kid, const float2* A, const flo
   const KernelCfg& k = kCfg[kid];
   g.tm = std::min(k.tm, d.nm);
   g.tk = std::min(k.tk, d.nk);
-  g.tn = std::min(k.tn, d.nn);
+  g.tn = std::min(tn_log >= 0 ? tn_log : k.tn, d.nn);
   std::memcpy(g.a_mpos, d.a_mpos, KMAXR);
   std::memcpy(g.a_kpos, d.a_kpos, KMAXR);
   std::memcpy(g.b_kpos, d.b_kpos, KMAXR);
@@ -544,6 +544,88 @@ extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_o
   API_END
 }
 
+// Autotuner: for every step, time the candidate kernels in place (tensor-core
+// tiles of 32, 64 or 128 complex columns in the TF32 / BF16X3 modes, and the
+// three CUDA-core tilings where the step is small or the mode is FP32) and keep
+// the fastest.  The chunk graph is captured again on the next call.
+extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) {
+  API_BEGIN
+  if (!h) fail(TN_ERR_ARG, "tn_plan_autotune: NULL plan");
+  if (reps < 1) fail(TN_ERR_ARG, "tn_plan_autotune: reps must be >= 1");
+  Plan& p = h->plan;
+  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_autotune: run tn_contract_slices first");
+  DeviceState& ds = *p.dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ds.have_done) CK(cudaStreamWaitEvent(s, ds.done, 0));
+  CK(cudaStreamSynchronize(s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int64_t ws_cap = 0;
+  for (const StepLaunch& L : ds.launches) ws_cap = std::max(ws_cap, L.ws_bytes);
+  auto time_launch = [&](StepLaunch& L) -> double {
+    if (L.ws_bytes > ws_cap) {
+      CK(cudaStreamSynchronize(s));
+      CK(cudaFree(ds.ws));
+      ds.ws = nullptr;
+      if (cudaMalloc(&ds.ws, (size_t)L.ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        fail(TN_ERR_OOM, "autotune workspace allocation failed");
+      }
+      ws_cap = L.ws_bytes;
+    }
+    launch_step(L, ds.ws, ds.err, s);  // warm-up
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) launch_step(L, ds.ws, ds.err, s);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    return (double)ms / reps;
+  };
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    const StepDesc& d = p.steps[i];
+    auto build = [&](int kid, int tn_log) {
+      return make_launch(make_args(d, kid, ds.arena + d.a_off, ds.arena + d.b_off, ds.arena + d.c_off, 1 << d.nb,
+                                   0, 0, 0, tn_log),
+                         kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1);
+    };
+    double best = time_launch(ds.launches[i]);
+    std::vector<std::pair<int, int>> cands;
+    const bool tc_mode = p.opts.precision == TN_PREC_TF32 || p.opts.precision == TN_PREC_BF16X3;
+    const int tc_kid = p.opts.precision == TN_PREC_TF32 ? K_TC_TF32 : K_TC_BF16X3;
+    if (tc_mode && d.nm >= 4)
+      for (int tn_log : {7, 6, 5})
+        if (tn_log <= std::max(3, d.nn)) cands.push_back({tc_kid, tn_log});
+    // CUDA-core tilings: FP32 mode, tiny steps, and low arithmetic intensity
+    // (complex flops per byte moved), where a tile's fixed cost on the tensor
+    // cores outweighs its few products
+    const double flops = 8.0 * std::ldexp(1.0, d.nm + d.nk + d.nn + d.nb);
+    const double bytes = 8.0 * (double)(d.a_elems + d.b_elems + d.c_elems);
+    if (!tc_mode || best < 0.05 || flops / bytes < 48.0)
+      for (int k : {K_SIMT_64x64, K_SIMT_128x16, K_SIMT_256x4}) cands.push_back({k, -1});
+    for (auto [kid, tn_log] : cands) {
+      if (kid == ds.launches[i].kid && (tn_log < 0 || std::min(tn_log, d.nn) == ds.launches[i].g.tn)) continue;
+      StepLaunch L = build(kid, tn_log);
+      const double t = time_launch(L);
+      if (t < best * 0.97) {
+        best = t;
+        ds.launches[i] = L;
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ds.graph) {
+    cudaGraphExecDestroy(ds.graph);
+    ds.graph = nullptr;
+  }
+  ds.graph_failed = false;
+  ds.eager_done = false;
+  API_END
+}
+
 extern "C" tn_status tn_plan_sync(tn_plan_t* h, void* stream) {
   API_BEGIN
   if (!h) fail(TN_ERR_ARG, "tn_plan_sync: NULL plan");
@@ -623,9 +705,40 @@ extern "C" tn_status tn_permute(const float* in, float* out, int32_t rank, const
   }
   const int64_t total = batch << rank;
   if (total == 0) return TN_OK;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
-  k_permute_gather<<<blocks, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(in),
-                                                             reinterpret_cast<float2*>(out), rank, pa, total);
+  if (rank < 10) {
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
+    k_permute_gather<<<blocks, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(in),
+                                                               reinterpret_cast<float2*>(out), rank, pa, total);
+  } else {
+    // tile bits: input positions 0..4 and the inputs of output positions 0..4
+    std::vector<int> out_of_in(rank);
+    for (int p = 0; p < rank; ++p) out_of_in[perm[p]] = p;
+    std::vector<char> in_tile(rank, 0);
+    for (int i = 0; i < 5; ++i) in_tile[i] = 1;
+    for (int p = 0; p < 5; ++p) in_tile[perm[p]] = 1;
+    pa.nt = 0;
+    pa.nr = 0;
+    for (int i = 0; i < rank; ++i) {
+      if (in_tile[i]) {
+        pa.t_in[pa.nt] = (int8_t)i;
+        pa.t_out[pa.nt] = (int8_t)out_of_in[i];
+        ++pa.nt;
+      } else {
+        pa.r_in[pa.nr] = (int8_t)i;
+        pa.r_out[pa.nr] = (int8_t)out_of_in[i];
+        ++pa.nr;
+      }
+    }
+    std::vector<int> ord(pa.nt);
+    for (int q = 0; q < pa.nt; ++q) ord[q] = q;
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return pa.t_out[x] < pa.t_out[y]; });
+    for (int q = 0; q < pa.nt; ++q) pa.t_out_order[q] = ord[q];
+    const int64_t tiles = (int64_t)1 << pa.nr;
+    const int blocks = (int)std::min<int64_t>(tiles * batch, 152 * 16);
+    k_permute_tiled<<<blocks, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(in),
+                                                              reinterpret_cast<float2*>(out), rank, pa, tiles,
+                                                              batch);
+  }
   CK(cudaGetLastError());
   API_END
 }
@@ -640,6 +753,7 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   if (batch < 1 || batch > 65535) fail(TN_ERR_ARG, "tn_contract_pair: batch must be in [1, 65535]");
   if (precision < TN_PREC_FP32 || precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
   if (cmult != 3 && cmult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
+  if (cmult == 3) fail(TN_ERR_UNSUPPORTED, "3M complex products are not built; use complex_mult = 4");
   std::vector<int> A(aw, aw + ar), B(bw, bw + br), Cw(cw, cw + cr);
   auto has = [](const std::vector<int>& v, int w) { return std::find(v.begin(), v.end(), w) != v.end(); };
   for (size_t i = 0; i < A.size(); ++i)
@@ -693,6 +807,23 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   }
   launch_step(L, sc.ws, sc.err, (cudaStream_t)stream);
   CK(cudaGetLastError());
+  API_END
+}
+
+extern "C" tn_status tn_selftest_bounded_wait(int32_t wait_ms, int32_t* device_status, void* stream) {
+  API_BEGIN
+  if (!device_status) fail(TN_ERR_ARG, "tn_selftest_bounded_wait: NULL argument");
+  if (wait_ms < 1 || wait_ms > 5000) fail(TN_ERR_ARG, "tn_selftest_bounded_wait: wait_ms must be in [1, 5000]");
+  Scratch& sc = scratch_for_device();
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(sc.err, 0, sizeof(int32_t), s));
+  k_selftest_wait<<<1, 32, 0, s>>>(sc.err, (uint64_t)wait_ms * 1000000ull);
+  CK(cudaGetLastError());
+  int32_t e = 0;
+  CK(cudaMemcpyAsync(&e, sc.err, sizeof(e), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemsetAsync(sc.err, 0, sizeof(int32_t), s));
+  *device_status = e;
   API_END
 }
 

@@ -31,7 +31,8 @@ struct HTensor {
   int rank() const { return (int)wires.size(); }
 };
 
-HTensor hcontract(const HTensor& a, const HTensor& b);       // sum over shared wires
+HTensor hcontract(const HTensor& a, const HTensor& b,
+                  const std::vector<char>* keep = nullptr);  // sum over shared wires not in keep
 HTensor hfix(const HTensor& t, int wire, int value);        // index one wire at a value
 HTensor hpermute(const HTensor& t, const std::vector<int>& order);  // new wire order
 

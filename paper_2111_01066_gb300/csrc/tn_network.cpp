@@ -24,16 +24,19 @@ static inline uint64_t deposit(uint64_t x, const std::vector<int>& pos) {
   return r;
 }
 
-HTensor hcontract(const HTensor& a, const HTensor& b) {
-  std::vector<int> shared, afree, bfree;           // positions
-  std::vector<int> sh_a, sh_b, fa_pos, fb_pos;
+HTensor hcontract(const HTensor& a, const HTensor& b, const std::vector<char>* keep) {
+  // shared wires are summed, except those marked in `keep`, which stay as one
+  // index of the result with both operands taken at the same value (diagonal)
+  std::vector<int> sh_a, sh_b, fa_pos, fb_pos, kb_of_fa;
   for (int i = 0; i < a.rank(); ++i) {
     auto it = std::find(b.wires.begin(), b.wires.end(), a.wires[i]);
-    if (it != b.wires.end()) {
+    const bool kept = keep && (*keep)[a.wires[i]];
+    if (it != b.wires.end() && !kept) {
       sh_a.push_back(i);
       sh_b.push_back(int(it - b.wires.begin()));
     } else {
       fa_pos.push_back(i);
+      kb_of_fa.push_back(it != b.wires.end() ? int(it - b.wires.begin()) : -1);
     }
   }
   for (int j = 0; j < b.rank(); ++j)
@@ -46,16 +49,19 @@ HTensor hcontract(const HTensor& a, const HTensor& b) {
   const uint64_t nsh = uint64_t(1) << sh_a.size();
   c.data.assign(nfa * nfb, cd(0, 0));
   std::vector<uint64_t> sa(nsh), sb(nsh);
-  for (uint64_t s = 0; s < nsh; ++s) {
-    sa[s] = deposit(s, sh_a);
-    sb[s] = deposit(s, sh_b);
+  for (uint64_t s2 = 0; s2 < nsh; ++s2) {
+    sa[s2] = deposit(s2, sh_a);
+    sb[s2] = deposit(s2, sh_b);
   }
   for (uint64_t j = 0; j < nfb; ++j) {
     const uint64_t bj = deposit(j, fb_pos);
     for (uint64_t i = 0; i < nfa; ++i) {
       const uint64_t ai = deposit(i, fa_pos);
+      uint64_t bk = 0;   // kept wires: B takes the value A's index carries
+      for (size_t t = 0; t < fa_pos.size(); ++t)
+        if (kb_of_fa[t] >= 0 && ((i >> t) & 1)) bk |= uint64_t(1) << kb_of_fa[t];
       cd acc(0, 0);
-      for (uint64_t s = 0; s < nsh; ++s) acc += a.data[ai | sa[s]] * b.data[bj | sb[s]];
+      for (uint64_t s2 = 0; s2 < nsh; ++s2) acc += a.data[ai | sa[s2]] * b.data[bj | bk | sb[s2]];
       c.data[i + nfa * j] = acc;
     }
   }

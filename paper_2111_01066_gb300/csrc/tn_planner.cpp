@@ -37,7 +37,7 @@ struct Simplified {
   std::vector<char> fixed;       // per network wire id
 };
 
-Simplified simplify(const Network& net, uint64_t open_mask) {
+Simplified simplify(const Network& net, uint64_t open_mask, const std::vector<int>& forced) {
   Simplified out;
   const int n = net.n_qubits;
   const int nw = (int)net.labels.size();
@@ -61,6 +61,8 @@ Simplified simplify(const Network& net, uint64_t open_mask) {
   out.fixed.assign(nw, 0);
   for (int q = 0; q < n; ++q)
     if (!((open_mask >> q) & 1)) out.fixed[net.output_wire[q]] = 1;
+  // caller-sliced wires are fixed per slice: kept as leaf indices, never planned
+  for (int w : forced) out.fixed[w] = 1;
   auto prank = [&](const HTensor& t) {
     int r = 0;
     for (int w : t.wires) r += !out.fixed[w];
@@ -101,7 +103,7 @@ Simplified simplify(const Network& net, uint64_t open_mask) {
           }
         if (best < 0) continue;
       }
-      ts[best] = hcontract(ts[best], ts[i]);
+      ts[best] = hcontract(ts[best], ts[i], &out.fixed);
       alive[i] = 0;
       changed = true;
       own = owners();
@@ -124,7 +126,7 @@ Simplified simplify(const Network& net, uint64_t open_mask) {
       }
       const int rc = (int)uni.size() - shared;
       if (rc <= std::max(prank(ts[a]), prank(ts[b]))) {
-        ts[a] = hcontract(ts[a], ts[b]);
+        ts[a] = hcontract(ts[a], ts[b], &out.fixed);
         alive[b] = 0;
         changed = true;
         own = owners();
@@ -531,6 +533,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
     fail(TN_ERR_ARG, "max_log2_intermediate must be in [1, 36]");
   if (o.precision < TN_PREC_FP32 || o.precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
   if (o.complex_mult != 3 && o.complex_mult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
+  if (o.complex_mult == 3) fail(TN_ERR_UNSUPPORTED, "3M complex products are not built; use complex_mult = 4");
   if (o.min_log2_slices < 0 || o.min_log2_slices > 48) fail(TN_ERR_ARG, "min_log2_slices out of range");
   const int n = net.n_qubits;
   if (n < 64 && (o.open_mask >> n) != 0) fail(TN_ERR_ARG, "open_mask names a qubit >= n_qubits");
@@ -544,7 +547,26 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   if (k_open > o.max_log2_intermediate) fail(TN_ERR_PLAN, "open qubits alone exceed the bound");
   if (k_open > 30) fail(TN_ERR_UNSUPPORTED, "more than 30 open qubits");
 
-  Simplified S = simplify(net, o.open_mask);
+  // caller-chosen slices: internal wires (q, t), 1 <= t < gates on q
+  std::vector<int> forced;
+  std::vector<int> forced_bit(net.labels.size(), -1);
+  if (o.n_forced_slices < 0 || o.n_forced_slices > 48) fail(TN_ERR_ARG, "n_forced_slices out of range");
+  if (o.n_forced_slices > 0 && (!o.forced_slice_qubit || !o.forced_slice_t))
+    fail(TN_ERR_ARG, "forced slice arrays are NULL");
+  for (int j = 0; j < o.n_forced_slices; ++j) {
+    const int q = o.forced_slice_qubit[j], t = o.forced_slice_t[j];
+    if (q < 0 || q >= n || t < 1 || t >= net.gates_per_qubit[q])
+      fail(TN_ERR_ARG, "forced slice (" + std::to_string(q) + ", " + std::to_string(t) + ") is not an internal wire");
+    int w = -1;
+    for (size_t i = 0; i < net.labels.size(); ++i)
+      if (net.labels[i].q == q && net.labels[i].t == t) w = (int)i;
+    if (w < 0 || forced_bit[w] >= 0) fail(TN_ERR_ARG, "forced slice wire missing or repeated");
+    forced_bit[w] = j;
+    forced.push_back(w);
+    P->sliced.push_back(net.labels[w]);
+  }
+  const int nF = (int)forced.size();
+  Simplified S = simplify(net, o.open_mask, forced);
   const int L = (int)S.leaves.size();
   P->n_leaves = L;
 
@@ -681,7 +703,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
     for (int w : rest) order_sl.push_back(w);
   }
   std::vector<int> slice_bit(W, -1);
-  for (int j = 0; j < nS; ++j) slice_bit[order_sl[j]] = j;
+  for (int j = 0; j < nS; ++j) slice_bit[order_sl[j]] = nF + j;
   for (int j = 0; j < nS; ++j) P->sliced.push_back(net.labels[wire_of_pw[order_sl[j]]]);
 
   // ------------------------------------------------ step program for a given b
@@ -875,6 +897,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   std::vector<StepDesc> steps;
   int64_t arena = 0;
   int b = o.log2_batch_slices > 0 ? std::min(o.log2_batch_slices, std::min(nS, 12)) : std::min(nS, 12);
+  if (nF > 0) b = 0;   // caller-sliced plans contract one slice per chunk
   while (true) {
     const bool ok = layout(b, info, steps, arena);
     if (ok) break;
@@ -901,7 +924,13 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       idx.push_back(j);
     }
     for (int w : lf.wires)
-      if (S.fixed[w]) {
+      if (S.fixed[w] && forced_bit[w] >= 0) {
+        ord.push_back(w);
+        kind.push_back(0);
+        idx.push_back(forced_bit[w]);
+      }
+    for (int w : lf.wires)
+      if (S.fixed[w] && forced_bit[w] < 0) {
         ord.push_back(w);
         kind.push_back(1);
         idx.push_back(net.labels[w].q);

@@ -49,7 +49,9 @@ class tn_plan_opts(ctypes.Structure):
                 ("trials", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("complex_mult", ctypes.c_int32), ("log2_batch_slices", ctypes.c_int32),
                 ("max_arena_bytes", ctypes.c_int64), ("fuse_permute", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("n_forced_slices", ctypes.c_int32),
+                ("forced_slice_qubit", ctypes.POINTER(ctypes.c_int32)),
+                ("forced_slice_t", ctypes.POINTER(ctypes.c_int32))]
 
 
 class tn_plan_stats(ctypes.Structure):
@@ -80,6 +82,7 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p]),
     "tn_plan_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tn_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "tn_plan_step_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "tn_plan_destroy": (None, [ctypes.c_void_p]),
@@ -91,6 +94,7 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                         ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "tn_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "tn_contract_pair_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
@@ -178,7 +182,8 @@ class Plan:
     def __init__(self, network: Network, open_mask: int = 0, max_log2_intermediate: int = 30,
                  min_log2_slices: int = 0, precision: str = "fp32", complex_mult: int = 4,
                  seed: int = 1, trials: int = 64, log2_batch_slices: int = 0,
-                 max_arena_bytes: int = 0, fuse_permute: int = 1):
+                 max_arena_bytes: int = 0, fuse_permute: int = 1,
+                 forced_slices: Sequence[Tuple[int, int]] = ()):
         lib = load()
         o = default_opts()
         o.open_mask = open_mask
@@ -192,6 +197,11 @@ class Plan:
         if max_arena_bytes:
             o.max_arena_bytes = max_arena_bytes
         o.fuse_permute = fuse_permute
+        fq = _i32([q for q, _ in forced_slices])
+        ft = _i32([t for _, t in forced_slices])
+        o.n_forced_slices = len(forced_slices)
+        o.forced_slice_qubit = ctypes.cast(fq, ctypes.POINTER(ctypes.c_int32))
+        o.forced_slice_t = ctypes.cast(ft, ctypes.POINTER(ctypes.c_int32))
         h = ctypes.c_void_p()
         _check(lib.tn_plan(network.handle, ctypes.byref(o), ctypes.byref(h)))
         self.handle = h
@@ -240,6 +250,10 @@ class Plan:
         _check(load().tn_plan_step_times(self.handle, reps, arr, kid, _stream_handle(stream)))
         return [(arr[i], self.KERNELS.get(kid[i], str(kid[i]))) for i in range(n)]
 
+    def autotune(self, reps: int = 2, stream=None) -> None:
+        """Pick the fastest kernel / tile for every step by timing (tn_plan_autotune)."""
+        _check(load().tn_plan_autotune(self.handle, reps, _stream_handle(stream)))
+
     def sync(self, stream=None) -> None:
         _check(load().tn_plan_sync(self.handle, _stream_handle(stream)))
 
@@ -255,6 +269,13 @@ def xeb(amplitudes, n_qubits: int, stream=None) -> float:
     _check(load().tn_xeb(ctypes.c_void_p(amplitudes.data_ptr()), amplitudes.numel(), n_qubits,
                          ctypes.byref(f), _stream_handle(stream)))
     return f.value
+
+
+def selftest_bounded_wait(wait_ms: int = 200, stream=None) -> int:
+    """Run the bounded-wait self-test kernel; returns the device status word."""
+    st = ctypes.c_int32()
+    _check(load().tn_selftest_bounded_wait(wait_ms, ctypes.byref(st), _stream_handle(stream)))
+    return st.value
 
 
 def permute(inp, out, rank: int, perm: Sequence[int], batch: int = 1, stream=None) -> None:

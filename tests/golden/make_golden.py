@@ -4,7 +4,7 @@ Calls only `oracle/` (and the seeded generator `rqcgen`).  Output: one text file
 per workload, `<name>_amplitudes.txt`, with a header line and one amplitude per
 line ("re im", 17 significant digits), in the batch order sum_j b(open_j) 2^j.
 
-    python tests/golden/make_golden.py c2
+    python tests/golden/make_golden.py c2 c3 c5
 """
 import os
 import sys
@@ -39,6 +39,38 @@ def write(name: str) -> None:
     print(path, f"{dt:.1f} s")
 
 
+def write_sliced(name: str, n_slices: int) -> None:
+    """A partial sum over slices for networks too large for the whole batch: the
+    oracle slices the wires of its own choice (the extra wires its bisection
+    order needs under a 2^25 bound) and sums slice ids 0..n_slices-1, slice id s
+    setting the j-th wire to bit j of s.  The wire list is written with it so
+    that a test can hand the same slice set to the library."""
+    circ, open_mask, closed = rqcgen.config_circuit(name)
+    net = tensornet.CircuitNetwork(circ, closed, open_mask)
+    t0 = time.time()
+    _, wires = net.plan([], max_log2=25, method="bisect", trials=12, seed=100)
+    amps = net.contract(wires, range(n_slices), max_log2=25, method="bisect", trials=12, seed=100)
+    dt = time.time() - t0
+    path = os.path.join(HERE, f"{name}_slices_amplitudes.txt")
+    with open(path, "w") as f:
+        f.write(f"# {name}: n={circ.n_qubits} open_mask={open_mask:#x} closed={closed:#x} count={amps.size} "
+                f"slices=0..{n_slices - 1} oracle=tensornet complex128 ({dt:.1f} s)\n")
+        f.write("# wires " + " ".join(f"{q},{t}" for q, t in wires) + "\n")
+        for a in amps:
+            f.write(f"{a.real:.17e} {a.imag:.17e}\n")
+    print(path, f"{dt:.1f} s")
+
+
+def read_sliced(name: str):
+    path = os.path.join(HERE, f"{name}_slices_amplitudes.txt")
+    with open(path) as f:
+        head = [f.readline(), f.readline()]
+    wires = [tuple(int(x) for x in w.split(",")) for w in head[1].split()[2:]]
+    n = int(head[0].split("slices=0..")[1].split()[0]) + 1
+    data = np.loadtxt(path, comments="#")
+    return wires, n, data[:, 0] + 1j * data[:, 1]
+
+
 def read(name: str) -> np.ndarray:
     path = os.path.join(HERE, f"{name}_amplitudes.txt")
     data = np.loadtxt(path, comments="#")
@@ -47,4 +79,7 @@ def read(name: str) -> np.ndarray:
 
 if __name__ == "__main__":
     for n in sys.argv[1:] or ["c2"]:
-        write(n)
+        if n == "c5":
+            write_sliced("c5", 2)
+        else:
+            write(n)

@@ -59,6 +59,9 @@ def test_plan_options_validated(tn):
     with pytest.raises(tn.TnError):
         tn.Plan(net, open_mask=om, complex_mult=5)
     with pytest.raises(tn.TnError) as e:
+        tn.Plan(net, open_mask=om, complex_mult=3)
+    assert e.value.status == tn.TN_ERR_UNSUPPORTED
+    with pytest.raises(tn.TnError) as e:
         tn.Plan(net, open_mask=om, max_log2_intermediate=6)   # 12 open qubits > 2^6
     assert e.value.status == tn.TN_ERR_PLAN
 
@@ -108,3 +111,18 @@ def test_plan_is_deterministic(tn):
     a = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3)
     b = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3)
     assert a.step_shapes() == b.step_shapes() and a.sliced_wires() == b.sliced_wires()
+
+
+def test_forced_slices_are_used_and_validated(tn):
+    circ, om, _ = rqcgen.config_circuit("c1")
+    net = tn.Network(circ)
+    forced = [(0, 3), (5, 4), (9, 2), (2, 5)]
+    plan = tn.Plan(net, open_mask=om & 0xF0F, max_log2_intermediate=30, forced_slices=forced, trials=8)
+    sl = plan.sliced_wires()
+    assert sl[:4] == forced
+    assert plan.info()["log2_batch_slices"] == 0
+    gpq = net.gates_per_qubit()
+    for bad in ([(0, 0)], [(3, gpq[3])], [(99, 1)], [(0, 3), (0, 3)]):
+        with pytest.raises(tn.TnError) as e:
+            tn.Plan(net, open_mask=om, forced_slices=bad, trials=2)
+        assert e.value.status == tn.TN_ERR_ARG

@@ -77,6 +77,39 @@ def test_c1_sliced_batches_and_ragged_ranges(env):
         assert _relerr(out.cpu().numpy().view(np.complex128), want) < FP32_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_c1_forced_slices_sum_to_statevector(env, prec):
+    """Caller-chosen sliced wires (kept as diagonal indices through the host
+    simplification) still sum to the unsliced amplitudes."""
+    tn, torch = env
+    circ, _, _ = rqcgen.config_circuit("c1")
+    om, cb = 0b111100001111, 0b000010100000
+    want = sv.batch_amplitudes(sv.simulate(circ), circ.n_qubits, cb, om)
+    forced = [(0, 3), (5, 4), (9, 2), (2, 5), (6, 1), (11, 6)]
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=30, forced_slices=forced,
+                   precision=prec, trials=8)
+    n = 1 << plan.info()["log2_slices"]
+    got = _run_plan(tn, torch, plan, 0, n, [cb], 8)
+    assert _relerr(got, want) < PLAN_TOL[prec]
+
+
+def test_c5_oracle_slices_against_golden(env):
+    """53 qubits, 20 cycles: the oracle's own slice set (stored with its partial
+    sums) is handed to the library as forced slices; slices 0..n-1 summed on the
+    GPU match the oracle's FP64 partial sum."""
+    tn, torch = env
+    from tests.golden.make_golden import read_sliced
+    wires, n, want = read_sliced("c5")
+    circ, om, cb = rqcgen.config_circuit("c5")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=30, forced_slices=wires,
+                   precision="bf16x3", trials=16)
+    assert plan.sliced_wires()[:len(wires)] == wires
+    got = _run_plan(tn, torch, plan, 0, n, [cb], 6)
+    err = _relerr(got, want)
+    print(f"c5 bf16x3 slices 0..{n - 1}: rel amp err {err:.3e}")
+    assert err < PLAN_TOL["bf16x3"]
+
+
 def test_c1_range_errors(env):
     tn, torch = env
     circ, om, cb = rqcgen.config_circuit("c1")
@@ -132,6 +165,21 @@ def test_c3_all_slices_against_golden(env, prec):
     assert xerr < (1e-3 if prec != "tf32" else 5e-2)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_c2_autotuned_plan_still_matches_golden(env, prec):
+    """The autotuner swaps kernels and tile widths per step; results keep their accuracy."""
+    tn, torch = env
+    from tests.golden.make_golden import read
+    want = read("c2")
+    circ, om, cb = rqcgen.config_circuit("c2")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=26, precision=prec)
+    _run_plan(tn, torch, plan, 0, 1, [cb], 10)
+    plan.autotune(reps=1)
+    for _ in range(2):   # eager chunk, then the re-captured graph
+        got = _run_plan(tn, torch, plan, 0, 1, [cb], 10)
+        assert _relerr(got, want) < PLAN_TOL[prec]
+
+
 SHAPES = [  # (m bits, k bits, n bits): several tiles, ragged (smaller than a tile), degenerate
     (0, 0, 0), (1, 0, 3), (0, 4, 0), (1, 1, 1), (3, 2, 5), (9, 5, 3), (10, 7, 7),
     (12, 3, 2), (5, 9, 8), (13, 4, 4), (8, 6, 11), (2, 12, 2), (11, 1, 6),
@@ -184,6 +232,23 @@ def test_permute_bit_exact(env, rank):
     for i in range(batch):
         want = pairwise.permute(x[i], rank, perm).astype(np.complex64)
         assert np.array_equal(got[i], want)
+
+
+def test_bounded_wait_times_out_and_context_survives(env):
+    """A device wait that nothing completes gives up after its limit and
+    reports TN_ERR_TIMEOUT; later kernels still run (no fault, no hang)."""
+    import time
+    tn, torch = env
+    t0 = time.time()
+    st = tn.selftest_bounded_wait(200)
+    dt = time.time() - t0
+    assert st == tn.TN_ERR_TIMEOUT
+    assert 0.15 < dt < 5.0
+    x = torch.ones(1 << 10, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    tn.permute(x, y, 10, list(range(10)))
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
 
 
 def test_xeb_against_oracle(env):
