@@ -204,6 +204,17 @@ class CircuitNetwork:
         perm = [final_legs.index(l) for l in want]
         return np.transpose(final, perm).reshape(-1)
 
+    def contract_in_order(self, merges: Sequence[Tuple[int, int]], sliced: Sequence[Label],
+                          slice_ids: Iterable[int]) -> np.ndarray:
+        """Sum over slice ids of the network with `sliced` fixed (slice id s sets
+        sliced[j] to bit j of s), contracted along a given order of this network
+        (e.g. the order plan() returned together with these wires)."""
+        total = np.zeros(1 << len(self.open_legs), dtype=np.complex128)
+        for s in slice_ids:
+            s = int(s)
+            total += self._run(merges, {leg: (s >> j) & 1 for j, leg in enumerate(sliced)})
+        return total
+
     def contract(self, sliced: Sequence[Label] = (), slice_ids: Optional[Iterable[int]] = None,
                  max_log2: int = 27, method: str = "greedy", trials: int = 8, seed: int = 0) -> np.ndarray:
         """Sum over the given slice ids (all 2^S when None) of the network with the

@@ -104,6 +104,12 @@ struct TcArgs {
   // block sorted by their storage position in C (sel = index | 64 for columns)
   int32_t epi_ok;
   int8_t epi_sel[9], epi_pos[9];
+  // split-K: tile t covers k chunks [s*kc_per, (s+1)*kc_per) with s = t % n_split
+  // of output tile t / n_split; with n_split > 1 each split writes its partial C
+  // (in C's layout) at c_part + s * c_part_stride and k_split_reduce adds them
+  int32_t n_split;
+  float2* c_part;
+  int64_t c_part_stride;
 };
 constexpr int TC_EPI_STRIDE = 17;                                  // staging row stride (float2)
 constexpr int TC_EPI_BYTES = TC_EPI_WARPS * 32 * TC_EPI_STRIDE * 8;  // epilogue staging
@@ -326,6 +332,20 @@ __global__ void k_tc_prep_b(const TcArgs a) {
   }
 }
 
+// Split-K: C[i] = sum over splits of the partials, in split order.
+__global__ void k_split_reduce(const float2* __restrict__ part, int n_split, int64_t stride,
+                               float2* __restrict__ C, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 acc = part[i];
+    for (int sp = 1; sp < n_split; ++sp) {
+      const float2 v = part[sp * stride + i];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    C[i] = acc;
+  }
+}
+
 // ------------------------------------------------------------------ the GEMM
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constant__ TcArgs a,
@@ -403,6 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int kc_n = a.n_kc;
+  const int kc_per = a.n_kc / a.n_split;
 
   if (warp == TC_PROD_WARP) {
     // ---------------------------------------------------------------- TMA producer
@@ -412,8 +433,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-        const int nt = (int)(tile % a.n_nt);
-        const int64_t rest = tile / a.n_nt;
+        const int64_t otile = tile / a.n_split;
+        const int kc0 = (int)(tile % a.n_split) * kc_per;
+        const int nt = (int)(otile % a.n_nt);
+        const int64_t rest = otile / a.n_nt;
         const int mt = (int)(rest % a.n_mt);
         const int inst = (int)(rest / a.n_mt);
         // tensor-map coordinates of the tile: rows from the m bits after the
@@ -425,7 +448,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         for (int j = 0; j < g.nb; ++j)
           if ((inst >> j) & 1) c2 += (int64_t)1 << (g.a_bpos[j] - a.hi_shift);
         const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * (int64_t)(T::NPL * b_plane);
-        for (int kc = 0; kc < kc_n; ++kc) {
+        for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
           if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
           uint8_t* sa = stages + stage * stage_bytes;
           uint8_t* sb = sa + T::NPL * a_plane;
@@ -460,7 +483,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-        for (int kc = 0; kc < kc_n; ++kc) {
+        for (int kc = 0; kc < kc_per; ++kc) {
           if (!mbar_wait(smem_u32(&rawfull[stage]), ph, abort_flag, a.err)) { ok = false; break; }
           uint8_t* sa = stages + stage * stage_bytes;
           const uint8_t* raw = sa + a.raw_off;
@@ -527,14 +550,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       }
     }
     auto tile_base = [&](int64_t tile) -> const float2* {
-      const int64_t rest = tile / a.n_nt;
+      const int64_t rest = tile / a.n_split / a.n_nt;
       const int mt = (int)(rest % a.n_mt);
       const int inst = (int)(rest / a.n_mt);
       return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) + deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
     };
     auto b_src = [&](int64_t tile, int kc) -> const uint8_t* {
-      const int nt = (int)(tile % a.n_nt);
-      const int inst = (int)(tile / a.n_nt / a.n_mt);
+      const int64_t otile = tile / a.n_split;
+      const int nt = (int)(otile % a.n_nt);
+      const int inst = (int)(otile / a.n_nt / a.n_mt);
       return a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n + kc) * (int64_t)(T::NPL * b_plane);
     };
     int stage = 0;
@@ -544,7 +568,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
         const float2* At = tile_base(tile);
         const uint8_t* bt = b_src(tile, 0);
-        for (int kc = 0; kc < kc_n; ++kc) {
+        const int kc0 = (int)(tile % a.n_split) * kc_per;
+        for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
           const float2* Ak = At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
           uint8_t* sa = stages + stage * stage_bytes;
           uint8_t* sb = sa + T::NPL * a_plane;
@@ -597,15 +622,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
       };
       int64_t tile = blockIdx.x;
-      int kc = 0;
+      int kc = (int)(tile % a.n_split) * kc_per;
       const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
       const float2* An = At;     // base of the tile of the prefetched stage
       auto body = [&](float4(&vc)[NCH][KPC / 2], float4(&vn)[NCH][KPC / 2]) -> bool {
         int64_t ntile = tile;
         int nkc = kc + 1;
-        if (nkc == kc_n) {
-          nkc = 0;
+        if (nkc == (int)(tile % a.n_split) * kc_per + kc_per) {
           ntile += gridDim.x;
+          nkc = (int)(ntile % a.n_split) * kc_per;
           if (ntile < a.n_tiles) An = tile_base(ntile);
         }
         if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
@@ -650,7 +675,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         kc = nkc;
         return true;
       };
-      if (tile < a.n_tiles) issue(v0, At);
+      if (tile < a.n_tiles) issue(v0, At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
       while (tile < a.n_tiles) {
         if (!body(v0, v1) || tile >= a.n_tiles) break;
         if (!body(v1, v0)) break;
@@ -673,7 +698,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ncp);
-        for (int kc = 0; kc < kc_n; ++kc) {
+        for (int kc = 0; kc < kc_per; ++kc) {
           if (!mbar_wait(smem_u32(&full[stage]), ph, abort_flag, a.err)) { ok = false; break; }
           fence_proxy_async();
           tc_fence_after();
@@ -727,11 +752,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       const uint32_t aph = (uint32_t)((it >> 1) & 1);
       if (!mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, a.err)) break;
       tc_fence_after();
-      const int nt = (int)(tile % a.n_nt);
-      const int64_t rest = tile / a.n_nt;
+      const int64_t otile = tile / a.n_split;
+      const int nt = (int)(otile % a.n_nt);
+      const int64_t rest = otile / a.n_nt;
       const int mt = (int)(rest % a.n_mt);
       const int inst = (int)(rest / a.n_mt);
-      float2* C = g.C + inst_offset(inst, g.c_istride, g.c_bpos, g.nb) +
+      float2* Cb = a.n_split > 1 ? a.c_part + (tile % a.n_split) * a.c_part_stride : g.C;
+      float2* C = Cb + inst_offset(inst, g.c_istride, g.c_bpos, g.nb) +
                   deposit_hi((uint64_t)mt, g.c_mpos, g.tm, g.nm) +
                   deposit_hi((uint64_t)nt, g.c_npos, a.tnb, g.nn);
       const bool row_ok = row < tmv;

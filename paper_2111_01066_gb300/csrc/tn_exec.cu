@@ -136,6 +136,8 @@ struct StepLaunch {
   TcArgs tc;
   alignas(64) CUtensorMap tma;
   int64_t ws_bytes = 0;
+  int64_t split_off = 0;   // split-K partials inside the workspace
+  int64_t c_total = 0;     // elements of C (all instances)
   int smem = 0;
 };
 
@@ -191,7 +193,8 @@ static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
   t.c2_inst_mul = n_lin > 1 ? ((int64_t)1 << (a_bits - hi_shift)) : 0;
 }
 
-static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_lin) {
+static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_lin, int64_t c_total = 0,
+                              bool allow_split = false) {
   StepLaunch L;
   L.kid = kid;
   L.g = g;
@@ -210,6 +213,21 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   const int b_plane = tc_plane_bytes(2 * t.tn_c, esz);
   const int a_plane = tc_plane_bytes(TC_M, esz);
   L.ws_bytes = (int64_t)g.n_inst * t.n_nt * t.n_kc * npl * b_plane;
+  // split-K when the output tiles cannot fill the SMs and the k loop is long
+  t.n_split = 1;
+  if (allow_split && c_total > 0 && t.n_tiles < sm_count() && t.n_kc >= 8) {
+    int sp = 1;
+    // enough tiles for several waves (tail below ~15%), each split >= 4 k chunks
+    while (sp < 32 && t.n_tiles * sp * 2 <= 8 * (int64_t)sm_count() && t.n_kc / (sp * 2) >= 4) sp *= 2;
+    if (sp > 1 && (int64_t)sp * c_total * 8 <= ((int64_t)256 << 20)) {
+      t.n_split = sp;
+      t.c_part_stride = c_total;
+      L.split_off = (L.ws_bytes + 255) / 256 * 256;
+      L.ws_bytes = L.split_off + (int64_t)sp * c_total * 8;
+      L.c_total = c_total;
+    }
+  }
+  t.n_tiles *= t.n_split;
   setup_tma(L, a_bits, n_lin);
   const bool staging = t.a_tma && kid == K_TC_BF16X3;
   t.stage_bytes = npl * (a_plane + b_plane) + (staging ? TC_RAW_BYTES : 0);
@@ -242,6 +260,7 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
   TcArgs t = L.tc;
   t.bimg = ws;
   t.err = err;
+  if (t.n_split > 1) t.c_part = reinterpret_cast<float2*>(ws + L.split_off);
   if (t.n_tiles <= 0) return;
   const int64_t prep_total = (int64_t)t.g.n_inst * t.n_nt * t.n_kc * TC_TK * t.tn_c;
   const int pblocks = (int)std::min<int64_t>((prep_total + 255) / 256, (int64_t)sm_count() * 16);
@@ -262,6 +281,10 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
       attr = true;
     }
     k_cgemm_tc<TC_BF16X3><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
+  }
+  if (t.n_split > 1) {
+    const int rb = (int)std::min<int64_t>((L.c_total + 255) / 256, (int64_t)sm_count() * 8);
+    k_split_reduce<<<rb, 256, 0, s>>>(t.c_part, t.n_split, t.c_part_stride, t.g.C, L.c_total);
   }
 }
 
@@ -352,7 +375,7 @@ static void ensure_device(Plan& p) {
     const int kid = pick_kernel(p.opts.precision, d);
     ds->launches.push_back(make_launch(
         make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off, 1 << d.nb), kid,
-        64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1));
+        64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true));
   }
   int64_t ws = 16;
   for (const StepLaunch& L : ds->launches) ws = std::max(ws, L.ws_bytes);
@@ -588,7 +611,7 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
     auto build = [&](int kid, int tn_log) {
       return make_launch(make_args(d, kid, ds.arena + d.a_off, ds.arena + d.b_off, ds.arena + d.c_off, 1 << d.nb,
                                    0, 0, 0, tn_log),
-                         kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1);
+                         kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true);
     };
     double best = time_launch(ds.launches[i]);
     std::vector<std::pair<int, int>> cands;
@@ -796,7 +819,7 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   const int kid = pick_kernel(precision, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                          reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
-  StepLaunch L = make_launch(g, kid, ar, batch);
+  StepLaunch L = make_launch(g, kid, ar, batch, batch * d.c_elems, true);
   Scratch& sc = scratch_for_device();
   if (L.ws_bytes > sc.ws_bytes) {
     CK(cudaStreamSynchronize((cudaStream_t)stream));

@@ -48,8 +48,8 @@ def write_sliced(name: str, n_slices: int) -> None:
     circ, open_mask, closed = rqcgen.config_circuit(name)
     net = tensornet.CircuitNetwork(circ, closed, open_mask)
     t0 = time.time()
-    _, wires = net.plan([], max_log2=25, method="bisect", trials=12, seed=100)
-    amps = net.contract(wires, range(n_slices), max_log2=25, method="bisect", trials=12, seed=100)
+    merges, wires = net.plan([], max_log2=25, method="bisect", trials=12, seed=100)
+    amps = net.contract_in_order(merges, wires, range(n_slices))
     dt = time.time() - t0
     path = os.path.join(HERE, f"{name}_slices_amplitudes.txt")
     with open(path, "w") as f:

@@ -188,6 +188,7 @@ SHAPES = [  # (m bits, k bits, n bits): several tiles, ragged (smaller than a ti
 
 TC_SHAPES = [  # big enough for the tensor-core kernel (m >= 4 bits, >= 2^20 multiply-adds)
     (10, 4, 6), (12, 5, 3), (8, 8, 8), (7, 13, 2), (14, 2, 4), (9, 6, 7), (16, 3, 1),
+    (8, 14, 5), (9, 13, 3), (7, 12, 8),   # few output tiles, long k: split-K
 ]
 
 

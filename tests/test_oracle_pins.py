@@ -278,6 +278,18 @@ def test_bisection_order_matches_greedy():
     assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
 
 
+def test_contract_in_order_sums_slices_of_its_own_order():
+    """Slicing the wires plan() picks and summing every slice along plan()'s
+    order reproduces the unsliced amplitudes."""
+    circ, _, cb = rqcgen.config_circuit("c1")
+    net = tn.CircuitNetwork(circ, cb, 0b1111)
+    merges, wires = net.plan([], max_log2=6, method="bisect", trials=2)
+    assert len(wires) > 0
+    a = net.contract_in_order(merges, wires, range(1 << len(wires)))
+    b = net.contract()
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+
+
 def test_oracle_subslicing_changes_nothing():
     circ, om, cb = rqcgen.config_circuit("c1")
     net = tn.CircuitNetwork(circ, cb, om)
