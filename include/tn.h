@@ -167,6 +167,17 @@ tn_status tn_plan_sliced_wires(const tn_plan_t* plan, int32_t* qubit, int32_t* t
 tn_status tn_plan_step_shape(const tn_plan_t* plan, int32_t step, int32_t* log2_m,
                              int32_t* log2_k, int32_t* log2_n, int32_t* log2_batch);
 
+/* Storage layout of step i's operands (host only; no paper counterpart: an
+ * introspection call for reports and tests).  Positions are bit positions of
+ * each operand's element index (element = complex64, position 0 the fastest).
+ * Writes to out[0..] in this order: nm, nk, nn, nb, then a_m[nm], a_k[nk],
+ * b_k[nk], b_n[nn], c_m[nm], c_n[nn], a_b[nb], b_b[nb], c_b[nb]: where A is
+ * the streamed operand, B the small one, C the result, and a_m[j] / c_m[j] the
+ * positions of row bit j in A and in C (and so on).  `count` receives the
+ * number of entries; at most `cap` are written (TN_ERR_ARG if cap is too small). */
+tn_status tn_plan_step_layout(const tn_plan_t* plan, int32_t step, int32_t* out, int32_t cap,
+                              int32_t* count);
+
 /* Contract slices [slice_first, slice_first + slice_count) for n_batches
  * correlated batches and ADD the result into out_amplitudes (main text, section
  * II: the sliced network is the sum of the slices; section III: one run gives

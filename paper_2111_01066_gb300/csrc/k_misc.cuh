@@ -7,18 +7,6 @@
 
 namespace tnx {
 
-__device__ __forceinline__ uint32_t pdep_u32(uint32_t x, uint32_t mask) {
-  uint32_t r = 0;
-  int k = 0;
-  while (mask) {
-    const uint32_t low = mask & (0u - mask);
-    if ((x >> k) & 1) r |= low;
-    ++k;
-    mask ^= low;
-  }
-  return r;
-}
-
 // Materialise every leaf of the chunk: the sliced wires take the bits of the
 // slice id, the closed output wires the bits of the batch's bitstring.
 __global__ void k_leaf_select(const float2* __restrict__ leaf_data, const LeafDesc* __restrict__ leaves,
@@ -29,11 +17,13 @@ __global__ void k_leaf_select(const float2* __restrict__ leaf_data, const LeafDe
     const LeafDesc& d = leaves[li];
     const int rank = d.rank;
     const int64_t per = (int64_t)1 << rank;
-    const int64_t total = per << __popc(d.bmask);
+    const int nbat = __popc(d.bmask);
+    const int64_t total = per << nbat;
     for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
       const uint32_t inst = (uint32_t)(e >> rank);
       const int64_t i = e & (per - 1);
-      const uint64_t sid = p.slice_base | (uint64_t)pdep_u32(inst, d.bmask);
+      uint64_t sid = p.slice_base;
+      for (int t = 0; t < nbat; ++t) sid |= (uint64_t)((inst >> t) & 1u) << d.bslice[t];
       int64_t fix = 0;
       for (int f = 0; f < d.nfixed; ++f) {
         const int idx = d.fixed_index[f];
@@ -58,6 +48,7 @@ __global__ void k_root_partial(const float2* __restrict__ arena, const RootDesc 
   const int64_t nout = (int64_t)1 << k;
   const uint32_t per = (1u << b) / (uint32_t)groups;
   const int g = blockIdx.y;
+  const int nbat = __popc(r.bmask);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nout;
        j += (int64_t)gridDim.x * blockDim.x) {
     int64_t ri = 0;
@@ -67,7 +58,8 @@ __global__ void k_root_partial(const float2* __restrict__ arena, const RootDesc 
     for (uint32_t s = (uint32_t)g * per; s < (uint32_t)(g + 1) * per; ++s) {
       const uint64_t sid = p.slice_base + s;
       if (sid < p.valid_lo || sid >= p.valid_hi) continue;
-      const uint32_t inst = pext_u32(s, r.bmask);
+      uint32_t inst = 0;
+      for (int t = 0; t < nbat; ++t) inst |= ((s >> r.bslice[t]) & 1u) << t;
       const float2 v = arena[r.off + ((int64_t)inst << k) + ri];
       sr += (double)v.x;
       si += (double)v.y;

@@ -246,8 +246,13 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
       t.epi_pos[t2] = (int8_t)bits[t2].first;
       t.epi_sel[t2] = (int8_t)bits[t2].second;
     }
-    // rows already contiguous at C's lowest position: direct per-column stores coalesce
-    t.epi_ok = (bits[0].second & 64) ? 1 : 0;
+    // direct per-column stores write runs of 2^run_d elements (C's lowest
+    // positions hold row bits 0, 1, ... in order); the staged order writes runs
+    // of 2^run_s (C's lowest positions among the block's 9 bits): stage when longer
+    int run_d = 0, run_s = 0;
+    while (run_d < 5 && g.c_mpos[run_d] == run_d) ++run_d;
+    while (run_s < 5 && bits[run_s].first == run_s) ++run_s;
+    t.epi_ok = run_s > run_d ? 1 : 0;
   }
   return L;
 }

@@ -78,6 +78,7 @@ struct LeafDesc {
   int64_t dst_off;    // arena offset of instance 0
   int32_t rank;       // planning wires kept (2^rank elements per instance)
   uint32_t bmask;     // batch (low slice) bits this leaf carries, as a mask over [0, b)
+  int8_t bslice[MAXB];  // slice bit of the t-th batch bit in storage order (positions rank + t)
   int32_t nfixed;
   int8_t fixed_kind[MAXFIX];   // 0: slice bit, 1: closed-output qubit
   int8_t fixed_index[MAXFIX];  // slice bit j or qubit q
@@ -88,6 +89,7 @@ struct RootDesc {
   int64_t off;
   int32_t rank;        // = number of open qubits
   uint32_t bmask;      // batch bits carried by the root (mask over [0, b))
+  int8_t bslice[MAXB]; // slice bit of the t-th batch bit in storage order
   int8_t pos_of_open[64];  // root bit position of the j-th open qubit
 };
 

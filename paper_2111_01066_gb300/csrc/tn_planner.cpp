@@ -710,13 +710,15 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   struct NodeInfo {
     std::vector<int> wires;  // planning wires (unsliced), storage order
     uint32_t bmask = 0;
+    std::vector<int> border;  // batch bits (chunk slice bits) in storage order, above the wires
     int64_t off = -1;
   };
   auto elems_of = [](const NodeInfo& ni) {
     return (int64_t)1 << (ni.wires.size() + __builtin_popcount(ni.bmask));
   };
   const int64_t cap_bytes = o.max_arena_bytes > 0 ? o.max_arena_bytes : (int64_t)96 << 30;
-  std::vector<std::vector<int>> node_order;   // storage order wanted by each node's consumer
+  std::vector<std::vector<int>> node_order;   // storage order of every node's wires
+  std::vector<std::vector<int>> border_of;    // and of its batch bits
   auto layout = [&](int b, std::vector<NodeInfo>& info, std::vector<StepDesc>& steps,
                     int64_t& arena) -> bool {
     info.assign(L + nm, NodeInfo{});
@@ -729,20 +731,25 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
           info[i].bmask |= 1u << slice_bit[pw_of[w]];
     }
     // Layout pass (SI figure S7a: C is written in the index order its consumer
-    // wants).  Every tensor that a step streams as its large operand A is stored
-    // as [the wires that step contracts..., its free wires...], i.e. as a plain
-    // row-major matrix of rows = free indices, so the GEMM can fetch its tiles
-    // with the tensor memory accelerator.  Other tensors keep the order they are
-    // produced in.
+    // wants), from the root down.  The streamed operand A of every step is stored
+    // as [contracted wires..., free wires..., free batch bits..., shared batch
+    // bits...]: a row-major matrix whose rows (the free wires, then the batch
+    // bits folded into them) are contiguous, so the GEMM fetches its tiles with
+    // the tensor memory accelerator.  Inside that frame the order is free and is
+    // chosen for the two kernels that touch the tensor: the free part follows the
+    // order of those wires in the step's result (tile rows then run along C's
+    // memory order), and the contracted part lists first the rows of the step
+    // that produces A (its 32-row warps then write contiguous runs).  A tensor
+    // that is no step's A keeps its producer's order: rows, then columns.
     {
       std::vector<std::vector<int>> wset(L + nm);
       std::vector<uint32_t> bm(L + nm, 0);
+      std::vector<int> a_of(nm, -1), b_of(nm, -1);
       for (int i = 0; i < L; ++i) {
         wset[i] = info[i].wires;
         std::sort(wset[i].begin(), wset[i].end());
         bm[i] = info[i].bmask;
       }
-      std::vector<std::vector<int>> want(L + nm);
       for (int mi : order) {
         const int x = T.merges[mi].first, y = T.merges[mi].second;
         std::vector<int> u;
@@ -753,18 +760,64 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
         const int64_t ex = (int64_t)1 << (wset[x].size() + __builtin_popcount(bm[x]));
         const int64_t ey = (int64_t)1 << (wset[y].size() + __builtin_popcount(bm[y]));
         const bool x_is_a = ex > ey || (ex == ey && wset[x].size() >= wset[y].size());
-        const int a = x_is_a ? x : y, bb = x_is_a ? y : x;
-        std::vector<int> k, m;
-        std::set_intersection(wset[a].begin(), wset[a].end(), wset[bb].begin(), wset[bb].end(),
-                              std::back_inserter(k));
-        std::set_difference(wset[a].begin(), wset[a].end(), wset[bb].begin(), wset[bb].end(),
-                            std::back_inserter(m));
-        want[a] = k;
-        want[a].insert(want[a].end(), m.begin(), m.end());
+        a_of[mi] = x_is_a ? x : y;
+        b_of[mi] = x_is_a ? y : x;
       }
-      for (int i = 0; i < L; ++i)
-        if (!want[i].empty()) info[i].wires = want[i];
-      node_order.swap(want);
+      auto has = [&](int node, int w) { return std::binary_search(wset[node].begin(), wset[node].end(), w); };
+      std::vector<std::vector<int>> lw(L + nm), lb(L + nm);
+      std::vector<char> lset(L + nm, 0);
+      for (auto it = order.rbegin(); it != order.rend(); ++it) {
+        const int mi = *it, c = L + mi, a = a_of[mi], bb = b_of[mi];
+        std::vector<int> k, m, n;
+        for (int w : wset[a]) (has(bb, w) ? k : m).push_back(w);
+        for (int w : wset[bb])
+          if (!has(a, w)) n.push_back(w);
+        std::vector<int> fb, sb, nbits;  // A-only, shared and B-only batch bits
+        for (int j = 0; j < 32; ++j) {
+          const bool ia = (bm[a] >> j) & 1, ib = (bm[bb] >> j) & 1;
+          if (ia && ib) sb.push_back(j);
+          else if (ia) fb.push_back(j);
+          else if (ib) nbits.push_back(j);
+        }
+        if (lset[c]) {
+          auto rank_in = [](const std::vector<int>& v, int x) {
+            return (int)(std::find(v.begin(), v.end(), x) - v.begin());
+          };
+          std::stable_sort(m.begin(), m.end(),
+                           [&](int u, int v) { return rank_in(lw[c], u) < rank_in(lw[c], v); });
+          std::stable_sort(fb.begin(), fb.end(),
+                           [&](int u, int v) { return rank_in(lb[c], u) < rank_in(lb[c], v); });
+        }
+        if (a >= L) {  // rows of A's producer first among the contracted wires
+          const int pa = a_of[a - L], pb = b_of[a - L];
+          std::stable_partition(k.begin(), k.end(), [&](int w) { return has(pa, w) && !has(pb, w); });
+        }
+        lw[a] = k;
+        lw[a].insert(lw[a].end(), m.begin(), m.end());
+        lb[a] = fb;
+        lb[a].insert(lb[a].end(), sb.begin(), sb.end());
+        lset[a] = 1;
+        if (!lset[c]) {
+          lw[c] = m;
+          lw[c].insert(lw[c].end(), n.begin(), n.end());
+          lb[c] = fb;
+          lb[c].insert(lb[c].end(), nbits.begin(), nbits.end());
+          lb[c].insert(lb[c].end(), sb.begin(), sb.end());
+          lset[c] = 1;
+        }
+      }
+      for (int i = 0; i < L; ++i) {
+        if (lset[i]) {
+          info[i].wires = lw[i];
+          info[i].border = lb[i];
+        } else {
+          info[i].border.clear();
+          for (int j = 0; j < 32; ++j)
+            if ((info[i].bmask >> j) & 1) info[i].border.push_back(j);
+        }
+      }
+      node_order.swap(lw);
+      border_of.swap(lb);
     }
     // best-fit arena allocator
     std::vector<std::pair<int64_t, int64_t>> freel;  // (offset, size)
@@ -823,28 +876,29 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
         (std::find(B.wires.begin(), B.wires.end(), w) != B.wires.end() ? kw : mw).push_back(w);
       for (int w : B.wires)
         if (std::find(A.wires.begin(), A.wires.end(), w) == A.wires.end()) nw.push_back(w);
-      C.wires = mw;
-      C.wires.insert(C.wires.end(), nw.begin(), nw.end());
-      if (!node_order[L + mi].empty()) C.wires = node_order[L + mi];
+      C.wires = node_order[L + mi];
       C.bmask = A.bmask | B.bmask;
+      C.border = border_of[L + mi];
+      if (C.wires.size() != mw.size() + nw.size() || (int)C.border.size() != __builtin_popcount(C.bmask))
+        fail(TN_ERR_PLAN, "internal: layout of a step result");
       auto pos_in = [](const std::vector<int>& ws, int w) {
         return (int)(std::find(ws.begin(), ws.end(), w) - ws.begin());
       };
-      // storage position of batch bit j in a node: rank + its index among the node's batch bits
-      auto bpos = [](const NodeInfo& x, int j) {
-        return (int)x.wires.size() + __builtin_popcount(x.bmask & ((1u << j) - 1u));
-      };
+      // tile columns follow C's memory order (the epilogue's writes then run along C)
+      std::stable_sort(nw.begin(), nw.end(), [&](int u, int v) { return pos_in(C.wires, u) < pos_in(C.wires, v); });
+      // storage position of batch bit j in a node: rank + its index in the node's batch order
+      auto bpos = [&](const NodeInfo& x, int j) { return (int)x.wires.size() + pos_in(x.border, j); };
       const int ra = (int)A.wires.size(), rb = (int)B.wires.size(), rc = (int)C.wires.size();
       std::vector<std::pair<int, int>> mb, nb;  // (pos in operand, pos in C)
       std::vector<std::array<int, 3>> bb;       // shared batch bits (pos A, pos B, pos C)
       for (int w : mw) mb.push_back({pos_in(A.wires, w), pos_in(C.wires, w)});
       for (int w : nw) nb.push_back({pos_in(B.wires, w), pos_in(C.wires, w)});
-      for (int j = 0; j < 32; ++j) {
-        const bool ia = (A.bmask >> j) & 1, ib = (B.bmask >> j) & 1;
-        if (ia && ib) bb.push_back({bpos(A, j), bpos(B, j), bpos(C, j)});
-        else if (ia) mb.push_back({bpos(A, j), bpos(C, j)});
-        else if (ib) nb.push_back({bpos(B, j), bpos(C, j)});
+      for (int j : A.border) {   // rows: A's batch bits in A's storage order
+        if ((B.bmask >> j) & 1) bb.push_back({bpos(A, j), bpos(B, j), bpos(C, j)});
+        else mb.push_back({bpos(A, j), bpos(C, j)});
       }
+      for (int j : B.border)
+        if (!((A.bmask >> j) & 1)) nb.push_back({bpos(B, j), bpos(C, j)});
       if ((int)(mb.size() + kw.size()) > MAXR || (int)(kw.size() + nb.size()) > MAXR ||
           (int)(mb.size() + nb.size()) > MAXR || (int)bb.size() > MAXB)
         fail(TN_ERR_UNSUPPORTED, "a tensor exceeds the kernels' rank limit");
@@ -943,6 +997,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
     ld.dst_off = info[i].off;
     ld.rank = (int)info[i].wires.size();
     ld.bmask = info[i].bmask;
+    for (size_t t = 0; t < info[i].border.size(); ++t) ld.bslice[t] = (int8_t)info[i].border[t];
     ld.nfixed = (int)kind.size();
     for (size_t f = 0; f < kind.size(); ++f) {
       ld.fixed_kind[f] = (int8_t)kind[f];
@@ -957,6 +1012,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   P->root.off = R.off;
   P->root.rank = k_open;
   P->root.bmask = R.bmask;
+  for (size_t t = 0; t < R.border.size(); ++t) P->root.bslice[t] = (int8_t)R.border[t];
   for (int j = 0; j < k_open; ++j) {
     const int w = pw_of[net.output_wire[P->open_qubits[j]]];
     const int p = (int)(std::find(R.wires.begin(), R.wires.end(), w) - R.wires.begin());
@@ -1066,6 +1122,41 @@ extern "C" tn_status tn_plan_sliced_wires(const tn_plan_t* h, int32_t* qubit, in
     qubit[j] = p.sliced[j].q;
     t[j] = p.sliced[j].t;
   }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_step_layout(const tn_plan_t* h, int32_t step, int32_t* out, int32_t cap,
+                                         int32_t* count) {
+  clear_error();
+  if (!h || !out || !count) {
+    set_error("tn_plan_step_layout: NULL argument");
+    return TN_ERR_ARG;
+  }
+  const Plan& p = h->plan;
+  if (step < 0 || step >= (int)p.steps.size()) {
+    set_error("tn_plan_step_layout: step out of range");
+    return TN_ERR_ARG;
+  }
+  const StepDesc& d = p.steps[step];
+  std::vector<int32_t> v = {d.nm, d.nk, d.nn, d.nb};
+  auto put = [&](const int8_t* pos, int n) {
+    for (int i = 0; i < n; ++i) v.push_back(pos[i]);
+  };
+  put(d.a_mpos, d.nm);
+  put(d.a_kpos, d.nk);
+  put(d.b_kpos, d.nk);
+  put(d.b_npos, d.nn);
+  put(d.c_mpos, d.nm);
+  put(d.c_npos, d.nn);
+  put(d.a_bpos, d.nb);
+  put(d.b_bpos, d.nb);
+  put(d.c_bpos, d.nb);
+  *count = (int32_t)v.size();
+  if ((int32_t)v.size() > cap) {
+    set_error("tn_plan_step_layout: cap smaller than the layout");
+    return TN_ERR_ARG;
+  }
+  for (size_t i = 0; i < v.size(); ++i) out[i] = v[i];
   return TN_OK;
 }
 

@@ -78,6 +78,8 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_step_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    "tn_plan_step_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "tn_contract_slices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p]),
@@ -230,6 +232,21 @@ class Plan:
             _check(load().tn_plan_step_shape(self.handle, i, ctypes.byref(a), ctypes.byref(b),
                                              ctypes.byref(c), ctypes.byref(d)))
             out.append((a.value, b.value, c.value, d.value))
+        return out
+
+    def step_layout(self, i: int) -> dict:
+        """Bit positions of step i's operands (A streamed, B small, C result):
+        keys a_m, a_k, b_k, b_n, c_m, c_n, a_b, b_b, c_b."""
+        buf = (ctypes.c_int32 * 256)()
+        cnt = ctypes.c_int32()
+        _check(load().tn_plan_step_layout(self.handle, i, buf, 256, ctypes.byref(cnt)))
+        v = list(buf[:cnt.value])
+        nm, nk, nn, nb = v[:4]
+        out, pos = {}, 4
+        for key, n in (("a_m", nm), ("a_k", nk), ("b_k", nk), ("b_n", nn), ("c_m", nm), ("c_n", nn),
+                       ("a_b", nb), ("b_b", nb), ("c_b", nb)):
+            out[key] = v[pos:pos + n]
+            pos += n
         return out
 
     def contract_slices(self, slice_first: int, slice_count: int, bitstrings: Sequence[int],
