@@ -19,13 +19,17 @@
 // S7a).  B' (small) is written once per step by k_tc_prep_b in the exact
 // shared-memory image of every (n tile, k chunk) and fetched by one bulk copy.
 //
-// Roles (416 threads, one CTA per SM, persistent over tiles):
+// Roles (480 threads, one CTA per SM, persistent over tiles):
 //   warps 0-3  epilogue: TMEM -> registers -> C (lane = tile row)
 //   warp  4    TMEM allocation; lane 0 issues tcgen05.mma and commits
-//   warps 5-12 loaders: A gathers + B' bulk copy per pipeline stage, or, when
-//              A is fetched by TMA in BF16X3 mode, the fp32 -> hi/lo converters
-//   warp  13   TMA producer: when A is stored as [contracted..., free...] its
-//              tiles are fetched by one tensor-map load per stage
+//   warps 5-12 loaders: A gathers into the A ring, or, when A is fetched by
+//              TMA in BF16X3 mode, the fp32 -> hi/lo converters (in place)
+//   warp  13   A producer: when A is stored as [contracted..., free...] its
+//              tiles are fetched by one tensor-map load per k chunk
+//   warp  14   B' producer: one bulk copy of the (n tile, k chunk) image per k chunk
+// Two rings decouple the operands: a deep ring of 16 KB A slots (more of the
+// streamed operand in flight for the memory-bound steps) and a shallow ring of
+// B' slots (B' comes from L2).
 // Every mbarrier wait is bounded by a globaltimer deadline; on expiry the
 // kernel records TN_ERR_TIMEOUT in *err, every role leaves its loop, and the
 // CTA frees its TMEM and returns.
@@ -41,14 +45,18 @@ namespace tnx {
 constexpr int TC_M = 128;
 constexpr int TC_TK = 16;            // complex k per pipeline stage
 constexpr int TC_KP = 2 * TC_TK;     // real K' per stage
-constexpr int TC_MAX_STAGES = 4;
+constexpr int TC_MAX_A = 8;           // A ring slots
+constexpr int TC_MAX_B = 4;           // B' ring slots
 constexpr int TC_EPI_WARPS = 4;
 constexpr int TC_MMA_WARP = 4;
 constexpr int TC_LOAD_WARPS = 8;
 constexpr int TC_LOAD_THREADS = TC_LOAD_WARPS * 32;
-constexpr int TC_PROD_WARP = TC_EPI_WARPS + 1 + TC_LOAD_WARPS;   // TMA producer
-constexpr int TC_THREADS = (TC_PROD_WARP + 1) * 32;
-constexpr int TC_RAW_BYTES = TC_M * TC_KP * 4;                     // fp32 A tile (TMA staging)
+constexpr int TC_PROD_WARP = TC_EPI_WARPS + 1 + TC_LOAD_WARPS;   // A producer (TMA)
+constexpr int TC_B_WARP = TC_PROD_WARP + 1;                        // B' producer
+constexpr int TC_THREADS = (TC_B_WARP + 1) * 32;
+// one A slot: the fp32 tile of a k chunk (128 rows x 32 real), which is also
+// the size of its TF32 plane and of its two BF16 planes
+constexpr int TC_A_SLOT = TC_M * TC_KP * 4;
 constexpr int TC_TMEM_COLS = 512;
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;           // 4 s per wait
 constexpr int TC_MIN_SMEM = 120 * 1024;                  // keeps one CTA per SM
@@ -93,10 +101,9 @@ struct TcArgs {
   int64_t n_tiles;
   int32_t* err;
   int32_t a_tma;         // 1: A tiles by tensor-map loads (A stored as [k..., m...])
-  int32_t nst;           // pipeline stages
-  int32_t stage_bytes;   // bytes per stage: A planes, B' planes, fp32 staging
-  int32_t raw_off;       // offset of the fp32 staging tile in a stage (BF16X3 + TMA)
-  int32_t full_count;    // arrivals expected on a stage's "full" barrier
+  int32_t na;            // A ring slots (TC_A_SLOT bytes each)
+  int32_t nbs;           // B' ring slots (one (n tile, k chunk) image each)
+  int32_t fa_count;      // arrivals expected on an A slot's "full" barrier
   int32_t nmw;           // m bits that are tensor-map rows (contiguous after the k bits)
   int32_t hi_shift;      // storage position where tensor-map dimension 2 starts
   int64_t c2_inst_mul;   // dimension-2 step per linear instance (tn_contract_pair batches)
@@ -178,6 +185,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t a, uint32_t bytes
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(a),
                "r"(bytes)
                : "memory");
+}
+// Barrier over `nthreads` threads (named barrier `id`) that also returns the
+// OR of `pred` over them, so that all of them take the same branch after it.
+__device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+      : "memory");
+  return r != 0;
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint32_t mbar) {
@@ -352,56 +371,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
                                                               const __grid_constant__ CUtensorMap tma_a) {
   using T = TcT<MODE>;
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
-  // swizzle atoms need 1024-byte aligned stage buffers
+  // swizzle atoms need 1024-byte aligned slots
   uint8_t* smem_raw = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
   const GemmArgs& g = a.g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ncp = 2 * a.tn_c;                                   // N'
   const int a_plane = tc_plane_bytes(TC_M, T::ESZ);
   const int b_plane = tc_plane_bytes(ncp, T::ESZ);
-  const int stage_bytes = a.stage_bytes;
-  const int nst = a.nst;
-  uint8_t* stages = smem_raw;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + nst * stage_bytes);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + TC_MAX_STAGES;
-  uint64_t* rawfull = bars + 2 * TC_MAX_STAGES;
-  uint64_t* tfull = bars + 3 * TC_MAX_STAGES;
-  uint64_t* tempty = bars + 3 * TC_MAX_STAGES + 2;
-  uint64_t* fin = bars + 3 * TC_MAX_STAGES + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TC_MAX_STAGES + 5);
+  const int b_slot = T::NPL * b_plane;
+  const int na = a.na, nbs = a.nbs;
+  uint8_t* aring = smem_raw;
+  uint8_t* bring = aring + na * TC_A_SLOT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bring + nbs * b_slot);
+  uint64_t* fullA = bars;
+  uint64_t* emptyA = bars + TC_MAX_A;
+  uint64_t* rawA = bars + 2 * TC_MAX_A;
+  uint64_t* fullB = bars + 3 * TC_MAX_A;
+  uint64_t* emptyB = fullB + TC_MAX_B;
+  uint64_t* tfull = emptyB + TC_MAX_B;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* fin = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int64_t* offCm = reinterpret_cast<int64_t*>(tmem_slot + 4);
-  float2* epi_stage = reinterpret_cast<float2*>(smem_raw + nst * stage_bytes + 4096);
-  int64_t* epi_off = offCm + 2 * TC_M;                  // [16]: offsets of e bits 5-8
-  int* epi_rj = reinterpret_cast<int*>(epi_off + 16);   // [16]: (row << 8) | column of e bits 5-8
+  float2* epi_stage = reinterpret_cast<float2*>(reinterpret_cast<uint8_t*>(bars) + 4096);
   int64_t* offCn = offCm + TC_M;
 
-  // zero every stage once: padding rows / columns are never written again
-  for (int i = threadIdx.x; i < nst * stage_bytes / 16; i += blockDim.x)
-    reinterpret_cast<uint4*>(stages)[i] = make_uint4(0, 0, 0, 0);
+  // zero every slot once: padding rows / columns are never written again
+  for (int i = threadIdx.x; i < (na * TC_A_SLOT + nbs * b_slot) / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(aring)[i] = make_uint4(0, 0, 0, 0);
   const int tmv = 1 << g.tm, tnv = 1 << a.tnb;
   for (int r = threadIdx.x; r < TC_M; r += blockDim.x)
     offCm[r] = r < tmv ? deposit_hi((uint64_t)r, g.c_mpos, 0, g.tm) : 0;
   for (int c = threadIdx.x; c < 128; c += blockDim.x)
     offCn[c] = c < tnv ? deposit_hi((uint64_t)c, g.c_npos, 0, a.tnb) : 0;
-  if (threadIdx.x < 16 && a.epi_ok) {
-    int rj = 0;
-    int64_t off = 0;
-    for (int t = 5; t < 9; ++t)
-      if ((threadIdx.x >> (t - 5)) & 1) {
-        const int sl = a.epi_sel[t];
-        rj |= (sl & 64) ? (1 << (sl & 63)) : (1 << ((sl & 63) + 8));
-        off += (int64_t)1 << a.epi_pos[t];
-      }
-    epi_rj[threadIdx.x] = rj;
-    epi_off[threadIdx.x] = off;
-  }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < nst; ++s) {
-      mbar_init(smem_u32(&full[s]), a.full_count);
-      mbar_init(smem_u32(&empty[s]), 1);
-      mbar_init(smem_u32(&rawfull[s]), 1);
+    for (int s = 0; s < na; ++s) {
+      mbar_init(smem_u32(&fullA[s]), a.fa_count);
+      mbar_init(smem_u32(&emptyA[s]), 1);
+      mbar_init(smem_u32(&rawA[s]), 1);
+    }
+    for (int s = 0; s < nbs; ++s) {
+      mbar_init(smem_u32(&fullB[s]), 1);
+      mbar_init(smem_u32(&emptyB[s]), 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&tfull[i]), 1);
@@ -426,16 +438,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   const int kc_per = a.n_kc / a.n_split;
 
   if (warp == TC_PROD_WARP) {
-    // ---------------------------------------------------------------- TMA producer
+    // ---------------------------------------------------------------- A producer (TMA)
     if (a.a_tma && lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tma_a)) : "memory");
-      int stage = 0;
+      int slot = 0;
       uint32_t ph = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
         const int64_t otile = tile / a.n_split;
         const int kc0 = (int)(tile % a.n_split) * kc_per;
-        const int nt = (int)(otile % a.n_nt);
         const int64_t rest = otile / a.n_nt;
         const int mt = (int)(rest % a.n_mt);
         const int inst = (int)(rest / a.n_mt);
@@ -447,27 +458,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           if ((mt >> (i - g.tm)) & 1) c2 += (int64_t)1 << (g.a_mpos[i] - a.hi_shift);
         for (int j = 0; j < g.nb; ++j)
           if ((inst >> j) & 1) c2 += (int64_t)1 << (g.a_bpos[j] - a.hi_shift);
-        const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * (int64_t)(T::NPL * b_plane);
         for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
-          if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
-          uint8_t* sa = stages + stage * stage_bytes;
-          uint8_t* sb = sa + T::NPL * a_plane;
-          const uint32_t fb = smem_u32(&full[stage]);
-          const uint8_t* bsrc = bt + (int64_t)kc * (T::NPL * b_plane);
-          if constexpr (MODE == TC_TF32) {
-            mbar_arrive_expect_tx(fb, (uint32_t)(TC_RAW_BYTES + T::NPL * b_plane));
-            bulk_g2s(smem_u32(sb), bsrc, T::NPL * b_plane, fb);
-            tma_load_3d(smem_u32(sa), &tma_a, kc * TC_KP, c1, (int)c2, fb);
-          } else {
-            // B' first, so that the converters cannot complete "full" before it is expected
-            mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
-            bulk_g2s(smem_u32(sb), bsrc, T::NPL * b_plane, fb);
-            const uint32_t rb = smem_u32(&rawfull[stage]);
-            mbar_arrive_expect_tx(rb, (uint32_t)TC_RAW_BYTES);
-            tma_load_3d(smem_u32(sa + a.raw_off), &tma_a, kc * TC_KP, c1, (int)c2, rb);
+          if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
+          // TF32: the tile is the MMA operand; BF16X3: converted in place first
+          const uint32_t bar = MODE == TC_TF32 ? smem_u32(&fullA[slot]) : smem_u32(&rawA[slot]);
+          mbar_arrive_expect_tx(bar, (uint32_t)TC_A_SLOT);
+          tma_load_3d(smem_u32(aring + slot * TC_A_SLOT), &tma_a, kc * TC_KP, c1, (int)c2, bar);
+          if (++slot == na) {
+            slot = 0;
+            ph ^= 1;
           }
-          if (++stage == nst) {
-            stage = 0;
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == TC_B_WARP) {
+    // ---------------------------------------------------------------- B' producer
+    if (lane == 0) {
+      int slot = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+        const int64_t otile = tile / a.n_split;
+        const int kc0 = (int)(tile % a.n_split) * kc_per;
+        const int nt = (int)(otile % a.n_nt);
+        const int inst = (int)(otile / a.n_nt / a.n_mt);
+        const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * (int64_t)b_slot;
+        for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
+          if (!mbar_wait(smem_u32(&emptyB[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
+          const uint32_t fb = smem_u32(&fullB[slot]);
+          mbar_arrive_expect_tx(fb, (uint32_t)b_slot);
+          bulk_g2s(smem_u32(bring + slot * b_slot), bt + (int64_t)kc * b_slot, (uint32_t)b_slot, fb);
+          if (++slot == nbs) {
+            slot = 0;
             ph ^= 1;
           }
         }
@@ -476,24 +499,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     __syncwarp();
   } else if (warp >= TC_MMA_WARP + 1 && a.a_tma) {
     // ---------------------------------------------------------------- converters (BF16X3 + TMA)
+    // The fp32 tile (128 rows x 128 bytes, 128-byte swizzle) is read into
+    // registers by all converter threads, then -- after a barrier -- rewritten
+    // in place as the bf16 hi and lo planes (128 rows x 64 bytes each).
     if constexpr (MODE != TC_TF32) {
       const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
       constexpr int NCH = TC_M * (TC_KP * T::ESZ / 16) / TC_LOAD_THREADS;
-      int stage = 0;
+      int slot = 0;
       uint32_t ph = 0;
-      bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        bool stop = false;
         for (int kc = 0; kc < kc_per; ++kc) {
-          if (!mbar_wait(smem_u32(&rawfull[stage]), ph, abort_flag, a.err)) { ok = false; break; }
-          uint8_t* sa = stages + stage * stage_bytes;
-          const uint8_t* raw = sa + a.raw_off;
+          const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
+          uint8_t* sa = aring + slot * TC_A_SLOT;
+          float4 x[NCH][2];
 #pragma unroll
           for (int j = 0; j < NCH; ++j) {
             const int q = lt + j * TC_LOAD_THREADS;
             const int row = q % TC_M, c = q / TC_M;     // 16-byte output chunk: 4 complex
-            const float4 x0 = *reinterpret_cast<const float4*>(raw + tc_elem_off(row, 8 * c, 4));
-            const float4 x1 = *reinterpret_cast<const float4*>(raw + tc_elem_off(row, 8 * c + 4, 4));
-            const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            x[j][0] = *reinterpret_cast<const float4*>(sa + tc_elem_off(row, 8 * c, 4));
+            x[j][1] = *reinterpret_cast<const float4*>(sa + tc_elem_off(row, 8 * c + 4, 4));
+          }
+          // every converter has read the tile; all agree whether to go on
+          stop = named_barrier_or(1, TC_LOAD_THREADS, !got || *abort_flag);
+          if (stop) break;
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            const int q = lt + j * TC_LOAD_THREADS;
+            const int row = q % TC_M, c = q / TC_M;
+            const float xs[8] = {x[j][0].x, x[j][0].y, x[j][0].z, x[j][0].w,
+                                 x[j][1].x, x[j][1].y, x[j][1].z, x[j][1].w};
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -508,12 +543,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
             *reinterpret_cast<uint4*>(sa + a_plane + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
           fence_proxy_async();
-          mbar_arrive(smem_u32(&full[stage]));
-          if (++stage == nst) {
-            stage = 0;
+          mbar_arrive(smem_u32(&fullA[slot]));
+          if (++slot == na) {
+            slot = 0;
             ph ^= 1;
           }
         }
+        if (stop) break;
       }
     }
   } else if (warp >= TC_MMA_WARP + 1) {
@@ -555,30 +591,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       const int inst = (int)(rest / a.n_mt);
       return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) + deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
     };
-    auto b_src = [&](int64_t tile, int kc) -> const uint8_t* {
-      const int64_t otile = tile / a.n_split;
-      const int nt = (int)(otile % a.n_nt);
-      const int inst = (int)(otile / a.n_nt / a.n_mt);
-      return a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n + kc) * (int64_t)(T::NPL * b_plane);
-    };
-    int stage = 0;
+    int slot = 0;
     uint32_t ph = 0;
     if constexpr (MODE == TC_TF32) {
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
         const float2* At = tile_base(tile);
-        const uint8_t* bt = b_src(tile, 0);
         const int kc0 = (int)(tile % a.n_split) * kc_per;
         for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
           const float2* Ak = At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
-          uint8_t* sa = stages + stage * stage_bytes;
-          uint8_t* sb = sa + T::NPL * a_plane;
-          const uint32_t fb = smem_u32(&full[stage]);
-          if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
-          if (lt == 0) {
-            mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
-            bulk_g2s(smem_u32(sb), bt + (int64_t)kc * (T::NPL * b_plane), T::NPL * b_plane, fb);
-          }
+          uint8_t* sa = aring + slot * TC_A_SLOT;
+          if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
           {
             const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
 #pragma unroll
@@ -593,16 +616,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
               }
             }
           }
-          cp_async_arrive_noinc(fb);
-          if (++stage == nst) {
-            stage = 0;
+          cp_async_arrive_noinc(smem_u32(&fullA[slot]));
+          if (++slot == na) {
+            slot = 0;
             ph ^= 1;
           }
         }
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
-      // BF16X3: the next stage's loads are in flight in registers while the
+      // BF16X3: the next slot's loads are in flight in registers while the
       // current one is split into hi/lo and stored
       float4 v0[NCH][KPC / 2], v1[NCH][KPC / 2];
       auto issue = [&](float4(&v)[NCH][KPC / 2], const float2* Ak) {
@@ -624,7 +647,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int64_t tile = blockIdx.x;
       int kc = (int)(tile % a.n_split) * kc_per;
       const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
-      const float2* An = At;     // base of the tile of the prefetched stage
+      const float2* An = At;     // base of the tile of the prefetched slot
       auto body = [&](float4(&vc)[NCH][KPC / 2], float4(&vn)[NCH][KPC / 2]) -> bool {
         int64_t ntile = tile;
         int nkc = kc + 1;
@@ -634,14 +657,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           if (ntile < a.n_tiles) An = tile_base(ntile);
         }
         if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
-        uint8_t* sa = stages + stage * stage_bytes;
-        uint8_t* sb = sa + T::NPL * a_plane;
-        const uint32_t fb = smem_u32(&full[stage]);
-        if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, a.err)) return false;
-        if (lt == 0) {
-          mbar_expect_tx(fb, (uint32_t)(T::NPL * b_plane));
-          bulk_g2s(smem_u32(sb), b_src(tile, kc), T::NPL * b_plane, fb);
-        }
+        uint8_t* sa = aring + slot * TC_A_SLOT;
+        if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) return false;
         {
 #pragma unroll
           for (int j = 0; j < NCH; ++j) {
@@ -665,9 +682,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
         }
         fence_proxy_async();
-        mbar_arrive(fb);
-        if (++stage == nst) {
-          stage = 0;
+        mbar_arrive(smem_u32(&fullA[slot]));
+        if (++slot == na) {
+          slot = 0;
           ph ^= 1;
         }
         if (ntile != tile) At = An;
@@ -688,8 +705,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
                              ((uint32_t)(ncp >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
       const uint32_t sbo = tc_sbo(T::ESZ);
       const uint32_t lay = T::ESZ == 4 ? 2u : 4u;
-      int stage = 0;
-      uint32_t ph = 0;
+      int sa_i = 0, sb_i = 0;
+      uint32_t pha = 0, phb = 0;
       int64_t it = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++it) {
@@ -699,11 +716,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ncp);
         for (int kc = 0; kc < kc_per; ++kc) {
-          if (!mbar_wait(smem_u32(&full[stage]), ph, abort_flag, a.err)) { ok = false; break; }
+          if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err) ||
+              !mbar_wait(smem_u32(&fullB[sb_i]), phb, abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
           fence_proxy_async();
           tc_fence_after();
-          const uint32_t sa = smem_u32(stages + stage * stage_bytes);
-          const uint32_t sb = sa + T::NPL * a_plane;
+          const uint32_t sa = smem_u32(aring + sa_i * TC_A_SLOT);
+          const uint32_t sb = smem_u32(bring + sb_i * b_slot);
 #pragma unroll
           for (int j = 0; j < TC_KP * T::ESZ / 32; ++j) {
             // one MMA K step = 32 bytes of every row: advance inside the swizzle atom
@@ -719,10 +740,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
               tc_mma<MODE>(d_tmem, adl, bd, idesc, 1u);
             }
           }
-          tc_commit(smem_u32(&empty[stage]));
-          if (++stage == nst) {
-            stage = 0;
-            ph ^= 1;
+          tc_commit(smem_u32(&emptyA[sa_i]));
+          tc_commit(smem_u32(&emptyB[sb_i]));
+          if (++sa_i == na) {
+            sa_i = 0;
+            pha ^= 1;
+          }
+          if (++sb_i == nbs) {
+            sb_i = 0;
+            phb ^= 1;
           }
         }
         if (!ok) break;
@@ -736,16 +762,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   } else {
     // ---------------------------------------------------------------- epilogue
     const int row = warp * 32 + lane;
-    // write-back decode: e = lane + 32 i; lane bits are e bits 0-4, i bits 5-8
-    int epi_rj_l = 0;
-    int64_t epi_off_l = 0;
-    if (a.epi_ok)
-      for (int t = 0; t < 5; ++t)
-        if ((lane >> t) & 1) {
-          const int sl = a.epi_sel[t];
-          epi_rj_l |= (sl & 64) ? (1 << (sl & 63)) : (1 << ((sl & 63) + 8));
-          epi_off_l += (int64_t)1 << a.epi_pos[t];
+    // staged write-back: element e = lane + 32 i of the warp's 32 x 16 block;
+    // e's bits (lane bits 0-4, i bits 5-8) sit at C positions epi_pos[] and at
+    // staging-buffer strides w (row bit r: STRIDE 2^r, column bit c: 2^c), so
+    // both addresses are sums of per-bit weights
+    int sidx_l = 0;
+    int64_t goff_l = 0;
+    int ws[4] = {0, 0, 0, 0};
+    int64_t wg[4] = {0, 0, 0, 0};
+    if (a.epi_ok) {
+      for (int t = 0; t < 9; ++t) {
+        const int sl = a.epi_sel[t];
+        const int w = (sl & 64) ? (1 << (sl & 63)) : (TC_EPI_STRIDE << (sl & 63));
+        const int64_t o = (int64_t)1 << a.epi_pos[t];
+        if (t < 5) {
+          if ((lane >> t) & 1) {
+            sidx_l += w;
+            goff_l += o;
+          }
+        } else {
+          ws[t - 5] = w;
+          wg[t - 5] = o;
         }
+      }
+    }
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
       const int acc = (int)(it & 1);
@@ -774,11 +814,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           for (int j = 0; j < 16; ++j) stg[lane * TC_EPI_STRIDE + j] = make_float2(v[2 * j], v[2 * j + 1]);
           __syncwarp();
           if (warp * 32 < tmv && c0 / 2 < tnv) {
-            float2* base = C + offCm[warp * 32] + offCn[c0 / 2] + epi_off_l;
-#pragma unroll 4
+            float2* base = C + offCm[warp * 32] + offCn[c0 / 2] + goff_l;
+            const float2* sbase = stg + sidx_l;
+#pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const int rj = epi_rj_l | epi_rj[i];
-              base[epi_off[i]] = stg[(rj >> 8) * TC_EPI_STRIDE + (rj & 255)];
+              int si = 0;
+              int64_t gi = 0;
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if ((i >> j) & 1) {
+                  si += ws[j];
+                  gi += wg[j];
+                }
+              base[gi] = sbase[si];
             }
           }
           __syncwarp();

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -193,8 +194,10 @@ static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
   t.c2_inst_mul = n_lin > 1 ? ((int64_t)1 << (a_bits - hi_shift)) : 0;
 }
 
+// epi_mode: -1 chooses the write-back by the coalesced run lengths, 0 forces
+// direct per-column stores, 1 the staged order (where the tile allows it)
 static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_lin, int64_t c_total = 0,
-                              bool allow_split = false) {
+                              bool allow_split = false, int epi_mode = -1) {
   StepLaunch L;
   L.kid = kid;
   L.g = g;
@@ -211,7 +214,6 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.n_tiles = (int64_t)g.n_inst * t.n_mt * t.n_nt;
   const int esz = kid == K_TC_TF32 ? 4 : 2, npl = kid == K_TC_TF32 ? 1 : 2;
   const int b_plane = tc_plane_bytes(2 * t.tn_c, esz);
-  const int a_plane = tc_plane_bytes(TC_M, esz);
   L.ws_bytes = (int64_t)g.n_inst * t.n_nt * t.n_kc * npl * b_plane;
   // split-K when the output tiles cannot fill the SMs and the k loop is long
   t.n_split = 1;
@@ -229,12 +231,13 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   }
   t.n_tiles *= t.n_split;
   setup_tma(L, a_bits, n_lin);
-  const bool staging = t.a_tma && kid == K_TC_BF16X3;
-  t.stage_bytes = npl * (a_plane + b_plane) + (staging ? TC_RAW_BYTES : 0);
-  t.raw_off = npl * (a_plane + b_plane);
-  t.nst = std::min(TC_MAX_STAGES, (220 * 1024 - 4096 - TC_EPI_BYTES) / t.stage_bytes);
-  t.full_count = t.a_tma ? (kid == K_TC_TF32 ? 1 : TC_LOAD_THREADS) : TC_LOAD_THREADS;
-  L.smem = std::max(t.nst * t.stage_bytes + 4096 + TC_EPI_BYTES + 1024, TC_MIN_SMEM);
+  // rings: B' slots first (3, or 4 when small), the rest of the budget to A slots
+  const int b_slot = npl * b_plane;
+  const int budget = 220 * 1024 - 4096 - TC_EPI_BYTES;
+  t.nbs = b_slot <= 16384 ? TC_MAX_B : 3;
+  t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / TC_A_SLOT);
+  t.fa_count = (t.a_tma && kid == K_TC_TF32) ? 1 : TC_LOAD_THREADS;
+  L.smem = std::max(t.na * TC_A_SLOT + t.nbs * b_slot + 4096 + TC_EPI_BYTES + 1024, TC_MIN_SMEM);
   // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
   t.epi_ok = 0;
   if (g.tm >= 5 && g.tn >= 4) {
@@ -248,11 +251,12 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
     }
     // direct per-column stores write runs of 2^run_d elements (C's lowest
     // positions hold row bits 0, 1, ... in order); the staged order writes runs
-    // of 2^run_s (C's lowest positions among the block's 9 bits): stage when longer
+    // of 2^run_s (C's lowest positions among the block's 9 bits).  Runs of 4+
+    // elements fill whole 32-byte sectors, so stage only below that
     int run_d = 0, run_s = 0;
     while (run_d < 5 && g.c_mpos[run_d] == run_d) ++run_d;
     while (run_s < 5 && bits[run_s].first == run_s) ++run_s;
-    t.epi_ok = run_s > run_d ? 1 : 0;
+    t.epi_ok = epi_mode >= 0 ? epi_mode : (run_s > run_d && run_d < 2 ? 1 : 0);
   }
   return L;
 }
@@ -613,28 +617,35 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   };
   for (size_t i = 0; i < p.steps.size(); ++i) {
     const StepDesc& d = p.steps[i];
-    auto build = [&](int kid, int tn_log) {
+    auto build = [&](int kid, int tn_log, int epi) {
       return make_launch(make_args(d, kid, ds.arena + d.a_off, ds.arena + d.b_off, ds.arena + d.c_off, 1 << d.nb,
                                    0, 0, 0, tn_log),
-                         kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true);
+                         kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true, epi);
     };
     double best = time_launch(ds.launches[i]);
-    std::vector<std::pair<int, int>> cands;
+    std::vector<std::array<int, 3>> cands;   // kernel, tile width (log2 complex columns), write-back
     const bool tc_mode = p.opts.precision == TN_PREC_TF32 || p.opts.precision == TN_PREC_BF16X3;
     const int tc_kid = p.opts.precision == TN_PREC_TF32 ? K_TC_TF32 : K_TC_BF16X3;
     if (tc_mode && d.nm >= 4)
       for (int tn_log : {7, 6, 5})
-        if (tn_log <= std::max(3, d.nn)) cands.push_back({tc_kid, tn_log});
+        if (tn_log <= std::max(3, d.nn))
+          for (int epi : {0, 1}) cands.push_back({tc_kid, tn_log, epi});
     // CUDA-core tilings: FP32 mode, tiny steps, and low arithmetic intensity
     // (complex flops per byte moved), where a tile's fixed cost on the tensor
     // cores outweighs its few products
     const double flops = 8.0 * std::ldexp(1.0, d.nm + d.nk + d.nn + d.nb);
     const double bytes = 8.0 * (double)(d.a_elems + d.b_elems + d.c_elems);
     if (!tc_mode || best < 0.05 || flops / bytes < 48.0)
-      for (int k : {K_SIMT_64x64, K_SIMT_128x16, K_SIMT_256x4}) cands.push_back({k, -1});
-    for (auto [kid, tn_log] : cands) {
-      if (kid == ds.launches[i].kid && (tn_log < 0 || std::min(tn_log, d.nn) == ds.launches[i].g.tn)) continue;
-      StepLaunch L = build(kid, tn_log);
+      for (int k : {K_SIMT_64x64, K_SIMT_128x16, K_SIMT_256x4}) cands.push_back({k, -1, 0});
+    std::vector<std::array<int, 3>> seen;
+    auto key = [](const StepLaunch& L) {
+      return std::array<int, 3>{L.kid, L.g.tn, is_tc(L.kid) ? L.tc.epi_ok : 0};
+    };
+    seen.push_back(key(ds.launches[i]));
+    for (auto [kid, tn_log, epi] : cands) {
+      StepLaunch L = build(kid, tn_log, epi);
+      if (std::find(seen.begin(), seen.end(), key(L)) != seen.end()) continue;
+      seen.push_back(key(L));
       const double t = time_launch(L);
       if (t < best * 0.97) {
         best = t;
