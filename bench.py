@@ -179,9 +179,7 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 x GHz (se
 
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels,
 # keyed by (kernel, log2 m,k,n,batch); see profiles/ for the command and scaling.
-MEASURED_TRAFFIC = {
-    ("tc_bf16x3", (16, 12, 9, 4)): 46.9e9,   # 64 x the 16384x4096x512 proxy capture (733.0 MB)
-}
+MEASURED_TRAFFIC = {}
 
 
 def load_peaks() -> dict:
@@ -197,10 +195,13 @@ def complex_peak_tflops(kernel: str, peaks: dict) -> float:
     """Peak in algorithmic complex flops (8 per complex multiply-add) of a kernel:
     a real tensor peak P runs a complex MAC as R real MACs, so P_eff = P * 8 / (2 R)."""
     bf16 = peaks["bf16_tflops"]
-    if kernel == "tc_tf32":
-        return bf16 / 2 * 8 / (2 * 4)          # TF32 dense = half the BF16 rate, 4M
-    if kernel == "tc_bf16x3":
-        return bf16 * 8 / (2 * 12)             # 3 bf16 products per real product, 4M
+    real = {"tc_tf32": (bf16 / 2, 4),          # TF32 dense = half the BF16 rate, 4M
+            "tc_tf32_3m": (bf16 / 2, 3),
+            "tc_bf16x3": (bf16, 12),           # 3 bf16 products per real product, 4M
+            "tc_bf16x3_3m": (bf16, 9)}
+    if kernel in real:
+        p, r = real[kernel]
+        return p * 8 / (2 * r)
     return FP32_SIMT_TFLOPS
 
 
@@ -372,6 +373,8 @@ def main() -> int:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(rqcgen.CONFIGS))
     ap.add_argument("--precision", default="auto")
+    ap.add_argument("--complex-mult", type=int, default=4, choices=[3, 4],
+                    help="4M or 3M complex products on the tensor cores")
     ap.add_argument("--compare-fp32", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--autotune", type=int, default=1, help="tune kernels per step before timing")
@@ -441,7 +444,7 @@ def main() -> int:
                    log2_batch_slices=run["log2_batch"], trials=run.get("trials", 64),
                    max_arena_bytes=int(run.get("arena_gib", 96)) << 30)
     t_plan = time.time()
-    plan = tn.Plan(net, precision=prec, **plan_kw)
+    plan = tn.Plan(net, precision=prec, complex_mult=args.complex_mult, **plan_kw)
     t_plan = time.time() - t_plan
     info = plan.info()
     all_slices = 1 << info["log2_slices"]
@@ -462,7 +465,7 @@ def main() -> int:
         p.contract_slices(first, n_slices, [bits], o, stream)
         return tn.xeb(o.view(torch.complex128), circ.n_qubits, stream)
 
-    def timed(p, o, k, w):
+    def timed(p, o, k, w, mark=False):
         for _ in range(w):
             step(p, o)
         torch.cuda.synchronize()
@@ -472,9 +475,13 @@ def main() -> int:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
+            if mark:   # NVTX range of the timed steps (a profiler can capture just these)
+                torch.cuda.nvtx.range_push("timed_step")
             e0.record(stream)
             step(p, o)
             e1.record(stream)
+            if mark:
+                torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         return times
@@ -491,7 +498,7 @@ def main() -> int:
     barrier(world)
     clocks = ClockSampler(local)
     clocks.start()
-    times = timed(plan, out, args.steps, args.warmup)
+    times = timed(plan, out, args.steps, args.warmup, mark=True)
     clk = clocks.stop()
     barrier(world)
     ms = statistics.mean(times)
@@ -534,10 +541,14 @@ def main() -> int:
                 "xeb_err": abs(f - oxeb.linear_xeb(gold, circ.n_qubits))}
 
     if args.compare_fp32:
-        for other in ("fp32", "tf32"):
-            if other == prec:
+        # the plain FP32 path, TF32, and the other complex product (4M / 3M) of this precision
+        alts = [("fp32", 4), ("tf32", 4)]
+        if prec in ("tf32", "bf16x3"):
+            alts.append((prec, 7 - args.complex_mult))
+        for other, ocm in alts:
+            if (other, ocm) == (prec, args.complex_mult):
                 continue
-            p2 = tn.Plan(net, precision=other, **plan_kw)
+            p2 = tn.Plan(net, precision=other, complex_mult=ocm, **plan_kw)
             o2 = torch.zeros_like(out)
             step(p2, o2)
             if args.autotune:
@@ -546,7 +557,8 @@ def main() -> int:
                 step(p2, o2)
             t2 = timed(p2, o2, min(3, args.steps), 1)
             ms2 = max_over_ranks(statistics.mean(t2), world, dev)
-            others[other] = {"value": total_units / (ms2 / 1e3), "ms_per_step": ms2,
+            others[other if ocm == 4 else other + "_3m"] = {"precision": other, "complex_mult": ocm,
+                                                             "value": total_units / (ms2 / 1e3), "ms_per_step": ms2,
                              "error_vs_oracle": amp_error(o2)}
             del p2, o2
     fp32 = others.get("fp32")
@@ -604,6 +616,7 @@ def main() -> int:
             "extrapolated_full_task_s": all_slices / value * world if n_slices < all_slices else None,
             "fp32_path": fp32,
             "tf32_path": others.get("tf32"),
+            "other_complex_mult_path": others.get(prec + "_3m") if args.complex_mult == 4 else others.get(prec),
             "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,
             "error_vs_oracle": err,
             "xeb": f_xeb,

@@ -108,7 +108,12 @@ typedef struct tn_plan_opts {
     uint64_t seed;                   /* seeds the randomised order search */
     int32_t  trials;                 /* order-search trials (<= 0: default) */
     int32_t  precision;              /* TN_PREC_* */
-    int32_t  complex_mult;           /* 4 (4M); 3 (3M) is reserved: TN_ERR_UNSUPPORTED in this build */
+    int32_t  complex_mult;           /* 4 (4M: Re = ArBr - AiBi, Im = ArBi + AiBr) or 3 (3M:
+                                        T1 = ArBr, T2 = AiBi, T3 = (Ar+Ai)(Br+Bi) with the sums
+                                        formed in FP32; Re = T1 - T2, Im = T3 - T1 - T2) for the
+                                        tensor-core kernels; 3 with TN_PREC_FP32 gives
+                                        TN_ERR_UNSUPPORTED (the CUDA-core path is 4M only; it
+                                        also serves the tiny steps of TF32/BF16X3 plans) */
     int32_t  log2_batch_slices;      /* slices contracted together per chunk (<= 0: auto) */
     int64_t  max_arena_bytes;        /* device arena cap for one chunk (<= 0: 96 GiB) */
     int32_t  fuse_permute;           /* 1: permutes folded into operand gathers; 0: explicit permute pass */

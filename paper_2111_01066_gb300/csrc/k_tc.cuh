@@ -92,6 +92,27 @@ __host__ __device__ inline int tc_elem_off(int row, int kp, int esz) {
   return (row >> 3) * tc_sbo(esz) + (row & 7) * tc_rowbytes(esz) + ((c ^ sw) << 4) + (byte & 15);
 }
 
+// Operand planes of one k chunk (16 complex k) for 4M or 3M products.
+//   4M: A' rows are the interleaved (re, im) storage itself, 32 real K'
+//       (TF32: one plane; BF16: hi and lo planes); B' holds the 2x2 real form
+//       of each B entry, two plane rows per complex column.
+//   3M (T1 = Ar Br, T2 = Ai Bi, T3 = (Ar + Ai)(Br + Bi); Re = T1 - T2,
+//       Im = T3 - T1 - T2): TF32 planes [Ar | Ai] and [As | unused]; BF16
+//       planes [Ar_hi | Ai_hi], [Ar_lo | Ai_lo], [As_hi | As_lo]; B likewise
+//       with Br, Bi, Bs, one plane row per complex column.  Sums are formed in
+//       FP32 before rounding or splitting.
+template <int MODE, int CM>
+struct TcPl {
+  static constexpr int ESZ = TcT<MODE>::ESZ;
+  static constexpr int PLANES = CM == 4 ? TcT<MODE>::NPL : (MODE == TC_TF32 ? 2 : 3);
+  static constexpr int ROWS_PER_COL = CM == 4 ? 2 : 1;   // B plane rows per complex column
+  static constexpr int ACC_PER_COL = CM == 4 ? 2 : 3;    // TMEM columns per complex column
+  static constexpr int A_PLANE = TC_M * TC_KP * ESZ;
+  static constexpr int RAW = TC_M * TC_KP * 4;             // the fp32 tile a TMA load brings
+  static constexpr int A_SLOT = PLANES * A_PLANE > RAW ? PLANES * A_PLANE : RAW;
+  static constexpr int MIN_TN_C = CM == 4 ? 8 : 16;       // keeps the MMA's N a multiple of 16
+};
+
 struct TcArgs {
   GemmArgs g;
   const uint8_t* bimg;   // B' images, [inst][n tile][k chunk] blocks
@@ -101,9 +122,11 @@ struct TcArgs {
   int64_t n_tiles;
   int32_t* err;
   int32_t a_tma;         // 1: A tiles by tensor-map loads (A stored as [k..., m...])
-  int32_t na;            // A ring slots (TC_A_SLOT bytes each)
+  int32_t na;            // A ring slots (TcPl::A_SLOT bytes each)
   int32_t nbs;           // B' ring slots (one (n tile, k chunk) image each)
   int32_t fa_count;      // arrivals expected on an A slot's "full" barrier
+  int32_t n_acc;         // TMEM accumulator sets: 2 (the epilogue of a tile overlaps the
+                         // next tile's MMAs) or 1 (3M with 128-column tiles: 384 columns)
   int32_t nmw;           // m bits that are tensor-map rows (contiguous after the k bits)
   int32_t hi_shift;      // storage position where tensor-map dimension 2 starts
   int64_t c2_inst_mul;   // dimension-2 step per linear instance (tn_contract_pair batches)
@@ -280,9 +303,76 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(lo_elem, hi_elem);
-  return *reinterpret_cast<uint32_t*>(&h);
+// Three 16-column TMEM loads (the 3M accumulators T1, T2, T3 of one 16-column
+// block) and the wait for them, in one asm statement so that no register is
+// read before the wait.
+__device__ __forceinline__ void tmem_ld16x3(uint32_t t1, uint32_t t2, uint32_t t3, float* v) {
+  uint32_t r[48];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%49];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%50];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+      : "r"(t1), "r"(t2), "r"(t3)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 48; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t w;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(x));
+  return w;
+}
+// hi = round(x), lo = round(x - hi) in the 16-bit operand type, for a pair of
+// consecutive K elements (packed low element first)
+template <int MODE>
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+__device__ __forceinline__ void st16(uint8_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  *reinterpret_cast<uint4*>(p) = make_uint4(a, b, c, d);
+}
+// 3M A planes for 8 consecutive complex k (k = 8h .. 8h+7 of the chunk) of tile
+// row `row`, from their values x[i] = (re, im)
+template <int MODE>
+__device__ __forceinline__ void put3m(uint8_t* sa, int row, int h, const float2 (&x)[8]) {
+  constexpr int AP = TcPl<MODE, 3>::A_PLANE;
+  if constexpr (MODE == TC_TF32) {
+    uint32_t r[8], i[8], s[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      r[e] = to_tf32(x[e].x);
+      i[e] = to_tf32(x[e].y);
+      s[e] = to_tf32(x[e].x + x[e].y);
+    }
+    st16(sa + tc_elem_off(row, 8 * h, 4), r[0], r[1], r[2], r[3]);
+    st16(sa + tc_elem_off(row, 8 * h + 4, 4), r[4], r[5], r[6], r[7]);
+    st16(sa + tc_elem_off(row, 16 + 8 * h, 4), i[0], i[1], i[2], i[3]);
+    st16(sa + tc_elem_off(row, 16 + 8 * h + 4, 4), i[4], i[5], i[6], i[7]);
+    st16(sa + AP + tc_elem_off(row, 8 * h, 4), s[0], s[1], s[2], s[3]);
+    st16(sa + AP + tc_elem_off(row, 8 * h + 4, 4), s[4], s[5], s[6], s[7]);
+  } else {
+    uint32_t rh[4], rl[4], ih[4], il[4], sh[4], sl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 u = x[2 * q], w = x[2 * q + 1];
+      split_pair<MODE>(u.x, w.x, rh[q], rl[q]);
+      split_pair<MODE>(u.y, w.y, ih[q], il[q]);
+      split_pair<MODE>(u.x + u.y, w.x + w.y, sh[q], sl[q]);
+    }
+    st16(sa + tc_elem_off(row, 8 * h, 2), rh[0], rh[1], rh[2], rh[3]);
+    st16(sa + tc_elem_off(row, 16 + 8 * h, 2), ih[0], ih[1], ih[2], ih[3]);
+    st16(sa + AP + tc_elem_off(row, 8 * h, 2), rl[0], rl[1], rl[2], rl[3]);
+    st16(sa + AP + tc_elem_off(row, 16 + 8 * h, 2), il[0], il[1], il[2], il[3]);
+    st16(sa + 2 * AP + tc_elem_off(row, 8 * h, 2), sh[0], sh[1], sh[2], sh[3]);
+    st16(sa + 2 * AP + tc_elem_off(row, 16 + 8 * h, 2), sl[0], sl[1], sl[2], sl[3]);
+  }
 }
 
 // ------------------------------------------------------------------ B' images
@@ -351,6 +441,78 @@ __global__ void k_tc_prep_b(const TcArgs a) {
   }
 }
 
+// 3M B images: per (instance, n tile, k chunk) block the planes of TcPl<MODE, 3>,
+// one plane row per complex column n; one thread per 16-byte chunk in memory
+// order of the image.  Padding (k or n beyond the operand) is zero.
+template <int MODE>
+__global__ void k_tc_prep_b3(const TcArgs a) {
+  using P = TcPl<MODE, 3>;
+  constexpr int ESZ = P::ESZ;
+  constexpr int EPC = 16 / ESZ;                 // elements per 16-byte chunk (4 or 8)
+  constexpr int CPR = TC_KP * ESZ / 16;         // chunks per plane row (8 or 4)
+  const GemmArgs& g = a.g;
+  const int rows = a.tn_c;
+  const int plane = tc_plane_bytes(rows, ESZ);
+  const int64_t block_bytes = (int64_t)P::PLANES * plane;
+  const int per_block = P::PLANES * rows * CPR;
+  const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
+  const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk = idx / per_block;
+    const int pq = (int)(idx % per_block);
+    const int pl = pq / (rows * CPR), q = pq % (rows * CPR);
+    const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
+    const int n = rg * 8 + rlo;
+    const int half = c / (CPR / 2), k0 = (c % (CPR / 2)) * EPC;   // k0.. within the half's 16 k
+    const int kc = (int)(blk % a.n_kc);
+    const int nt = (int)((blk / a.n_kc) % a.n_nt);
+    const int inst = (int)(blk / ((int64_t)a.n_kc * a.n_nt));
+    float2 b[8];
+    const bool n_ok = n < tnv;
+    int64_t base = 0;
+    if (n_ok)
+      base = inst_offset(inst, g.b_istride, g.b_bpos, g.nb) + deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk) +
+             deposit_hi((uint64_t)n, g.b_npos, 0, a.tnb) + deposit_hi((uint64_t)nt, g.b_npos, a.tnb, g.nn);
+#pragma unroll
+    for (int i = 0; i < EPC; ++i) {
+      const int kl = k0 + i;
+      b[i] = (n_ok && kl < tkv) ? g.B[base + deposit_hi((uint64_t)kl, g.b_kpos, 0, g.tk)] : make_float2(0.f, 0.f);
+    }
+    uint8_t* dst = const_cast<uint8_t*>(a.bimg) + blk * block_bytes + (int64_t)pl * plane +
+                   tc_elem_off(n, c * EPC, ESZ);
+    if constexpr (MODE == TC_TF32) {
+      // plane 0: [Br | Bi]; plane 1: [Bs | 0]
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float v = pl == 0 ? (half == 0 ? b[i].x : b[i].y) : (half == 0 ? b[i].x + b[i].y : 0.f);
+        w[i] = to_tf32(v);
+      }
+      st16(dst, w[0], w[1], w[2], w[3]);
+    } else {
+      // plane 0: [Br_hi | Bi_hi]; plane 1: [Br_lo | Bi_lo]; plane 2: [Bs_hi | Bs_lo]
+      uint32_t w[4];
+#pragma unroll
+      for (int q2 = 0; q2 < 4; ++q2) {
+        const float2 u = b[2 * q2], v = b[2 * q2 + 1];
+        float x0, x1;
+        if (pl < 2) {
+          x0 = half == 0 ? u.x : u.y;
+          x1 = half == 0 ? v.x : v.y;
+        } else {
+          x0 = u.x + u.y;
+          x1 = v.x + v.y;
+        }
+        uint32_t hi, lo;
+        split_pair<MODE>(x0, x1, hi, lo);
+        w[q2] = (pl == 0 || (pl == 2 && half == 0)) ? hi : lo;
+      }
+      st16(dst, w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 // Split-K: C[i] = sum over splits of the partials, in split order.
 __global__ void k_split_reduce(const float2* __restrict__ part, int n_split, int64_t stride,
                                float2* __restrict__ C, int64_t n) {
@@ -366,22 +528,24 @@ __global__ void k_split_reduce(const float2* __restrict__ part, int n_split, int
 }
 
 // ------------------------------------------------------------------ the GEMM
-template <int MODE>
+template <int MODE, int CM>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constant__ TcArgs a,
                                                               const __grid_constant__ CUtensorMap tma_a) {
   using T = TcT<MODE>;
+  using P = TcPl<MODE, CM>;
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
   // swizzle atoms need 1024-byte aligned slots
   uint8_t* smem_raw = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
   const GemmArgs& g = a.g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncp = 2 * a.tn_c;                                   // N'
-  const int a_plane = tc_plane_bytes(TC_M, T::ESZ);
-  const int b_plane = tc_plane_bytes(ncp, T::ESZ);
-  const int b_slot = T::NPL * b_plane;
+  const int ncp = 2 * a.tn_c;                                   // real columns of C per tile
+  const int setw = P::ACC_PER_COL * a.tn_c;                     // TMEM columns per accumulator set
+  const int a_plane = P::A_PLANE;
+  const int b_plane = tc_plane_bytes(P::ROWS_PER_COL * a.tn_c, T::ESZ);
+  const int b_slot = P::PLANES * b_plane;
   const int na = a.na, nbs = a.nbs;
   uint8_t* aring = smem_raw;
-  uint8_t* bring = aring + na * TC_A_SLOT;
+  uint8_t* bring = aring + na * P::A_SLOT;
   uint64_t* bars = reinterpret_cast<uint64_t*>(bring + nbs * b_slot);
   uint64_t* fullA = bars;
   uint64_t* emptyA = bars + TC_MAX_A;
@@ -398,7 +562,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   int64_t* offCn = offCm + TC_M;
 
   // zero every slot once: padding rows / columns are never written again
-  for (int i = threadIdx.x; i < (na * TC_A_SLOT + nbs * b_slot) / 16; i += blockDim.x)
+  for (int i = threadIdx.x; i < (na * P::A_SLOT + nbs * b_slot) / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(aring)[i] = make_uint4(0, 0, 0, 0);
   const int tmv = 1 << g.tm, tnv = 1 << a.tnb;
   for (int r = threadIdx.x; r < TC_M; r += blockDim.x)
@@ -460,10 +624,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           if ((inst >> j) & 1) c2 += (int64_t)1 << (g.a_bpos[j] - a.hi_shift);
         for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
           if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
-          // TF32: the tile is the MMA operand; BF16X3: converted in place first
-          const uint32_t bar = MODE == TC_TF32 ? smem_u32(&fullA[slot]) : smem_u32(&rawA[slot]);
-          mbar_arrive_expect_tx(bar, (uint32_t)TC_A_SLOT);
-          tma_load_3d(smem_u32(aring + slot * TC_A_SLOT), &tma_a, kc * TC_KP, c1, (int)c2, bar);
+          // TF32 4M: the tile is the MMA operand; otherwise converted in place first
+          const uint32_t bar = (MODE == TC_TF32 && CM == 4) ? smem_u32(&fullA[slot]) : smem_u32(&rawA[slot]);
+          mbar_arrive_expect_tx(bar, (uint32_t)P::RAW);
+          tma_load_3d(smem_u32(aring + slot * P::A_SLOT), &tma_a, kc * TC_KP, c1, (int)c2, bar);
           if (++slot == na) {
             slot = 0;
             ph ^= 1;
@@ -498,11 +662,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     }
     __syncwarp();
   } else if (warp >= TC_MMA_WARP + 1 && a.a_tma) {
-    // ---------------------------------------------------------------- converters (BF16X3 + TMA)
+    // ---------------------------------------------------------------- converters (TMA)
     // The fp32 tile (128 rows x 128 bytes, 128-byte swizzle) is read into
     // registers by all converter threads, then -- after a barrier -- rewritten
-    // in place as the bf16 hi and lo planes (128 rows x 64 bytes each).
-    if constexpr (MODE != TC_TF32) {
+    // in place as the operand planes: 4M BF16X3 hi and lo (128 rows x 64 bytes
+    // each); 3M the planes of TcPl<MODE, 3>, one item (row, 8 complex k) per thread.
+    if constexpr (CM == 3) {
+      const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
+      const int row = lt % TC_M, h = lt / TC_M;
+      int slot = 0;
+      uint32_t ph = 0;
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        bool stop = false;
+        for (int kc = 0; kc < kc_per; ++kc) {
+          const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
+          uint8_t* sa = aring + slot * P::A_SLOT;
+          float2 x[8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {   // raw chunk 4h + j: complex k 8h + 2j, 8h + 2j + 1
+            const float4 r = *reinterpret_cast<const float4*>(sa + tc_elem_off(row, 16 * h + 4 * j, 4));
+            x[2 * j] = make_float2(r.x, r.y);
+            x[2 * j + 1] = make_float2(r.z, r.w);
+          }
+          stop = named_barrier_or(1, TC_LOAD_THREADS, !got || *abort_flag);
+          if (stop) break;
+          put3m<MODE>(sa, row, h, x);
+          fence_proxy_async();
+          mbar_arrive(smem_u32(&fullA[slot]));
+          if (++slot == na) {
+            slot = 0;
+            ph ^= 1;
+          }
+        }
+        if (stop) break;
+      }
+    } else if constexpr (MODE != TC_TF32) {
       const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
       constexpr int NCH = TC_M * (TC_KP * T::ESZ / 16) / TC_LOAD_THREADS;
       int slot = 0;
@@ -511,7 +705,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         bool stop = false;
         for (int kc = 0; kc < kc_per; ++kc) {
           const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
-          uint8_t* sa = aring + slot * TC_A_SLOT;
+          uint8_t* sa = aring + slot * P::A_SLOT;
           float4 x[NCH][2];
 #pragma unroll
           for (int j = 0; j < NCH; ++j) {
@@ -554,101 +748,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     }
   } else if (warp >= TC_MMA_WARP + 1) {
     // ---------------------------------------------------------------- loaders
-    // Thread lt owns tile row (lt % 128) and every other 16-byte chunk of it, so
-    // the 32 lanes of a warp write 32 consecutive rows: four whole 8 x 16-byte
-    // core matrices, free of bank conflicts whatever A's storage order.  A chunk
-    // holds KPC consecutive complex k (2 for TF32, 4 for BF16); when the lowest
-    // k bit is memory position 0 those are contiguous in global memory too.
-    constexpr int KPC = 16 / (2 * T::ESZ);
-    constexpr int CPR = TC_KP * T::ESZ / 16;      // 16-byte chunks per row
-    constexpr int NCH = TC_M * CPR / TC_LOAD_THREADS;  // chunks per thread per stage
-    const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
-    const int tkv = 1 << g.tk;
-    const bool kadj = g.nk > 0 && g.a_kpos[0] == 0;
-    // lanes walk the k chunks of a row when A's lowest memory bit is a k bit,
-    // else they walk rows; either way the swizzled stores are conflict-free
-    const bool klanes = kadj;
-    int64_t goff[NCH][KPC];   // offset of each complex of each chunk, -1 = padding
-    int soff[NCH];
-    bool cok[NCH];
+    if constexpr (CM == 3) {
+      // 3M: one item (tile row, 8 complex k) per thread, gathered from A's
+      // storage order into registers; the next slot's item is in flight while
+      // the current one is converted into the planes and stored
+      const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
+      const int row = lt % TC_M, h = lt / TC_M;
+      const int tkv = 1 << g.tk;
+      const bool rok = row < (1 << g.tm);
+      const bool kadj = g.nk > 0 && g.a_kpos[0] == 0;
+      int64_t goff[8];
+      const int64_t roff = rok ? deposit_hi((uint64_t)row, g.a_mpos, 0, g.tm) : 0;
 #pragma unroll
-    for (int j = 0; j < NCH; ++j) {
-      const int q = lt + j * TC_LOAD_THREADS;
-      const int row = klanes ? q / CPR : q % TC_M;
-      const int c = klanes ? q % CPR : q / TC_M;
-      cok[j] = row < (1 << g.tm);
-      soff[j] = tc_elem_off(row, c * KPC * 2, T::ESZ);
-      const int64_t roff = deposit_hi((uint64_t)row, g.a_mpos, 0, g.tm);
-#pragma unroll
-      for (int i = 0; i < KPC; ++i) {
-        const int k = c * KPC + i;
-        goff[j][i] = (cok[j] && k < tkv) ? roff + deposit_hi((uint64_t)k, g.a_kpos, 0, g.tk) : -1;
+      for (int i = 0; i < 8; ++i) {
+        const int k = 8 * h + i;
+        goff[i] = (rok && k < tkv) ? roff + deposit_hi((uint64_t)k, g.a_kpos, 0, g.tk) : -1;
       }
-    }
-    auto tile_base = [&](int64_t tile) -> const float2* {
-      const int64_t rest = tile / a.n_split / a.n_nt;
-      const int mt = (int)(rest % a.n_mt);
-      const int inst = (int)(rest / a.n_mt);
-      return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) + deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
-    };
-    int slot = 0;
-    uint32_t ph = 0;
-    if constexpr (MODE == TC_TF32) {
-      bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-        const float2* At = tile_base(tile);
-        const int kc0 = (int)(tile % a.n_split) * kc_per;
-        for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
-          const float2* Ak = At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
-          uint8_t* sa = aring + slot * TC_A_SLOT;
-          if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
-          {
-            const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
-#pragma unroll
-            for (int j = 0; j < NCH; ++j) {
-              if (!cok[j]) continue;
-              if (v16 && goff[j][1] >= 0) {
-                cp_async16(smem_u32(sa + soff[j]), Ak + goff[j][0]);
-              } else {
-#pragma unroll
-                for (int i = 0; i < KPC; ++i)
-                  if (goff[j][i] >= 0) cp_async8(smem_u32(sa + soff[j] + 8 * i), Ak + goff[j][i]);
-              }
-            }
-          }
-          cp_async_arrive_noinc(smem_u32(&fullA[slot]));
-          if (++slot == na) {
-            slot = 0;
-            ph ^= 1;
-          }
-        }
-      }
-      asm volatile("cp.async.wait_all;" ::: "memory");
-    } else {
-      // BF16X3: the next slot's loads are in flight in registers while the
-      // current one is split into hi/lo and stored
-      float4 v0[NCH][KPC / 2], v1[NCH][KPC / 2];
-      auto issue = [&](float4(&v)[NCH][KPC / 2], const float2* Ak) {
+      auto tile_base = [&](int64_t tile) -> const float2* {
+        const int64_t rest = tile / a.n_split / a.n_nt;
+        const int mt = (int)(rest % a.n_mt);
+        const int inst = (int)(rest / a.n_mt);
+        return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) +
+               deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
+      };
+      auto issue = [&](float2(&v)[8], const float2* Ak) {
         const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
 #pragma unroll
-        for (int j = 0; j < NCH; ++j)
-#pragma unroll
-          for (int h = 0; h < KPC / 2; ++h) {
-            const int64_t o0 = goff[j][2 * h], o1 = goff[j][2 * h + 1];
-            if (v16 && o1 >= 0) {
-              v[j][h] = __ldg(reinterpret_cast<const float4*>(Ak + o0));
-            } else {
-              const float2 x = o0 >= 0 ? __ldg(Ak + o0) : make_float2(0.f, 0.f);
-              const float2 y = o1 >= 0 ? __ldg(Ak + o1) : make_float2(0.f, 0.f);
-              v[j][h] = make_float4(x.x, x.y, y.x, y.y);
-            }
+        for (int q = 0; q < 4; ++q) {
+          const int64_t o0 = goff[2 * q], o1 = goff[2 * q + 1];
+          if (v16 && o1 >= 0) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(Ak + o0));
+            v[2 * q] = make_float2(t.x, t.y);
+            v[2 * q + 1] = make_float2(t.z, t.w);
+          } else {
+            v[2 * q] = o0 >= 0 ? __ldg(Ak + o0) : make_float2(0.f, 0.f);
+            v[2 * q + 1] = o1 >= 0 ? __ldg(Ak + o1) : make_float2(0.f, 0.f);
           }
+        }
       };
+      int slot = 0;
+      uint32_t ph = 0;
       int64_t tile = blockIdx.x;
       int kc = (int)(tile % a.n_split) * kc_per;
-      const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
-      const float2* An = At;     // base of the tile of the prefetched slot
-      auto body = [&](float4(&vc)[NCH][KPC / 2], float4(&vn)[NCH][KPC / 2]) -> bool {
+      const float2* An = tile < a.n_tiles ? tile_base(tile) : g.A;
+      float2 v0[8], v1[8];
+      auto body = [&](float2(&vc)[8], float2(&vn)[8]) -> bool {
         int64_t ntile = tile;
         int nkc = kc + 1;
         if (nkc == (int)(tile % a.n_split) * kc_per + kc_per) {
@@ -657,52 +801,177 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           if (ntile < a.n_tiles) An = tile_base(ntile);
         }
         if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
-        uint8_t* sa = aring + slot * TC_A_SLOT;
+        uint8_t* sa = aring + slot * P::A_SLOT;
         if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) return false;
-        {
-#pragma unroll
-          for (int j = 0; j < NCH; ++j) {
-            if (!cok[j]) continue;
-            uint32_t hi[4], lo[4];
-#pragma unroll
-            for (int h = 0; h < KPC / 2; ++h) {
-              const float4 x = vc[j][h];
-              const __nv_bfloat162 h0 = __floats2bfloat162_rn(x.x, x.y);
-              const __nv_bfloat162 h1 = __floats2bfloat162_rn(x.z, x.w);
-              const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-              const __nv_bfloat162 l0 = __floats2bfloat162_rn(x.x - f0.x, x.y - f0.y);
-              const __nv_bfloat162 l1 = __floats2bfloat162_rn(x.z - f1.x, x.w - f1.y);
-              hi[2 * h] = *reinterpret_cast<const uint32_t*>(&h0);
-              hi[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&h1);
-              lo[2 * h] = *reinterpret_cast<const uint32_t*>(&l0);
-              lo[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&l1);
-            }
-            *reinterpret_cast<uint4*>(sa + soff[j]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(sa + a_plane + soff[j]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-          }
-        }
+        if (rok) put3m<MODE>(sa, row, h, vc);
         fence_proxy_async();
         mbar_arrive(smem_u32(&fullA[slot]));
         if (++slot == na) {
           slot = 0;
           ph ^= 1;
         }
-        if (ntile != tile) At = An;
         tile = ntile;
         kc = nkc;
         return true;
       };
-      if (tile < a.n_tiles) issue(v0, At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
+      if (tile < a.n_tiles) issue(v0, An + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
       while (tile < a.n_tiles) {
         if (!body(v0, v1) || tile >= a.n_tiles) break;
         if (!body(v1, v0)) break;
+      }
+    } else {
+      // Thread lt owns tile row (lt % 128) and every other 16-byte chunk of it, so
+      // the 32 lanes of a warp write 32 consecutive rows: four whole 8 x 16-byte
+      // core matrices, free of bank conflicts whatever A's storage order.  A chunk
+      // holds KPC consecutive complex k (2 for TF32, 4 for BF16); when the lowest
+      // k bit is memory position 0 those are contiguous in global memory too.
+      constexpr int KPC = 16 / (2 * T::ESZ);
+      constexpr int CPR = TC_KP * T::ESZ / 16;      // 16-byte chunks per row
+      constexpr int NCH = TC_M * CPR / TC_LOAD_THREADS;  // chunks per thread per stage
+      const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
+      const int tkv = 1 << g.tk;
+      const bool kadj = g.nk > 0 && g.a_kpos[0] == 0;
+      // lanes walk the k chunks of a row when A's lowest memory bit is a k bit,
+      // else they walk rows; either way the swizzled stores are conflict-free
+      const bool klanes = kadj;
+      int64_t goff[NCH][KPC];   // offset of each complex of each chunk, -1 = padding
+      int soff[NCH];
+      bool cok[NCH];
+  #pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int q = lt + j * TC_LOAD_THREADS;
+        const int row = klanes ? q / CPR : q % TC_M;
+        const int c = klanes ? q % CPR : q / TC_M;
+        cok[j] = row < (1 << g.tm);
+        soff[j] = tc_elem_off(row, c * KPC * 2, T::ESZ);
+        const int64_t roff = deposit_hi((uint64_t)row, g.a_mpos, 0, g.tm);
+  #pragma unroll
+        for (int i = 0; i < KPC; ++i) {
+          const int k = c * KPC + i;
+          goff[j][i] = (cok[j] && k < tkv) ? roff + deposit_hi((uint64_t)k, g.a_kpos, 0, g.tk) : -1;
+        }
+      }
+      auto tile_base = [&](int64_t tile) -> const float2* {
+        const int64_t rest = tile / a.n_split / a.n_nt;
+        const int mt = (int)(rest % a.n_mt);
+        const int inst = (int)(rest / a.n_mt);
+        return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) + deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
+      };
+      int slot = 0;
+      uint32_t ph = 0;
+      if constexpr (MODE == TC_TF32) {
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+          const float2* At = tile_base(tile);
+          const int kc0 = (int)(tile % a.n_split) * kc_per;
+          for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
+            const float2* Ak = At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
+            uint8_t* sa = aring + slot * P::A_SLOT;
+            if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
+            {
+              const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
+  #pragma unroll
+              for (int j = 0; j < NCH; ++j) {
+                if (!cok[j]) continue;
+                if (v16 && goff[j][1] >= 0) {
+                  cp_async16(smem_u32(sa + soff[j]), Ak + goff[j][0]);
+                } else {
+  #pragma unroll
+                  for (int i = 0; i < KPC; ++i)
+                    if (goff[j][i] >= 0) cp_async8(smem_u32(sa + soff[j] + 8 * i), Ak + goff[j][i]);
+                }
+              }
+            }
+            cp_async_arrive_noinc(smem_u32(&fullA[slot]));
+            if (++slot == na) {
+              slot = 0;
+              ph ^= 1;
+            }
+          }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+      } else {
+        // BF16X3: the next slot's loads are in flight in registers while the
+        // current one is split into hi/lo and stored
+        float4 v0[NCH][KPC / 2], v1[NCH][KPC / 2];
+        auto issue = [&](float4(&v)[NCH][KPC / 2], const float2* Ak) {
+          const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
+  #pragma unroll
+          for (int j = 0; j < NCH; ++j)
+  #pragma unroll
+            for (int h = 0; h < KPC / 2; ++h) {
+              const int64_t o0 = goff[j][2 * h], o1 = goff[j][2 * h + 1];
+              if (v16 && o1 >= 0) {
+                v[j][h] = __ldg(reinterpret_cast<const float4*>(Ak + o0));
+              } else {
+                const float2 x = o0 >= 0 ? __ldg(Ak + o0) : make_float2(0.f, 0.f);
+                const float2 y = o1 >= 0 ? __ldg(Ak + o1) : make_float2(0.f, 0.f);
+                v[j][h] = make_float4(x.x, x.y, y.x, y.y);
+              }
+            }
+        };
+        int64_t tile = blockIdx.x;
+        int kc = (int)(tile % a.n_split) * kc_per;
+        const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
+        const float2* An = At;     // base of the tile of the prefetched slot
+        auto body = [&](float4(&vc)[NCH][KPC / 2], float4(&vn)[NCH][KPC / 2]) -> bool {
+          int64_t ntile = tile;
+          int nkc = kc + 1;
+          if (nkc == (int)(tile % a.n_split) * kc_per + kc_per) {
+            ntile += gridDim.x;
+            nkc = (int)(ntile % a.n_split) * kc_per;
+            if (ntile < a.n_tiles) An = tile_base(ntile);
+          }
+          if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
+          uint8_t* sa = aring + slot * P::A_SLOT;
+          if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) return false;
+          {
+  #pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+              if (!cok[j]) continue;
+              uint32_t hi[4], lo[4];
+  #pragma unroll
+              for (int h = 0; h < KPC / 2; ++h) {
+                const float4 x = vc[j][h];
+                const __nv_bfloat162 h0 = __floats2bfloat162_rn(x.x, x.y);
+                const __nv_bfloat162 h1 = __floats2bfloat162_rn(x.z, x.w);
+                const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+                const __nv_bfloat162 l0 = __floats2bfloat162_rn(x.x - f0.x, x.y - f0.y);
+                const __nv_bfloat162 l1 = __floats2bfloat162_rn(x.z - f1.x, x.w - f1.y);
+                hi[2 * h] = *reinterpret_cast<const uint32_t*>(&h0);
+                hi[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&h1);
+                lo[2 * h] = *reinterpret_cast<const uint32_t*>(&l0);
+                lo[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&l1);
+              }
+              *reinterpret_cast<uint4*>(sa + soff[j]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+              *reinterpret_cast<uint4*>(sa + a_plane + soff[j]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+          }
+          fence_proxy_async();
+          mbar_arrive(smem_u32(&fullA[slot]));
+          if (++slot == na) {
+            slot = 0;
+            ph ^= 1;
+          }
+          if (ntile != tile) At = An;
+          tile = ntile;
+          kc = nkc;
+          return true;
+        };
+        if (tile < a.n_tiles) issue(v0, At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
+        while (tile < a.n_tiles) {
+          if (!body(v0, v1) || tile >= a.n_tiles) break;
+          if (!body(v1, v0)) break;
+        }
       }
     }
   } else if (warp == TC_MMA_WARP) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
+      // N of one MMA: all N' = 2 tn_c real columns (4M), or tn_c per product (3M)
+      const int mma_n = CM == 4 ? ncp : a.tn_c;
       const uint32_t idesc = (1u << 4) | ((uint32_t)T::FMT << 7) | ((uint32_t)T::FMT << 10) |
-                             ((uint32_t)(ncp >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+                             ((uint32_t)(mma_n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
       const uint32_t sbo = tc_sbo(T::ESZ);
       const uint32_t lay = T::ESZ == 4 ? 2u : 4u;
       int sa_i = 0, sb_i = 0;
@@ -710,11 +979,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int64_t it = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++it) {
-        const int acc = (int)(it & 1);
-        const uint32_t aph = (uint32_t)((it >> 1) & 1);
+        const int acc = a.n_acc == 2 ? (int)(it & 1) : 0;
+        const uint32_t aph = (uint32_t)((a.n_acc == 2 ? (it >> 1) : it) & 1);
         if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ncp);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * setw);
         for (int kc = 0; kc < kc_per; ++kc) {
           if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err) ||
               !mbar_wait(smem_u32(&fullB[sb_i]), phb, abort_flag, a.err)) {
@@ -723,21 +992,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
           fence_proxy_async();
           tc_fence_after();
-          const uint32_t sa = smem_u32(aring + sa_i * TC_A_SLOT);
+          const uint32_t sa = smem_u32(aring + sa_i * P::A_SLOT);
           const uint32_t sb = smem_u32(bring + sb_i * b_slot);
+          // one MMA K step = 32 bytes of every plane row: advance inside the swizzle atom
+          auto mma = [&](uint32_t d, uint32_t a_addr, uint32_t b_addr, uint32_t accumulate) {
+            tc_mma<MODE>(d, smem_desc(a_addr, sbo, lay), smem_desc(b_addr, sbo, lay), idesc, accumulate);
+          };
+          if constexpr (CM == 4) {
 #pragma unroll
-          for (int j = 0; j < TC_KP * T::ESZ / 32; ++j) {
-            // one MMA K step = 32 bytes of every row: advance inside the swizzle atom
-            const uint32_t koff = (uint32_t)j * 32u;
-            const uint32_t first = (kc > 0 || j > 0) ? 1u : 0u;
-            const uint64_t ad = smem_desc(sa + koff, sbo, lay);
-            const uint64_t bd = smem_desc(sb + koff, sbo, lay);
-            tc_mma<MODE>(d_tmem, ad, bd, idesc, first);
-            if constexpr (MODE == TC_BF16X3) {
-              const uint64_t bdl = smem_desc(sb + b_plane + koff, sbo, lay);
-              const uint64_t adl = smem_desc(sa + a_plane + koff, sbo, lay);
-              tc_mma<MODE>(d_tmem, ad, bdl, idesc, 1u);
-              tc_mma<MODE>(d_tmem, adl, bd, idesc, 1u);
+            for (int j = 0; j < TC_KP * T::ESZ / 32; ++j) {
+              const uint32_t koff = (uint32_t)j * 32u;
+              const uint32_t first = (kc > 0 || j > 0) ? 1u : 0u;
+              mma(d_tmem, sa + koff, sb + koff, first);
+              if constexpr (MODE != TC_TF32) {   // hi*hi + hi*lo + lo*hi
+                mma(d_tmem, sa + koff, sb + b_plane + koff, 1u);
+                mma(d_tmem, sa + a_plane + koff, sb + koff, 1u);
+              }
+            }
+          } else {
+            // T1, T2, T3 in consecutive tn_c-column blocks of the accumulator set
+            const uint32_t d1 = d_tmem, d2 = d_tmem + (uint32_t)a.tn_c, d3 = d_tmem + 2u * (uint32_t)a.tn_c;
+            if constexpr (MODE == TC_TF32) {
+              // planes [Ar | Ai], [As | -] against [Br | Bi], [Bs | 0]: two K steps of 8
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                const uint32_t ko = (uint32_t)j * 32u;
+                const uint32_t first = (kc > 0 || j > 0) ? 1u : 0u;
+                mma(d1, sa + ko, sb + ko, first);
+                mma(d2, sa + 64u + ko, sb + 64u + ko, first);
+                mma(d3, sa + a_plane + ko, sb + b_plane + ko, first);
+              }
+            } else {
+              // planes H = [Ar_hi | Ai_hi], L = [Ar_lo | Ai_lo], S = [As_hi | As_lo]
+              const uint32_t first = kc > 0 ? 1u : 0u;
+              const uint32_t H = sa, L = sa + a_plane, S = sa + 2 * a_plane;
+              const uint32_t BH = sb, BL = sb + b_plane, BS = sb + 2 * b_plane;
+              mma(d1, H, BH, first);
+              mma(d1, H, BL, 1u);
+              mma(d1, L, BH, 1u);
+              mma(d2, H + 32u, BH + 32u, first);
+              mma(d2, H + 32u, BL + 32u, 1u);
+              mma(d2, L + 32u, BH + 32u, 1u);
+              mma(d3, S, BS, first);
+              mma(d3, S, BS + 32u, 1u);
+              mma(d3, S + 32u, BS, 1u);
             }
           }
           tc_commit(smem_u32(&emptyA[sa_i]));
@@ -788,8 +1086,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     }
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-      const int acc = (int)(it & 1);
-      const uint32_t aph = (uint32_t)((it >> 1) & 1);
+      const int acc = a.n_acc == 2 ? (int)(it & 1) : 0;
+      const uint32_t aph = (uint32_t)((a.n_acc == 2 ? (it >> 1) : it) & 1);
       if (!mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, a.err)) break;
       tc_fence_after();
       const int64_t otile = tile / a.n_split;
@@ -803,9 +1101,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
                   deposit_hi((uint64_t)nt, g.c_npos, a.tnb, g.nn);
       const bool row_ok = row < tmv;
       const int64_t crow = offCm[row];
-      for (int c0 = 0; c0 < ncp; c0 += 32) {
+      const uint32_t tl = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * setw);
+      for (int c0 = 0; c0 < ncp; c0 += 32) {   // 16 complex columns per pass
         float v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * ncp + c0), v);
+        if constexpr (CM == 4) {
+          tmem_ld32(tl + (uint32_t)c0, v);
+        } else {
+          // Re = T1 - T2, Im = T3 - T1 - T2
+          float t[48];
+          const uint32_t cc = (uint32_t)(c0 / 2);
+          tmem_ld16x3(tl + cc, tl + (uint32_t)a.tn_c + cc, tl + 2u * (uint32_t)a.tn_c + cc, t);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            v[2 * j] = t[j] - t[16 + j];
+            v[2 * j + 1] = t[32 + j] - t[j] - t[16 + j];
+          }
+        }
         if (a.epi_ok) {
           // stage the warp's 32 x 16 block, then write it in C's memory order:
           // element e = lane + 32 i has its bits on C's lowest positions first

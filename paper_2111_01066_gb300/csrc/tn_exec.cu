@@ -34,12 +34,14 @@ enum KernelId {
   K_SIMT_256x4 = 2,   // TM 256, TN 4, TK 16
   K_TC_TF32 = 3,      // tcgen05 kind::tf32, tile 128 x (<=128 complex), k chunk 16
   K_TC_BF16X3 = 4,    // tcgen05 kind::f16 bf16 hi/lo split
+  K_TC_TF32_3M = 5,   // the same with 3M products (three accumulators per tile)
+  K_TC_BF16X3_3M = 6,
   K_COUNT
 };
 struct KernelCfg {
   int tm, tn, tk;  // log2 tile extents
 };
-static const KernelCfg kCfg[K_COUNT] = {{6, 6, 3}, {7, 4, 4}, {8, 2, 4}, {7, 7, 4}, {7, 7, 4}};
+static const KernelCfg kCfg[K_COUNT] = {{6, 6, 3}, {7, 4, 4}, {8, 2, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}};
 
 static int pick_simt(const StepDesc& d) {
   if (d.nn >= 5 && d.nm >= 5) return K_SIMT_64x64;
@@ -135,14 +137,34 @@ struct StepLaunch {
   int kid = 0;
   GemmArgs g;
   TcArgs tc;
-  alignas(64) CUtensorMap tma;
+  CUtensorMap tma;   // 64-byte aligned by its own declaration
   int64_t ws_bytes = 0;
   int64_t split_off = 0;   // split-K partials inside the workspace
   int64_t c_total = 0;     // elements of C (all instances)
   int smem = 0;
 };
 
-static bool is_tc(int kid) { return kid == K_TC_TF32 || kid == K_TC_BF16X3; }
+static bool is_tc(int kid) { return kid >= K_TC_TF32 && kid <= K_TC_BF16X3_3M; }
+static bool tc_is_3m(int kid) { return kid == K_TC_TF32_3M || kid == K_TC_BF16X3_3M; }
+struct TcGeom {   // the plane geometry of TcPl<MODE, CM> for a kernel id
+  int planes, rows_per_col, a_slot, min_tn_c, esz;
+};
+static TcGeom tc_geom(int kid) {
+  switch (kid) {
+    case K_TC_TF32:
+      return {TcPl<TC_TF32, 4>::PLANES, TcPl<TC_TF32, 4>::ROWS_PER_COL, TcPl<TC_TF32, 4>::A_SLOT,
+              TcPl<TC_TF32, 4>::MIN_TN_C, 4};
+    case K_TC_BF16X3:
+      return {TcPl<TC_BF16X3, 4>::PLANES, TcPl<TC_BF16X3, 4>::ROWS_PER_COL, TcPl<TC_BF16X3, 4>::A_SLOT,
+              TcPl<TC_BF16X3, 4>::MIN_TN_C, 2};
+    case K_TC_TF32_3M:
+      return {TcPl<TC_TF32, 3>::PLANES, TcPl<TC_TF32, 3>::ROWS_PER_COL, TcPl<TC_TF32, 3>::A_SLOT,
+              TcPl<TC_TF32, 3>::MIN_TN_C, 4};
+    default:
+      return {TcPl<TC_BF16X3, 3>::PLANES, TcPl<TC_BF16X3, 3>::ROWS_PER_COL, TcPl<TC_BF16X3, 3>::A_SLOT,
+              TcPl<TC_BF16X3, 3>::MIN_TN_C, 2};
+  }
+}
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -207,13 +229,14 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   TcArgs& t = L.tc;
   t.g = g;
   t.tnb = g.tn;
-  t.tn_c = std::max(8, 1 << g.tn);
+  const TcGeom geo = tc_geom(kid);
+  t.tn_c = std::max(geo.min_tn_c, 1 << g.tn);
   t.n_mt = 1 << (g.nm - g.tm);
   t.n_nt = 1 << (g.nn - g.tn);
   t.n_kc = 1 << (g.nk - g.tk);
   t.n_tiles = (int64_t)g.n_inst * t.n_mt * t.n_nt;
-  const int esz = kid == K_TC_TF32 ? 4 : 2, npl = kid == K_TC_TF32 ? 1 : 2;
-  const int b_plane = tc_plane_bytes(2 * t.tn_c, esz);
+  const int b_plane = tc_plane_bytes(geo.rows_per_col * t.tn_c, geo.esz);
+  const int npl = geo.planes;
   L.ws_bytes = (int64_t)g.n_inst * t.n_nt * t.n_kc * npl * b_plane;
   // split-K when the output tiles cannot fill the SMs and the k loop is long
   t.n_split = 1;
@@ -235,9 +258,11 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   const int b_slot = npl * b_plane;
   const int budget = 220 * 1024 - 4096 - TC_EPI_BYTES;
   t.nbs = b_slot <= 16384 ? TC_MAX_B : 3;
-  t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / TC_A_SLOT);
+  t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
   t.fa_count = (t.a_tma && kid == K_TC_TF32) ? 1 : TC_LOAD_THREADS;
-  L.smem = std::max(t.na * TC_A_SLOT + t.nbs * b_slot + 4096 + TC_EPI_BYTES + 1024, TC_MIN_SMEM);
+  // two accumulator sets when they fit the 512 TMEM columns
+  t.n_acc = 2 * (tc_is_3m(kid) ? 3 : 2) * t.tn_c <= TC_TMEM_COLS ? 2 : 1;
+  L.smem = std::max(t.na * geo.a_slot + t.nbs * b_slot + 4096 + TC_EPI_BYTES + 1024, TC_MIN_SMEM);
   // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
   t.epi_ok = 0;
   if (g.tm >= 5 && g.tn >= 4) {
@@ -261,6 +286,20 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   return L;
 }
 
+template <int MODE, int CM>
+static void launch_tc(const TcArgs& t, const StepLaunch& L, int pblocks, int grid, cudaStream_t s) {
+  if constexpr (CM == 4)
+    k_tc_prep_b<MODE><<<pblocks, 256, 0, s>>>(t);
+  else
+    k_tc_prep_b3<MODE><<<pblocks, 256, 0, s>>>(t);
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(k_cgemm_tc<MODE, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  k_cgemm_tc<MODE, CM><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
+}
+
 static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s) {
   if (!is_tc(L.kid)) {
     launch_simt(L.g, L.kid, s);
@@ -274,22 +313,19 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
   const int64_t prep_total = (int64_t)t.g.n_inst * t.n_nt * t.n_kc * TC_TK * t.tn_c;
   const int pblocks = (int)std::min<int64_t>((prep_total + 255) / 256, (int64_t)sm_count() * 16);
   const int grid = (int)std::min<int64_t>(t.n_tiles, sm_count());
-  if (L.kid == K_TC_TF32) {
-    k_tc_prep_b<TC_TF32><<<pblocks, 256, 0, s>>>(t);
-    static bool attr = false;
-    if (!attr) {
-      CK(cudaFuncSetAttribute(k_cgemm_tc<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      attr = true;
-    }
-    k_cgemm_tc<TC_TF32><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
-  } else {
-    k_tc_prep_b<TC_BF16X3><<<pblocks, 256, 0, s>>>(t);
-    static bool attr = false;
-    if (!attr) {
-      CK(cudaFuncSetAttribute(k_cgemm_tc<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      attr = true;
-    }
-    k_cgemm_tc<TC_BF16X3><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
+  switch (L.kid) {
+    case K_TC_TF32:
+      launch_tc<TC_TF32, 4>(t, L, pblocks, grid, s);
+      break;
+    case K_TC_BF16X3:
+      launch_tc<TC_BF16X3, 4>(t, L, pblocks, grid, s);
+      break;
+    case K_TC_TF32_3M:
+      launch_tc<TC_TF32, 3>(t, L, pblocks, grid, s);
+      break;
+    default:
+      launch_tc<TC_BF16X3, 3>(t, L, pblocks, grid, s);
+      break;
   }
   if (t.n_split > 1) {
     const int rb = (int)std::min<int64_t>((L.c_total + 255) / 256, (int64_t)sm_count() * 8);
@@ -320,14 +356,19 @@ struct DeviceState {
   bool eager_done = false;
 };
 
-// Tensor-core kernels for every step with enough work in the TF32 / BF16X3
-// modes; tiny steps (and the FP32 mode) on the CUDA cores.
-static int pick_kernel(int precision, const StepDesc& d) {
+static int tc_kernel(int precision, int cmult) {
+  if (precision == TN_PREC_TF32) return cmult == 3 ? K_TC_TF32_3M : K_TC_TF32;
+  return cmult == 3 ? K_TC_BF16X3_3M : K_TC_BF16X3;
+}
+// Tensor-core kernels (4M or 3M products) for every step with enough work in
+// the TF32 / BF16X3 modes; tiny steps (and the FP32 mode) on the CUDA cores,
+// which always form 4M products in FP32.
+static int pick_kernel(int precision, int cmult, const StepDesc& d) {
   if (precision == TN_PREC_FP32) return pick_simt(d);
   if (precision == TN_PREC_FP16X3) fail(TN_ERR_UNSUPPORTED, "FP16X3 is not built");
   const int work = d.nm + d.nk + d.nn + d.nb;
   if (work < 20 || d.nm < 4) return pick_simt(d);
-  return precision == TN_PREC_TF32 ? K_TC_TF32 : K_TC_BF16X3;
+  return tc_kernel(precision, cmult);
 }
 
 static void ensure_device(Plan& p) {
@@ -381,7 +422,7 @@ static void ensure_device(Plan& p) {
                     ((int64_t)1 << (d.nk + d.nn + d.nb)) == d.b_elems &&
                     ((int64_t)1 << (d.nm + d.nn + d.nb)) == d.c_elems;
     if (!ok) fail(TN_ERR_PLAN, "internal: step operand outside its extent");
-    const int kid = pick_kernel(p.opts.precision, d);
+    const int kid = pick_kernel(p.opts.precision, p.opts.complex_mult, d);
     ds->launches.push_back(make_launch(
         make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off, 1 << d.nb), kid,
         64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true));
@@ -625,7 +666,7 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
     double best = time_launch(ds.launches[i]);
     std::vector<std::array<int, 3>> cands;   // kernel, tile width (log2 complex columns), write-back
     const bool tc_mode = p.opts.precision == TN_PREC_TF32 || p.opts.precision == TN_PREC_BF16X3;
-    const int tc_kid = p.opts.precision == TN_PREC_TF32 ? K_TC_TF32 : K_TC_BF16X3;
+    const int tc_kid = tc_kernel(p.opts.precision, p.opts.complex_mult);
     if (tc_mode && d.nm >= 4)
       for (int tn_log : {7, 6, 5})
         if (tn_log <= std::max(3, d.nn))
@@ -792,7 +833,8 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   if (batch < 1 || batch > 65535) fail(TN_ERR_ARG, "tn_contract_pair: batch must be in [1, 65535]");
   if (precision < TN_PREC_FP32 || precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
   if (cmult != 3 && cmult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
-  if (cmult == 3) fail(TN_ERR_UNSUPPORTED, "3M complex products are not built; use complex_mult = 4");
+  if (cmult == 3 && precision == TN_PREC_FP32)
+    fail(TN_ERR_UNSUPPORTED, "the FP32 CUDA-core path forms 4M products only; 3M needs TF32 or BF16X3");
   std::vector<int> A(aw, aw + ar), B(bw, bw + br), Cw(cw, cw + cr);
   auto has = [](const std::vector<int>& v, int w) { return std::find(v.begin(), v.end(), w) != v.end(); };
   for (size_t i = 0; i < A.size(); ++i)
@@ -832,7 +874,7 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   d.b_elems = (int64_t)1 << br;
   d.c_elems = (int64_t)1 << cr;
   d.nb = 0;
-  const int kid = pick_kernel(precision, d);
+  const int kid = pick_kernel(precision, cmult, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                          reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
   StepLaunch L = make_launch(g, kid, ar, batch, batch * d.c_elems, true);
@@ -906,6 +948,8 @@ extern "C" tn_status tn_contract_pair_noalloc(const float* a, const int32_t* aw,
   if (batch < 1 || batch > 65535) fail(TN_ERR_ARG, "tn_contract_pair_noalloc: batch must be in [1, 65535]");
   if (precision < TN_PREC_FP32 || precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
   if (cmult != 3 && cmult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
+  if (cmult == 3 && precision == TN_PREC_FP32)
+    fail(TN_ERR_UNSUPPORTED, "the FP32 CUDA-core path forms 4M products only; 3M needs TF32 or BF16X3");
   std::vector<int> A(aw, aw + ar), B(bw, bw + br), Cw(cw, cw + cr);
   auto has = [](const std::vector<int>& v, int w) { return std::find(v.begin(), v.end(), w) != v.end(); };
   auto dup = [](const std::vector<int>& v) {
@@ -945,7 +989,7 @@ extern "C" tn_status tn_contract_pair_noalloc(const float* a, const int32_t* aw,
   d.a_elems = (int64_t)1 << ar;
   d.b_elems = (int64_t)1 << br;
   d.c_elems = (int64_t)1 << cr;
-  const int kid = pick_kernel(precision, d);
+  const int kid = pick_kernel(precision, cmult, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                          reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
   StepLaunch L = make_launch(g, kid, ar, batch);

@@ -533,7 +533,8 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
     fail(TN_ERR_ARG, "max_log2_intermediate must be in [1, 36]");
   if (o.precision < TN_PREC_FP32 || o.precision > TN_PREC_FP16X3) fail(TN_ERR_ARG, "unknown precision");
   if (o.complex_mult != 3 && o.complex_mult != 4) fail(TN_ERR_ARG, "complex_mult must be 3 or 4");
-  if (o.complex_mult == 3) fail(TN_ERR_UNSUPPORTED, "3M complex products are not built; use complex_mult = 4");
+  if (o.complex_mult == 3 && o.precision == TN_PREC_FP32)
+    fail(TN_ERR_UNSUPPORTED, "the FP32 CUDA-core path forms 4M products only; 3M needs TF32 or BF16X3");
   if (o.min_log2_slices < 0 || o.min_log2_slices > 48) fail(TN_ERR_ARG, "min_log2_slices out of range");
   const int n = net.n_qubits;
   if (n < 64 && (o.open_mask >> n) != 0) fail(TN_ERR_ARG, "open_mask names a qubit >= n_qubits");

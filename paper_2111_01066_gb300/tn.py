@@ -257,7 +257,8 @@ class Plan:
         _check(load().tn_contract_slices(self.handle, slice_first, slice_count, bs, len(bitstrings),
                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
 
-    KERNELS = {0: "simt64x64", 1: "simt128x16", 2: "simt256x4", 3: "tc_tf32", 4: "tc_bf16x3"}
+    KERNELS = {0: "simt64x64", 1: "simt128x16", 2: "simt256x4", 3: "tc_tf32", 4: "tc_bf16x3",
+               5: "tc_tf32_3m", 6: "tc_bf16x3_3m"}
 
     def step_times(self, reps: int = 3, stream=None) -> List[Tuple[float, str]]:
         """(mean device milliseconds per launch, kernel name) of every step."""

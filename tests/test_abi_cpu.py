@@ -59,8 +59,10 @@ def test_plan_options_validated(tn):
     with pytest.raises(tn.TnError):
         tn.Plan(net, open_mask=om, complex_mult=5)
     with pytest.raises(tn.TnError) as e:
-        tn.Plan(net, open_mask=om, complex_mult=3)
+        tn.Plan(net, open_mask=om, complex_mult=3)          # the FP32 path is 4M only
     assert e.value.status == tn.TN_ERR_UNSUPPORTED
+    for prec in ("tf32", "bf16x3"):                         # 3M on the tensor cores
+        assert tn.Plan(net, open_mask=om, precision=prec, complex_mult=3, trials=2).info()["n_steps"] > 0
     with pytest.raises(tn.TnError) as e:
         tn.Plan(net, open_mask=om, max_log2_intermediate=6)   # 12 open qubits > 2^6
     assert e.value.status == tn.TN_ERR_PLAN

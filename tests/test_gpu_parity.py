@@ -125,22 +125,22 @@ def test_c1_range_errors(env):
     assert float(out.abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
-def test_c2_against_golden(env, prec):
+@pytest.mark.parametrize("prec,cm", [("fp32", 4), ("tf32", 4), ("bf16x3", 4), ("tf32", 3), ("bf16x3", 3)])
+def test_c2_against_golden(env, prec, cm):
     tn, torch = env
     from tests.golden.make_golden import read
     want = read("c2")
     circ, om, cb = rqcgen.config_circuit("c2")
-    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=26, precision=prec)
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=26, precision=prec, complex_mult=cm)
     n_sl = 1 << plan.info()["log2_slices"]
     got = _run_plan(tn, torch, plan, 0, n_sl, [cb], 10)
     err = _relerr(got, want)
-    print(f"c2 {prec}: rel amp err {err:.3e}")
+    print(f"c2 {prec} {cm}M: rel amp err {err:.3e}")
     assert err < PLAN_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "fp32"])
-def test_c3_all_slices_against_golden(env, prec):
+@pytest.mark.parametrize("prec,cm", [("bf16x3", 4), ("bf16x3", 3), ("tf32", 4), ("fp32", 4)])
+def test_c3_all_slices_against_golden(env, prec, cm):
     """The benchmark workload at full size: 42 qubits, 16 cycles, 2^12 slices
     contracted in the configuration bench.py times, summed, against the oracle's
     plan-independent amplitudes of the whole batch; XEB of the batch too."""
@@ -151,7 +151,7 @@ def test_c3_all_slices_against_golden(env, prec):
     cfg = rqcgen.CONFIGS["c3"]
     circ, om, cb = rqcgen.config_circuit("c3")
     plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
-                   min_log2_slices=cfg["log2_slices"], precision=prec)
+                   min_log2_slices=cfg["log2_slices"], precision=prec, complex_mult=cm)
     assert plan.info()["log2_slices"] == 12
     out = torch.zeros(2 << 12, dtype=torch.float64, device="cuda")
     plan.contract_slices(0, 1 << 12, [cb], out)
@@ -160,7 +160,7 @@ def test_c3_all_slices_against_golden(env, prec):
     err = _relerr(got, want)
     f = tn.xeb(out.view(torch.complex128), circ.n_qubits)
     xerr = abs(f - oxeb.linear_xeb(want, circ.n_qubits))
-    print(f"c3 {prec}: rel amp err {err:.3e}, xeb err {xerr:.3e}")
+    print(f"c3 {prec} {cm}M: rel amp err {err:.3e}, xeb err {xerr:.3e}")
     assert err < PLAN_TOL[prec]
     assert xerr < (1e-3 if prec != "tf32" else 5e-2)
 
@@ -216,6 +216,49 @@ def test_contract_pair(env, shape, batch, prec):
         want = pairwise.contract_pair(a[i], a_w, b[i], b_w, c_w)
         scale = math.sqrt(2 ** nk) * np.sqrt(np.mean(np.abs(a[i]) ** 2) * np.mean(np.abs(b[i]) ** 2))
         assert np.max(np.abs(got[i] - want)) <= PAIR_TOL[prec] * max(scale, 1e-30) * 8
+
+
+PAIR_TOL_3M = {"tf32": 6e-3, "bf16x3": 1e-4}   # 3M: Im = T3 - T1 - T2 loses a few bits more
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+@pytest.mark.parametrize("shape", [(5, 4, 4), (9, 5, 3), (13, 4, 4)] + TC_SHAPES)
+@pytest.mark.parametrize("layout", ["random", "kfast"])
+@pytest.mark.parametrize("batch", [1, 3])
+def test_contract_pair_3m(env, shape, layout, batch, prec):
+    """3M products (T1 = ArBr, T2 = AiBi, T3 = (Ar+Ai)(Br+Bi); Re = T1 - T2,
+    Im = T3 - T1 - T2) on the tensor cores, A gathered (random storage order)
+    or fetched by TMA ([k..., m...] order), against the FP64 contraction."""
+    tn, torch = env
+    nm, nk, nn = shape
+    rng = np.random.default_rng(hash((shape, layout)) % 1000 + batch)
+    wires = list(range(200, 200 + nm + nk + nn))
+    m_w, k_w, n_w = wires[:nm], wires[nm:nm + nk], wires[nm + nk:]
+    if layout == "random":
+        a_w, b_w = list(rng.permutation(m_w + k_w)), list(rng.permutation(k_w + n_w))
+    else:
+        a_w, b_w = k_w + m_w, k_w + n_w
+    c_w = list(rng.permutation(m_w + n_w))
+    a = (rng.normal(size=(batch, 2 ** len(a_w))) + 1j * rng.normal(size=(batch, 2 ** len(a_w)))) / 2
+    b = (rng.normal(size=(batch, 2 ** len(b_w))) + 1j * rng.normal(size=(batch, 2 ** len(b_w)))) / 2
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    ta, tb = dev(a), dev(b)
+    tc = torch.empty((batch, 2 ** len(c_w)), dtype=torch.complex64, device="cuda")
+    tn.contract_pair(ta, a_w, tb, b_w, tc, c_w, batch=batch, precision=prec, complex_mult=3)
+    torch.cuda.synchronize()
+    got = tc.cpu().numpy()
+    for i in range(batch):
+        want = pairwise.contract_pair(a[i], a_w, b[i], b_w, c_w)
+        scale = math.sqrt(2 ** nk) * np.sqrt(np.mean(np.abs(a[i]) ** 2) * np.mean(np.abs(b[i]) ** 2))
+        assert np.max(np.abs(got[i] - want)) <= PAIR_TOL_3M[prec] * max(scale, 1e-30) * 8
+
+
+def test_contract_pair_3m_fp32_unsupported(env):
+    tn, torch = env
+    x = torch.zeros(1 << 10, dtype=torch.complex64, device="cuda")
+    with pytest.raises(tn.TnError) as e:
+        tn.contract_pair(x, list(range(10)), x, list(range(10)), x[:1], [], precision="fp32", complex_mult=3)
+    assert e.value.status == tn.TN_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("rank", [1, 2, 5, 9, 14, 20])
