@@ -198,7 +198,9 @@ def complex_peak_tflops(kernel: str, peaks: dict) -> float:
     real = {"tc_tf32": (bf16 / 2, 4),          # TF32 dense = half the BF16 rate, 4M
             "tc_tf32_3m": (bf16 / 2, 3),
             "tc_bf16x3": (bf16, 12),           # 3 bf16 products per real product, 4M
-            "tc_bf16x3_3m": (bf16, 9)}
+            "tc_bf16x3_3m": (bf16, 9),
+            "tc_fp16x3": (bf16, 12),           # FP16 dense runs at the BF16 rate
+            "tc_fp16x3_3m": (bf16, 9)}
     if kernel in real:
         p, r = real[kernel]
         return p * 8 / (2 * r)
@@ -543,7 +545,7 @@ def main() -> int:
     if args.compare_fp32:
         # the plain FP32 path, TF32, and the other complex product (4M / 3M) of this precision
         alts = [("fp32", 4), ("tf32", 4)]
-        if prec in ("tf32", "bf16x3"):
+        if prec in ("tf32", "bf16x3", "fp16x3"):
             alts.append((prec, 7 - args.complex_mult))
         for other, ocm in alts:
             if (other, ocm) == (prec, args.complex_mult):

@@ -99,7 +99,12 @@ void tn_network_destroy(tn_network_t* net);
 #define TN_PREC_FP32    0  /* complex64 SIMT FMA (the plain FP32 path) */
 #define TN_PREC_TF32    1  /* tcgen05 kind::tf32, FP32 accumulate */
 #define TN_PREC_BF16X3  2  /* tcgen05 kind::f16, bf16 hi+lo split operands, FP32 accumulate */
-#define TN_PREC_FP16X3  3  /* tcgen05 kind::f16, fp16 hi+lo split operands, FP32 accumulate */
+#define TN_PREC_FP16X3  3  /* tcgen05 kind::f16, fp16 hi+lo split operands, FP32 accumulate;
+                              every operand is scaled by a power of two that maps its largest
+                              component into [2^14, 2^15) before the split, and the product is
+                              scaled back exactly.  A plan records each intermediate's largest
+                              component in its producer's epilogue; tn_contract_pair finds A's
+                              and B's by one extra read of each */
 
 typedef struct tn_plan_opts {
     uint64_t open_mask;              /* qubits left open: 2^popcount amplitudes per batch */

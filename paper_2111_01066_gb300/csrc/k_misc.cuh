@@ -89,6 +89,15 @@ __global__ void k_root_finish(const double2* __restrict__ part, int groups, int 
 
 __global__ void k_advance(unsigned* counter) { *counter += 1u; }
 
+// Largest |re|, |im| over n complex values, raised into *out (which the caller
+// zeroes first): the FP16 split's scale of an operand without a producer.
+__global__ void k_amax(const float2* __restrict__ x, int64_t n, float* out) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, cabs_max(x[i]));
+  amax_update(out, m);   // blockDim is a multiple of 32
+}
+
 // sum_i |a_i|^2 in FP64 (one block; count is small)
 __global__ void k_xeb_sum(const double2* __restrict__ a, int64_t n, double* __restrict__ out) {
   __shared__ double red[1024];

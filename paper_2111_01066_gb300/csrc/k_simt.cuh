@@ -75,6 +75,7 @@ k_cgemm_simt(const GemmArgs g) {
   __syncthreads();
 
   const int nkc = 1 << (g.nk - g.tk);
+  float am = 0.f;   // largest component written (for the FP16 split's scaling)
   for (int inst = blockIdx.z; inst < g.n_inst; inst += gridDim.z) {
     const float2* A = g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) +
                       deposit_hi(blockIdx.x, g.a_mpos, g.tm, g.nm);
@@ -132,9 +133,13 @@ k_cgemm_simt(const GemmArgs g) {
 #pragma unroll
       for (int j = 0; j < RN; ++j) {
         const int r = tx + i * NTX, c = ty + j * NTY;
-        if (r < TMv && c < TNv) C[offCm[r] + offCn[c]] = acc[i][j];
+        if (r < TMv && c < TNv) {
+          C[offCm[r] + offCn[c]] = acc[i][j];
+          am = fmaxf(am, cabs_max(acc[i][j]));
+        }
       }
   }
+  if (g.amax_c) amax_update(g.amax_c, am);   // every thread reaches here (NT is a multiple of 32)
 }
 
 }  // namespace tnx

@@ -61,7 +61,7 @@ constexpr int TC_TMEM_COLS = 512;
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;           // 4 s per wait
 constexpr int TC_MIN_SMEM = 120 * 1024;                  // keeps one CTA per SM
 
-enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1 };
+enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_FP16X3 = 2 };
 
 template <int MODE>
 struct TcT;
@@ -72,6 +72,10 @@ struct TcT<TC_TF32> {
 template <>
 struct TcT<TC_BF16X3> {
   static constexpr int ESZ = 2, NPL = 2, FMT = 1;
+};
+template <>
+struct TcT<TC_FP16X3> {   // operands scaled by powers of two into the FP16 range
+  static constexpr int ESZ = 2, NPL = 2, FMT = 0;
 };
 
 // bytes of one operand plane per stage: rows x 32 real elements
@@ -329,11 +333,27 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 // consecutive K elements (packed low element first)
 template <int MODE>
 __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
+  if constexpr (MODE == TC_FP16X3) {
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+  }
+}
+// the operand scale of a mode: 2^s from the tensor's recorded maximum (FP16X3), else 1
+template <int MODE>
+__device__ __forceinline__ float operand_scale(const float* amax) {
+  if constexpr (MODE == TC_FP16X3)
+    return pow2f(fp16_scale_exp(amax));
+  else
+    return 1.f;
 }
 __device__ __forceinline__ void st16(uint8_t* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   *reinterpret_cast<uint4*>(p) = make_uint4(a, b, c, d);
@@ -341,7 +361,7 @@ __device__ __forceinline__ void st16(uint8_t* p, uint32_t a, uint32_t b, uint32_
 // 3M A planes for 8 consecutive complex k (k = 8h .. 8h+7 of the chunk) of tile
 // row `row`, from their values x[i] = (re, im)
 template <int MODE>
-__device__ __forceinline__ void put3m(uint8_t* sa, int row, int h, const float2 (&x)[8]) {
+__device__ __forceinline__ void put3m(uint8_t* sa, int row, int h, const float2 (&x)[8], float sc) {
   constexpr int AP = TcPl<MODE, 3>::A_PLANE;
   if constexpr (MODE == TC_TF32) {
     uint32_t r[8], i[8], s[8];
@@ -362,9 +382,9 @@ __device__ __forceinline__ void put3m(uint8_t* sa, int row, int h, const float2 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float2 u = x[2 * q], w = x[2 * q + 1];
-      split_pair<MODE>(u.x, w.x, rh[q], rl[q]);
-      split_pair<MODE>(u.y, w.y, ih[q], il[q]);
-      split_pair<MODE>(u.x + u.y, w.x + w.y, sh[q], sl[q]);
+      split_pair<MODE>(u.x * sc, w.x * sc, rh[q], rl[q]);
+      split_pair<MODE>(u.y * sc, w.y * sc, ih[q], il[q]);
+      split_pair<MODE>((u.x + u.y) * sc, (w.x + w.y) * sc, sh[q], sl[q]);
     }
     st16(sa + tc_elem_off(row, 8 * h, 2), rh[0], rh[1], rh[2], rh[3]);
     st16(sa + tc_elem_off(row, 16 + 8 * h, 2), ih[0], ih[1], ih[2], ih[3]);
@@ -393,6 +413,7 @@ __global__ void k_tc_prep_b(const TcArgs a) {
   const int per_block = ncp * CPR;              // chunks per plane
   const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
   const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
+  const float sc = operand_scale<MODE>(g.amax_b);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx % per_block);
@@ -428,13 +449,7 @@ __global__ void k_tc_prep_b(const TcArgs a) {
     } else {
       uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(vals[2 * i], vals[2 * i + 1]);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(vals[2 * i] - hf.x, vals[2 * i + 1] - hf.y);
-        hi[i] = *reinterpret_cast<const uint32_t*>(&h);
-        lo[i] = *reinterpret_cast<const uint32_t*>(&l);
-      }
+      for (int i = 0; i < 4; ++i) split_pair<MODE>(vals[2 * i] * sc, vals[2 * i + 1] * sc, hi[i], lo[i]);
       *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(dst + plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
@@ -457,6 +472,7 @@ __global__ void k_tc_prep_b3(const TcArgs a) {
   const int per_block = P::PLANES * rows * CPR;
   const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
   const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
+  const float sc = operand_scale<MODE>(g.amax_b);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t blk = idx / per_block;
@@ -505,7 +521,7 @@ __global__ void k_tc_prep_b3(const TcArgs a) {
           x1 = v.x + v.y;
         }
         uint32_t hi, lo;
-        split_pair<MODE>(x0, x1, hi, lo);
+        split_pair<MODE>(x0 * sc, x1 * sc, hi, lo);
         w[q2] = (pl == 0 || (pl == 2 && half == 0)) ? hi : lo;
       }
       st16(dst, w[0], w[1], w[2], w[3]);
@@ -515,7 +531,8 @@ __global__ void k_tc_prep_b3(const TcArgs a) {
 
 // Split-K: C[i] = sum over splits of the partials, in split order.
 __global__ void k_split_reduce(const float2* __restrict__ part, int n_split, int64_t stride,
-                               float2* __restrict__ C, int64_t n) {
+                               float2* __restrict__ C, int64_t n, float* amax_c) {
+  float am = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float2 acc = part[i];
     for (int sp = 1; sp < n_split; ++sp) {
@@ -524,7 +541,9 @@ __global__ void k_split_reduce(const float2* __restrict__ part, int n_split, int
       acc.y += v.y;
     }
     C[i] = acc;
+    am = fmaxf(am, cabs_max(acc));
   }
+  if (amax_c) amax_update(amax_c, am);   // blockDim is a multiple of 32
 }
 
 // ------------------------------------------------------------------ the GEMM
@@ -542,6 +561,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   const int setw = P::ACC_PER_COL * a.tn_c;                     // TMEM columns per accumulator set
   const int a_plane = P::A_PLANE;
   const int b_plane = tc_plane_bytes(P::ROWS_PER_COL * a.tn_c, T::ESZ);
+  // FP16X3: A and B enter scaled by 2^sa, 2^sb; the epilogue multiplies by 2^-sa 2^-sb (exact)
+  const float sc_a = operand_scale<MODE>(g.amax_a);
+  const float us_a = 1.f / sc_a, us_b = 1.f / operand_scale<MODE>(g.amax_b);
   const int b_slot = P::PLANES * b_plane;
   const int na = a.na, nbs = a.nbs;
   uint8_t* aring = smem_raw;
@@ -686,7 +708,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
           stop = named_barrier_or(1, TC_LOAD_THREADS, !got || *abort_flag);
           if (stop) break;
-          put3m<MODE>(sa, row, h, x);
+          put3m<MODE>(sa, row, h, x, sc_a);
           fence_proxy_async();
           mbar_arrive(smem_u32(&fullA[slot]));
           if (++slot == na) {
@@ -725,13 +747,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
                                  x[j][1].x, x[j][1].y, x[j][1].z, x[j][1].w};
             uint32_t hi[4], lo[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const __nv_bfloat162 h = __floats2bfloat162_rn(xs[2 * i], xs[2 * i + 1]);
-              const float2 hf = __bfloat1622float2(h);
-              const __nv_bfloat162 l = __floats2bfloat162_rn(xs[2 * i] - hf.x, xs[2 * i + 1] - hf.y);
-              hi[i] = *reinterpret_cast<const uint32_t*>(&h);
-              lo[i] = *reinterpret_cast<const uint32_t*>(&l);
-            }
+            for (int i = 0; i < 4; ++i) split_pair<MODE>(xs[2 * i] * sc_a, xs[2 * i + 1] * sc_a, hi[i], lo[i]);
             const int off = tc_elem_off(row, 8 * c, T::ESZ);
             *reinterpret_cast<uint4*>(sa + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(sa + a_plane + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -803,7 +819,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
         uint8_t* sa = aring + slot * P::A_SLOT;
         if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) return false;
-        if (rok) put3m<MODE>(sa, row, h, vc);
+        if (rok) put3m<MODE>(sa, row, h, vc, sc_a);
         fence_proxy_async();
         mbar_arrive(smem_u32(&fullA[slot]));
         if (++slot == na) {
@@ -837,7 +853,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int64_t goff[NCH][KPC];   // offset of each complex of each chunk, -1 = padding
       int soff[NCH];
       bool cok[NCH];
-  #pragma unroll
+#pragma unroll
       for (int j = 0; j < NCH; ++j) {
         const int q = lt + j * TC_LOAD_THREADS;
         const int row = klanes ? q / CPR : q % TC_M;
@@ -845,7 +861,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         cok[j] = row < (1 << g.tm);
         soff[j] = tc_elem_off(row, c * KPC * 2, T::ESZ);
         const int64_t roff = deposit_hi((uint64_t)row, g.a_mpos, 0, g.tm);
-  #pragma unroll
+#pragma unroll
         for (int i = 0; i < KPC; ++i) {
           const int k = c * KPC + i;
           goff[j][i] = (cok[j] && k < tkv) ? roff + deposit_hi((uint64_t)k, g.a_kpos, 0, g.tk) : -1;
@@ -870,13 +886,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
             if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
             {
               const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < NCH; ++j) {
                 if (!cok[j]) continue;
                 if (v16 && goff[j][1] >= 0) {
                   cp_async16(smem_u32(sa + soff[j]), Ak + goff[j][0]);
                 } else {
-  #pragma unroll
+#pragma unroll
                   for (int i = 0; i < KPC; ++i)
                     if (goff[j][i] >= 0) cp_async8(smem_u32(sa + soff[j] + 8 * i), Ak + goff[j][i]);
                 }
@@ -896,9 +912,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         float4 v0[NCH][KPC / 2], v1[NCH][KPC / 2];
         auto issue = [&](float4(&v)[NCH][KPC / 2], const float2* Ak) {
           const bool v16 = kadj && ((reinterpret_cast<uintptr_t>(Ak) & 15) == 0);
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < NCH; ++j)
-  #pragma unroll
+#pragma unroll
             for (int h = 0; h < KPC / 2; ++h) {
               const int64_t o0 = goff[j][2 * h], o1 = goff[j][2 * h + 1];
               if (v16 && o1 >= 0) {
@@ -926,22 +942,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           uint8_t* sa = aring + slot * P::A_SLOT;
           if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) return false;
           {
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < NCH; ++j) {
               if (!cok[j]) continue;
               uint32_t hi[4], lo[4];
-  #pragma unroll
+#pragma unroll
               for (int h = 0; h < KPC / 2; ++h) {
                 const float4 x = vc[j][h];
-                const __nv_bfloat162 h0 = __floats2bfloat162_rn(x.x, x.y);
-                const __nv_bfloat162 h1 = __floats2bfloat162_rn(x.z, x.w);
-                const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-                const __nv_bfloat162 l0 = __floats2bfloat162_rn(x.x - f0.x, x.y - f0.y);
-                const __nv_bfloat162 l1 = __floats2bfloat162_rn(x.z - f1.x, x.w - f1.y);
-                hi[2 * h] = *reinterpret_cast<const uint32_t*>(&h0);
-                hi[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&h1);
-                lo[2 * h] = *reinterpret_cast<const uint32_t*>(&l0);
-                lo[2 * h + 1] = *reinterpret_cast<const uint32_t*>(&l1);
+                split_pair<MODE>(x.x * sc_a, x.y * sc_a, hi[2 * h], lo[2 * h]);
+                split_pair<MODE>(x.z * sc_a, x.w * sc_a, hi[2 * h + 1], lo[2 * h + 1]);
               }
               *reinterpret_cast<uint4*>(sa + soff[j]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
               *reinterpret_cast<uint4*>(sa + a_plane + soff[j]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -1084,11 +1093,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         }
       }
     }
+    // the result's largest component, for its consumer's FP16 scaling (split-K
+    // partials are not the result: the reduction records it)
+    const bool track = g.amax_c != nullptr && a.n_split == 1;
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
       const int acc = a.n_acc == 2 ? (int)(it & 1) : 0;
       const uint32_t aph = (uint32_t)((a.n_acc == 2 ? (it >> 1) : it) & 1);
-      if (!mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, a.err)) break;
+      // warp-uniform decision: the TMEM loads and shuffles below need all 32 lanes
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, a.err))) break;
       tc_fence_after();
       const int64_t otile = tile / a.n_split;
       const int nt = (int)(otile % a.n_nt);
@@ -1101,6 +1114,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
                   deposit_hi((uint64_t)nt, g.c_npos, a.tnb, g.nn);
       const bool row_ok = row < tmv;
       const int64_t crow = offCm[row];
+      float am = 0.f;
       const uint32_t tl = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * setw);
       for (int c0 = 0; c0 < ncp; c0 += 32) {   // 16 complex columns per pass
         float v[32];
@@ -1116,6 +1130,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
             v[2 * j] = t[j] - t[16 + j];
             v[2 * j + 1] = t[32 + j] - t[j] - t[16 + j];
           }
+        }
+        if constexpr (MODE == TC_FP16X3) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = v[j] * us_a * us_b;
+        }
+        if (track) {   // largest component of the valid columns of this row
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (row_ok && c0 / 2 + j < tnv) am = fmaxf(am, fmaxf(fabsf(v[2 * j]), fabsf(v[2 * j + 1])));
         }
         if (a.epi_ok) {
           // stage the warp's 32 x 16 block, then write it in C's memory order:
@@ -1149,6 +1172,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
         }
       }
+      if (track) amax_update(g.amax_c, am);   // all 32 lanes of the warp
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty[acc]));
     }

@@ -39,7 +39,34 @@ struct GemmArgs {
   // all bit positions (tile bits first)
   int8_t a_mpos[KMAXR], a_kpos[KMAXR], b_kpos[KMAXR], b_npos[KMAXR], c_mpos[KMAXR], c_npos[KMAXR];
   int8_t a_bpos[KMAXB], b_bpos[KMAXB], c_bpos[KMAXB];
+  // FP16 split with power-of-two scaling (NULL when unused): max |re|, |im| of
+  // A and B (written by their producers) and C's maximum, which this GEMM
+  // records for its consumer
+  const float* amax_a;
+  const float* amax_b;
+  float* amax_c;
 };
+
+// Exponent s of the power-of-two scale 2^s that maps a tensor's largest
+// component into [2^14, 2^15), inside the FP16 range (|s| <= 126; 0 when the
+// maximum is zero, subnormal or not recorded).
+__device__ __forceinline__ int fp16_scale_exp(const float* amax) {
+  if (!amax) return 0;
+  const int be = (int)((__float_as_uint(*amax) >> 23) & 255u);
+  if (be == 0 || be == 255) return 0;
+  const int s = 14 - (be - 127);
+  return s < -126 ? -126 : (s > 126 ? 126 : s);
+}
+// 2^e for |e| <= 126, exact
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+// Warp-collective: raise *amax_c to the warp's largest m (m >= 0; non-negative
+// floats order like their bit patterns).
+__device__ __forceinline__ void amax_update(float* amax_c, float m) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned*>(amax_c), __float_as_uint(m));
+}
+__device__ __forceinline__ float cabs_max(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
 
 __device__ __forceinline__ uint32_t pext_u32(uint32_t x, uint32_t mask) {
   uint32_t r = 0, k = 0;

@@ -36,12 +36,14 @@ enum KernelId {
   K_TC_BF16X3 = 4,    // tcgen05 kind::f16 bf16 hi/lo split
   K_TC_TF32_3M = 5,   // the same with 3M products (three accumulators per tile)
   K_TC_BF16X3_3M = 6,
+  K_TC_FP16X3 = 7,    // tcgen05 kind::f16 fp16 hi/lo split, operands scaled by powers of two
+  K_TC_FP16X3_3M = 8,
   K_COUNT
 };
 struct KernelCfg {
   int tm, tn, tk;  // log2 tile extents
 };
-static const KernelCfg kCfg[K_COUNT] = {{6, 6, 3}, {7, 4, 4}, {8, 2, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}};
+static const KernelCfg kCfg[K_COUNT] = {{6, 6, 3}, {7, 4, 4}, {8, 2, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}, {7, 7, 4}};
 
 static int pick_simt(const StepDesc& d) {
   if (d.nn >= 5 && d.nm >= 5) return K_SIMT_64x64;
@@ -144,8 +146,8 @@ struct StepLaunch {
   int smem = 0;
 };
 
-static bool is_tc(int kid) { return kid >= K_TC_TF32 && kid <= K_TC_BF16X3_3M; }
-static bool tc_is_3m(int kid) { return kid == K_TC_TF32_3M || kid == K_TC_BF16X3_3M; }
+static bool is_tc(int kid) { return kid >= K_TC_TF32 && kid <= K_TC_FP16X3_3M; }
+static bool tc_is_3m(int kid) { return kid == K_TC_TF32_3M || kid == K_TC_BF16X3_3M || kid == K_TC_FP16X3_3M; }
 struct TcGeom {   // the plane geometry of TcPl<MODE, CM> for a kernel id
   int planes, rows_per_col, a_slot, min_tn_c, esz;
 };
@@ -160,9 +162,15 @@ static TcGeom tc_geom(int kid) {
     case K_TC_TF32_3M:
       return {TcPl<TC_TF32, 3>::PLANES, TcPl<TC_TF32, 3>::ROWS_PER_COL, TcPl<TC_TF32, 3>::A_SLOT,
               TcPl<TC_TF32, 3>::MIN_TN_C, 4};
-    default:
+    case K_TC_BF16X3_3M:
       return {TcPl<TC_BF16X3, 3>::PLANES, TcPl<TC_BF16X3, 3>::ROWS_PER_COL, TcPl<TC_BF16X3, 3>::A_SLOT,
               TcPl<TC_BF16X3, 3>::MIN_TN_C, 2};
+    case K_TC_FP16X3:
+      return {TcPl<TC_FP16X3, 4>::PLANES, TcPl<TC_FP16X3, 4>::ROWS_PER_COL, TcPl<TC_FP16X3, 4>::A_SLOT,
+              TcPl<TC_FP16X3, 4>::MIN_TN_C, 2};
+    default:
+      return {TcPl<TC_FP16X3, 3>::PLANES, TcPl<TC_FP16X3, 3>::ROWS_PER_COL, TcPl<TC_FP16X3, 3>::A_SLOT,
+              TcPl<TC_FP16X3, 3>::MIN_TN_C, 2};
   }
 }
 
@@ -323,13 +331,19 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
     case K_TC_TF32_3M:
       launch_tc<TC_TF32, 3>(t, L, pblocks, grid, s);
       break;
-    default:
+    case K_TC_BF16X3_3M:
       launch_tc<TC_BF16X3, 3>(t, L, pblocks, grid, s);
+      break;
+    case K_TC_FP16X3:
+      launch_tc<TC_FP16X3, 4>(t, L, pblocks, grid, s);
+      break;
+    default:
+      launch_tc<TC_FP16X3, 3>(t, L, pblocks, grid, s);
       break;
   }
   if (t.n_split > 1) {
     const int rb = (int)std::min<int64_t>((L.c_total + 255) / 256, (int64_t)sm_count() * 8);
-    k_split_reduce<<<rb, 256, 0, s>>>(t.c_part, t.n_split, t.c_part_stride, t.g.C, L.c_total);
+    k_split_reduce<<<rb, 256, 0, s>>>(t.c_part, t.n_split, t.c_part_stride, t.g.C, L.c_total, t.g.amax_c);
   }
 }
 
@@ -345,6 +359,7 @@ struct DeviceState {
   int32_t* err = nullptr;
   uint8_t* ws = nullptr;
   double2* root_part = nullptr;   // [groups][2^k] partial slice sums
+  float* amax = nullptr;          // FP16X3: largest component of every node (leaves, then steps)
   int root_groups = 1;
   std::vector<StepLaunch> launches;
   cudaEvent_t done = nullptr;
@@ -358,17 +373,30 @@ struct DeviceState {
 
 static int tc_kernel(int precision, int cmult) {
   if (precision == TN_PREC_TF32) return cmult == 3 ? K_TC_TF32_3M : K_TC_TF32;
+  if (precision == TN_PREC_FP16X3) return cmult == 3 ? K_TC_FP16X3_3M : K_TC_FP16X3;
   return cmult == 3 ? K_TC_BF16X3_3M : K_TC_BF16X3;
 }
 // Tensor-core kernels (4M or 3M products) for every step with enough work in
-// the TF32 / BF16X3 modes; tiny steps (and the FP32 mode) on the CUDA cores,
-// which always form 4M products in FP32.
+// the TF32 / BF16X3 / FP16X3 modes; tiny steps (and the FP32 mode) on the CUDA
+// cores, which always form 4M products in FP32.
 static int pick_kernel(int precision, int cmult, const StepDesc& d) {
   if (precision == TN_PREC_FP32) return pick_simt(d);
-  if (precision == TN_PREC_FP16X3) fail(TN_ERR_UNSUPPORTED, "FP16X3 is not built");
   const int work = d.nm + d.nk + d.nn + d.nb;
   if (work < 20 || d.nm < 4) return pick_simt(d);
   return tc_kernel(precision, cmult);
+}
+
+// Launch arguments of plan step d for kernel kid; FP16X3 plans also get the
+// maxima of the step's operands (to scale them) and of its result (to record).
+static GemmArgs step_args(const Plan& p, const DeviceState& ds, const StepDesc& d, int kid, int tn_log = -1) {
+  GemmArgs g = make_args(d, kid, ds.arena + d.a_off, ds.arena + d.b_off, ds.arena + d.c_off, 1 << d.nb, 0, 0, 0,
+                         tn_log);
+  if (ds.amax) {
+    g.amax_a = ds.amax + d.a_node;
+    g.amax_b = ds.amax + d.b_node;
+    g.amax_c = ds.amax + d.c_node;
+  }
+  return g;
 }
 
 static void ensure_device(Plan& p) {
@@ -397,6 +425,14 @@ static void ensure_device(Plan& p) {
   CK(cudaMalloc(&ds->err, sizeof(int32_t)));
   CK(cudaMemset(ds->err, 0, sizeof(int32_t)));
   CK(cudaEventCreateWithFlags(&ds->done, cudaEventDisableTiming));
+  if (p.opts.precision == TN_PREC_FP16X3) {
+    // leaves' maxima are constants of the plan; the steps' are recorded per chunk
+    const size_t nn = p.leaves.size() + p.steps.size();
+    CK(cudaMalloc(&ds->amax, sizeof(float) * std::max<size_t>(nn, 1)));
+    CK(cudaMemset(ds->amax, 0, sizeof(float) * std::max<size_t>(nn, 1)));
+    if (!p.leaf_amax.empty())
+      CK(cudaMemcpy(ds->amax, p.leaf_amax.data(), sizeof(float) * p.leaf_amax.size(), cudaMemcpyHostToDevice));
+  }
   // bounds of every operand inside the arena, checked once on the host
   const int64_t ae = p.arena_elems;
   auto in_arena = [&](int64_t off, int64_t size, int insts) {
@@ -423,9 +459,8 @@ static void ensure_device(Plan& p) {
                     ((int64_t)1 << (d.nm + d.nn + d.nb)) == d.c_elems;
     if (!ok) fail(TN_ERR_PLAN, "internal: step operand outside its extent");
     const int kid = pick_kernel(p.opts.precision, p.opts.complex_mult, d);
-    ds->launches.push_back(make_launch(
-        make_args(d, kid, ds->arena + d.a_off, ds->arena + d.b_off, ds->arena + d.c_off, 1 << d.nb), kid,
-        64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true));
+    ds->launches.push_back(
+        make_launch(step_args(p, *ds, d, kid), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true));
   }
   int64_t ws = 16;
   for (const StepLaunch& L : ds->launches) ws = std::max(ws, L.ws_bytes);
@@ -454,6 +489,7 @@ void destroy_device_state(Plan* p) {
   cudaFree(ds->err);
   cudaFree(ds->ws);
   cudaFree(ds->root_part);
+  cudaFree(ds->amax);
   if (ds->graph) cudaGraphExecDestroy(ds->graph);
   if (ds->done) cudaEventDestroy(ds->done);
   cudaSetDevice(cur);
@@ -464,6 +500,8 @@ void destroy_device_state(Plan* p) {
 static void run_chunk(Plan& p, cudaStream_t s) {
   DeviceState& ds = *p.dev;
   const int nl = (int)p.leaves.size();
+  if (ds.amax && !p.steps.empty())   // the steps' maxima start from zero in every chunk
+    CK(cudaMemsetAsync(ds.amax + nl, 0, sizeof(float) * p.steps.size(), s));
   k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
                                                                  ds.params, ds.counter);
   for (size_t i = 0; i < p.steps.size(); ++i) launch_step(ds.launches[i], ds.ws, ds.err, s);
@@ -659,13 +697,12 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   for (size_t i = 0; i < p.steps.size(); ++i) {
     const StepDesc& d = p.steps[i];
     auto build = [&](int kid, int tn_log, int epi) {
-      return make_launch(make_args(d, kid, ds.arena + d.a_off, ds.arena + d.b_off, ds.arena + d.c_off, 1 << d.nb,
-                                   0, 0, 0, tn_log),
-                         kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true, epi);
+      return make_launch(step_args(p, ds, d, kid, tn_log), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
+                         d.c_elems, true, epi);
     };
     double best = time_launch(ds.launches[i]);
     std::vector<std::array<int, 3>> cands;   // kernel, tile width (log2 complex columns), write-back
-    const bool tc_mode = p.opts.precision == TN_PREC_TF32 || p.opts.precision == TN_PREC_BF16X3;
+    const bool tc_mode = p.opts.precision != TN_PREC_FP32;
     const int tc_kid = tc_kernel(p.opts.precision, p.opts.complex_mult);
     if (tc_mode && d.nm >= 4)
       for (int tn_log : {7, 6, 5})
@@ -731,9 +768,19 @@ extern "C" void tn_plan_destroy(tn_plan_t* h) {
 
 // Per-device scratch of the calls that have no plan: the XEB sum, the error
 // word and the B' workspace of tn_contract_pair.
+// FP16X3 calls without a plan: the maxima of A and B by one reduction pass each
+static void operand_maxima(const float2* a, int64_t na, const float2* b, int64_t nb, float* amax, cudaStream_t s) {
+  CK(cudaMemsetAsync(amax, 0, 2 * sizeof(float), s));
+  const int ga = (int)std::min<int64_t>((na + 255) / 256, (int64_t)sm_count() * 8);
+  const int gb = (int)std::min<int64_t>((nb + 255) / 256, (int64_t)sm_count() * 8);
+  k_amax<<<std::max(ga, 1), 256, 0, s>>>(a, na, amax);
+  k_amax<<<std::max(gb, 1), 256, 0, s>>>(b, nb, amax + 1);
+}
+
 struct Scratch {
   double* xeb = nullptr;
   int32_t* err = nullptr;
+  float* amax = nullptr;   // FP16X3 operand maxima of the last call (A, B)
   uint8_t* ws = nullptr;
   int64_t ws_bytes = 0;
 };
@@ -748,6 +795,7 @@ static Scratch& scratch_for_device() {
     CK(cudaMalloc(&s.xeb, sizeof(double)));
     CK(cudaMalloc(&s.err, sizeof(int32_t)));
     CK(cudaMemset(s.err, 0, sizeof(int32_t)));
+    CK(cudaMalloc(&s.amax, 2 * sizeof(float)));
   }
   return s;
 }
@@ -877,8 +925,14 @@ extern "C" tn_status tn_contract_pair(const float* a, const int32_t* aw, int32_t
   const int kid = pick_kernel(precision, cmult, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                          reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
-  StepLaunch L = make_launch(g, kid, ar, batch, batch * d.c_elems, true);
   Scratch& sc = scratch_for_device();
+  if (precision == TN_PREC_FP16X3 && is_tc(kid)) {   // operand maxima for the FP16 scaling (one extra read)
+    operand_maxima(reinterpret_cast<const float2*>(a), batch << ar, reinterpret_cast<const float2*>(b),
+                   batch << br, sc.amax, (cudaStream_t)stream);
+    g.amax_a = sc.amax;
+    g.amax_b = sc.amax + 1;
+  }
+  StepLaunch L = make_launch(g, kid, ar, batch, batch * d.c_elems, true);
   if (L.ws_bytes > sc.ws_bytes) {
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     if (sc.ws) CK(cudaFree(sc.ws));
@@ -992,15 +1046,23 @@ extern "C" tn_status tn_contract_pair_noalloc(const float* a, const int32_t* aw,
   const int kid = pick_kernel(precision, cmult, d);
   GemmArgs g = make_args(d, kid, reinterpret_cast<const float2*>(a), reinterpret_cast<const float2*>(b),
                          reinterpret_cast<float2*>(c), (int32_t)batch, d.a_elems, d.b_elems, d.c_elems);
-  StepLaunch L = make_launch(g, kid, ar, batch);
   const int64_t cap = (int64_t)(kNoAllocScratchBytes - kNoAllocErrBytes);
+  uint8_t* base = static_cast<uint8_t*>(noalloc_scratch_address());
+  int32_t* err = reinterpret_cast<int32_t*>(base);
+  float* amax = reinterpret_cast<float*>(base + 16);   // FP16X3 operand maxima, inside the header
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == TN_PREC_FP16X3 && is_tc(kid)) {
+    g.amax_a = amax;
+    g.amax_b = amax + 1;
+  }
+  StepLaunch L = make_launch(g, kid, ar, batch);
   if (L.ws_bytes > cap)
     fail(TN_ERR_ARG, "tn_contract_pair_noalloc: this contraction needs " + std::to_string(L.ws_bytes) +
                          " bytes of scratch; the static array holds " + std::to_string(cap));
-  uint8_t* base = static_cast<uint8_t*>(noalloc_scratch_address());
-  int32_t* err = reinterpret_cast<int32_t*>(base);
-  cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemsetAsync(err, 0, sizeof(int32_t), s));   // the array keeps the last call's contents
+  if (g.amax_a)
+    operand_maxima(reinterpret_cast<const float2*>(a), batch << ar, reinterpret_cast<const float2*>(b),
+                   batch << br, amax, s);
   launch_step(L, base + kNoAllocErrBytes, err, s);
   CK(cudaGetLastError());
   API_END

@@ -68,6 +68,7 @@ struct StepDesc {
   int32_t nm_wires, nn_wires;         // m / n bits that are wires (the rest are batch bits)
   int32_t rank_a, rank_b, rank_c;     // per-slice ranks
   int32_t kernel;                     // kernel variant chosen by the executor
+  int32_t a_node, b_node, c_node;     // node ids (leaves 0..L-1, step i's result L+i)
   int8_t a_mpos[MAXR], a_kpos[MAXR], b_kpos[MAXR], b_npos[MAXR], c_mpos[MAXR], c_npos[MAXR];
   int8_t a_bpos[MAXB], b_bpos[MAXB], c_bpos[MAXB];
 };
@@ -110,6 +111,7 @@ struct Plan {
   int n_leaves = 0;
   std::vector<std::complex<float>> leaf_data;
   std::vector<LeafDesc> leaves;
+  std::vector<float> leaf_amax;        // largest |re|, |im| of each leaf's data (FP16 scaling)
   std::vector<StepDesc> steps;
   RootDesc root{};
   int64_t arena_elems = 0;

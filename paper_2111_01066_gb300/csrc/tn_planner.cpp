@@ -863,6 +863,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       peak = std::max(peak, end);
     }
     steps.clear();
+    std::vector<int> step_of(nm, -1);
     for (int mi : order) {
       const int x = T.merges[mi].first, y = T.merges[mi].second;
       const int64_t ex = elems_of(info[x]), ey = elems_of(info[y]);
@@ -872,6 +873,12 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       NodeInfo C;
       StepDesc d;
       std::memset(&d, 0, sizeof(d));
+      // node ids: leaves 0..L-1, the result of step j is L + j
+      auto node_id = [&](int v) { return v < L ? v : L + step_of[v - L]; };
+      d.a_node = node_id(x_is_a ? x : y);
+      d.b_node = node_id(x_is_a ? y : x);
+      d.c_node = L + (int)steps.size();
+      step_of[mi] = (int)steps.size();
       std::vector<int> mw, kw, nw;
       for (int w : A.wires)
         (std::find(B.wires.begin(), B.wires.end(), w) != B.wires.end() ? kw : mw).push_back(w);
@@ -1004,7 +1011,13 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       ld.fixed_kind[f] = (int8_t)kind[f];
       ld.fixed_index[f] = (int8_t)idx[f];
     }
-    for (const cd& v : pt.data) P->leaf_data.push_back(std::complex<float>((float)v.real(), (float)v.imag()));
+    float am = 0.f;
+    for (const cd& v : pt.data) {
+      const std::complex<float> f((float)v.real(), (float)v.imag());
+      P->leaf_data.push_back(f);
+      am = std::max(am, std::max(std::fabs(f.real()), std::fabs(f.imag())));
+    }
+    P->leaf_amax.push_back(am);
   }
   // root
   const int root = (nm > 0) ? (L + order.back()) : 0;

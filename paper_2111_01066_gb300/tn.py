@@ -258,7 +258,7 @@ class Plan:
                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
 
     KERNELS = {0: "simt64x64", 1: "simt128x16", 2: "simt256x4", 3: "tc_tf32", 4: "tc_bf16x3",
-               5: "tc_tf32_3m", 6: "tc_bf16x3_3m"}
+               5: "tc_tf32_3m", 6: "tc_bf16x3_3m", 7: "tc_fp16x3", 8: "tc_fp16x3_3m"}
 
     def step_times(self, reps: int = 3, stream=None) -> List[Tuple[float, str]]:
         """(mean device milliseconds per launch, kernel name) of every step."""
