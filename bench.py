@@ -628,7 +628,7 @@ def main() -> int:
             "clocks": clk,
             "e2e": {"value": total_units / e2e_s, "unit": "slices/s", "h2d_bytes_per_step": 8 + 40 * n_chunks,
                     "d2h_bytes_per_step": (16 << k_open) + 8},
-            "gpu_launches": args.steps * (n_chunks * info["n_kernel_launches_per_chunk"] + 1),
+            "gpu_launches": args.steps * (n_chunks * plan.chunk_launches() + 1),   # + the XEB kernel
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

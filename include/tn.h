@@ -161,7 +161,8 @@ typedef struct tn_plan_stats {
     int64_t  arena_bytes;            /* device arena of one chunk */
     int32_t  k_histogram[40];        /* steps per log2(contracted size k), as figure S4 */
     int32_t  complex_mult;
-    int32_t  n_kernel_launches_per_chunk;
+    int32_t  n_kernel_launches_per_chunk;  /* before kernels are chosen: slice-dependent steps + 4
+                                              (tn_plan_chunk_launches gives the exact count) */
 } tn_plan_stats;
 
 tn_status tn_plan_info(const tn_plan_t* plan, tn_plan_stats* out);
@@ -181,7 +182,9 @@ tn_status tn_plan_step_shape(const tn_plan_t* plan, int32_t step, int32_t* log2_
  * introspection call for reports and tests).  Positions are bit positions of
  * each operand's element index (element = complex64, position 0 the fastest).
  * Writes to out[0..] in this order: nm, nk, nn, nb, then a_m[nm], a_k[nk],
- * b_k[nk], b_n[nn], c_m[nm], c_n[nn], a_b[nb], b_b[nb], c_b[nb]: where A is
+ * b_k[nk], b_n[nn], c_m[nm], c_n[nn], a_b[nb], b_b[nb], c_b[nb], then the
+ * step's dependence flags (bit 0: its result depends on the slice id, bit 1:
+ * on the closed output bits; 0 = the same tensor in every chunk): where A is
  * the streamed operand, B the small one, C the result, and a_m[j] / c_m[j] the
  * positions of row bit j in A and in C (and so on).  `count` receives the
  * number of entries; at most `cap` are written (TN_ERR_ARG if cap is too small). */
@@ -223,6 +226,14 @@ tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int3
  * fastest for later calls.  Synchronises `stream`; the arena contents are
  * overwritten (the next call recomputes them). */
 tn_status tn_plan_autotune(tn_plan_t* plan, int32_t reps, void* stream);
+
+/* Kernels one chunk launches with the kernels chosen so far (after the first
+ * tn_contract_slices call; TN_ERR_ARG before): leaf select, every
+ * slice-dependent step's kernels (tensor-core steps: B' image + GEMM [+ split-K
+ * reduction]; CUDA-core steps: one), the two slice-sum kernels and the chunk
+ * advance.  Steps that depend on no slice run once per plan or per batch and
+ * are not counted.  Host only. */
+tn_status tn_plan_chunk_launches(const tn_plan_t* plan, int32_t* launches);
 
 /* Wait for the plan's work on `stream` and return its sticky device error, if any. */
 tn_status tn_plan_sync(tn_plan_t* plan, void* stream);

@@ -309,6 +309,7 @@ static void launch_tc(const TcArgs& t, const StepLaunch& L, int pblocks, int gri
 }
 
 static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s) {
+  if (L.g.amax_c) CK(cudaMemsetAsync(L.g.amax_c, 0, sizeof(float), s));   // the result's maximum, recorded anew
   if (!is_tc(L.kid)) {
     launch_simt(L.g, L.kid, s);
     return;
@@ -369,6 +370,12 @@ struct DeviceState {
   cudaGraphExec_t graph = nullptr;
   bool graph_failed = false;
   bool eager_done = false;
+  // prologues: steps whose result depends on no slice run once per plan
+  // (dependence flags 0) or once per batch bitstring (flags 2); their results
+  // that later steps read sit in the arena's persistent pool
+  bool pro0_done = false;
+  bool pro2_valid = false;
+  uint64_t pro2_bits = 0;
 };
 
 static int tc_kernel(int precision, int cmult) {
@@ -500,17 +507,30 @@ void destroy_device_state(Plan* p) {
 static void run_chunk(Plan& p, cudaStream_t s) {
   DeviceState& ds = *p.dev;
   const int nl = (int)p.leaves.size();
-  if (ds.amax && !p.steps.empty())   // the steps' maxima start from zero in every chunk
-    CK(cudaMemsetAsync(ds.amax + nl, 0, sizeof(float) * p.steps.size(), s));
   k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
                                                                  ds.params, ds.counter);
-  for (size_t i = 0; i < p.steps.size(); ++i) launch_step(ds.launches[i], ds.ws, ds.err, s);
+  for (size_t i = 0; i < p.steps.size(); ++i)
+    if (p.steps[i].dep_flags & 1) launch_step(ds.launches[i], ds.ws, ds.err, s);   // slice-dependent steps
   const int64_t nout = (int64_t)1 << p.root.rank;
   const int blocks = (int)std::min<int64_t>((nout + 255) / 256, 4096);
   k_root_partial<<<dim3(blocks, ds.root_groups), 256, 0, s>>>(ds.arena, p.root, p.log2_batch, ds.root_groups,
                                                                ds.root_part, ds.params, ds.counter);
   k_root_finish<<<blocks, 256, 0, s>>>(ds.root_part, ds.root_groups, p.root.rank, ds.params, ds.counter);
   k_advance<<<1, 1, 0, s>>>(ds.counter);
+}
+
+// The steps of one dependence class (0: neither slice nor bitstring, 2:
+// bitstring only), after a leaf select with the current chunk's parameters.
+static void run_prologue(Plan& p, cudaStream_t s, int cls) {
+  DeviceState& ds = *p.dev;
+  bool any = false;
+  for (const StepDesc& d : p.steps) any = any || d.dep_flags == cls;
+  if (!any) return;
+  const int nl = (int)p.leaves.size();
+  k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
+                                                                 ds.params, ds.counter);
+  for (size_t i = 0; i < p.steps.size(); ++i)
+    if (p.steps[i].dep_flags == cls) launch_step(ds.launches[i], ds.ws, ds.err, s);
 }
 
 // Capture run_chunk once into a graph (on a private stream, thread-local
@@ -607,6 +627,18 @@ extern "C" tn_status tn_contract_slices(tn_plan_t* h, uint64_t first, uint64_t c
   CK(cudaMemcpyAsync(ds.params, prm.data(), prm.size() * sizeof(ChunkParam), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(ds.counter, 0, sizeof(unsigned), s));
   for (size_t c = 0; c < prm.size(); ++c) {
+    if (c == 0 || prm[c].out_index != prm[c - 1].out_index) {   // first chunk of a batch
+      if (!ds.pro0_done) {
+        run_prologue(p, s, 0);
+        ds.pro0_done = true;
+      }
+      if (!ds.pro2_valid || ds.pro2_bits != prm[c].bitstring) {
+        run_prologue(p, s, 2);
+        ds.pro2_valid = true;
+        ds.pro2_bits = prm[c].bitstring;
+      }
+      CK(cudaGetLastError());
+    }
     if (!ds.eager_done) {
       run_chunk(p, s);           // the first chunk runs eagerly (sets kernel attributes)
       CK(cudaGetLastError());
@@ -652,6 +684,8 @@ extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_o
   CK(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  ds.pro0_done = false;   // the arena was overwritten: prologues run again
+  ds.pro2_valid = false;
   API_END
 }
 
@@ -740,6 +774,23 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   }
   ds.graph_failed = false;
   ds.eager_done = false;
+  ds.pro0_done = false;   // the arena was overwritten: prologues run again
+  ds.pro2_valid = false;
+  API_END
+}
+
+extern "C" tn_status tn_plan_chunk_launches(const tn_plan_t* h, int32_t* launches) {
+  API_BEGIN
+  if (!h || !launches) fail(TN_ERR_ARG, "tn_plan_chunk_launches: NULL argument");
+  const Plan& p = h->plan;
+  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_chunk_launches: call after the first tn_contract_slices");
+  int n = 4;
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    if ((p.steps[i].dep_flags & 1) == 0) continue;
+    const StepLaunch& L = p.dev->launches[i];
+    n += is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
+  }
+  *launches = n;
   API_END
 }
 

@@ -69,6 +69,7 @@ struct StepDesc {
   int32_t rank_a, rank_b, rank_c;     // per-slice ranks
   int32_t kernel;                     // kernel variant chosen by the executor
   int32_t a_node, b_node, c_node;     // node ids (leaves 0..L-1, step i's result L+i)
+  int32_t dep_flags;                  // result depends on the slice id (bit 0), on closed output bits (bit 1)
   int8_t a_mpos[MAXR], a_kpos[MAXR], b_kpos[MAXR], b_npos[MAXR], c_mpos[MAXR], c_npos[MAXR];
   int8_t a_bpos[MAXB], b_bpos[MAXB], c_bpos[MAXB];
 };

@@ -720,6 +720,27 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   const int64_t cap_bytes = o.max_arena_bytes > 0 ? o.max_arena_bytes : (int64_t)96 << 30;
   std::vector<std::vector<int>> node_order;   // storage order of every node's wires
   std::vector<std::vector<int>> border_of;    // and of its batch bits
+  // Dependence of every tree node on the slice id (bit 0) and on the closed
+  // output bits (bit 1).  Results of steps with flags 0 (the same in every
+  // chunk of every call) or 2 (the same in every chunk of one batch) are
+  // computed once, by a prologue; those that a later-class step (or the root
+  // sum) reads stay in a persistent pool at the start of the arena.
+  std::vector<int> nflag(L + nm, 0), parent(L + nm, -1);
+  for (int i = 0; i < L; ++i)
+    for (int w : S.leaves[i].wires) {
+      if (!S.fixed[w] && SL.test(pw_of[w])) nflag[i] |= 1;
+      if (S.fixed[w]) nflag[i] |= forced_bit[w] >= 0 ? 1 : 2;
+    }
+  for (int mi : order) {
+    nflag[L + mi] = nflag[T.merges[mi].first] | nflag[T.merges[mi].second];
+    parent[T.merges[mi].first] = L + mi;
+    parent[T.merges[mi].second] = L + mi;
+  }
+  std::vector<char> pooled(L + nm, 0);
+  for (int mi : order) {
+    const int v = L + mi;
+    if ((nflag[v] & 1) == 0 && (parent[v] < 0 || nflag[parent[v]] != nflag[v])) pooled[v] = 1;
+  }
   auto layout = [&](int b, std::vector<NodeInfo>& info, std::vector<StepDesc>& steps,
                     int64_t& arena) -> bool {
     info.assign(L + nm, NodeInfo{});
@@ -857,7 +878,15 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
         freel.pop_back();
       }
     };
-    int64_t peak = 0;
+    // the persistent pool first: one slot per pooled result (no batch bits: it
+    // depends on no slice)
+    std::vector<int64_t> pool_off(L + nm, -1);
+    for (int mi : order)
+      if (pooled[L + mi]) {
+        pool_off[L + mi] = end;
+        end += (((int64_t)1 << node_order[L + mi].size()) + AL - 1) / AL * AL;
+      }
+    int64_t peak = end;
     for (int i = 0; i < L; ++i) {
       info[i].off = alloc(elems_of(info[i]));
       peak = std::max(peak, end);
@@ -940,13 +969,15 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       d.b_elems = elems_of(B);
       d.a_off = A.off;
       d.b_off = B.off;
-      C.off = alloc(elems_of(C));
+      if (pooled[L + mi] && C.bmask != 0) fail(TN_ERR_PLAN, "internal: pooled result with batch bits");
+      C.off = pooled[L + mi] ? pool_off[L + mi] : alloc(elems_of(C));
       d.c_off = C.off;
       d.c_elems = elems_of(C);
       peak = std::max(peak, end);
       d.kernel = -1;
-      release(A.off, elems_of(A));
-      release(B.off, elems_of(B));
+      const int a_id = x_is_a ? x : y, b_id = x_is_a ? y : x;
+      if (!pooled[a_id]) release(A.off, elems_of(A));
+      if (!pooled[b_id]) release(B.off, elems_of(B));
       info[L + mi] = C;
       steps.push_back(d);
     }
@@ -969,6 +1000,10 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   P->log2_batch = b;
   P->steps = steps;
   P->arena_elems = arena;
+  // dependence of every step's result on the slice id (bit 0) and on the
+  // closed output bits (bit 1): a step with neither computes the same tensor
+  // in every chunk of every call
+  for (size_t j = 0; j < P->steps.size(); ++j) P->steps[j].dep_flags = nflag[L + order[j]];
 
   // leaves: source data ordered [kept planning wires, sliced wires by slice bit, closed outputs]
   P->leaves.resize(L);
@@ -1119,7 +1154,12 @@ extern "C" tn_status tn_plan_info(const tn_plan_t* h, tn_plan_stats* s) {
   s->arena_bytes = p.arena_elems * 8;
   for (int i = 0; i < 40; ++i) s->k_histogram[i] = p.stats.khist[i];
   s->complex_mult = p.opts.complex_mult;
-  s->n_kernel_launches_per_chunk = (int)p.steps.size() + 4;
+  // steps that depend on the slice id run in every chunk (the others run once
+  // per plan or per batch); one kernel each at least, plus leaf select, the
+  // two slice-sum kernels and the chunk advance
+  int per_chunk = 4;
+  for (const StepDesc& d : p.steps) per_chunk += (d.dep_flags & 1) ? 1 : 0;
+  s->n_kernel_launches_per_chunk = per_chunk;
   return TN_OK;
 }
 
@@ -1165,6 +1205,7 @@ extern "C" tn_status tn_plan_step_layout(const tn_plan_t* h, int32_t step, int32
   put(d.a_bpos, d.nb);
   put(d.b_bpos, d.nb);
   put(d.c_bpos, d.nb);
+  v.push_back(d.dep_flags);
   *count = (int32_t)v.size();
   if ((int32_t)v.size() > cap) {
     set_error("tn_plan_step_layout: cap smaller than the layout");

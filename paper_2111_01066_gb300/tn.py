@@ -78,6 +78,7 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_step_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    "tn_plan_chunk_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_step_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "tn_contract_slices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
@@ -236,7 +237,8 @@ class Plan:
 
     def step_layout(self, i: int) -> dict:
         """Bit positions of step i's operands (A streamed, B small, C result):
-        keys a_m, a_k, b_k, b_n, c_m, c_n, a_b, b_b, c_b."""
+        keys a_m, a_k, b_k, b_n, c_m, c_n, a_b, b_b, c_b; and dep_flags (bit 0:
+        depends on the slice id, bit 1: on the closed output bits)."""
         buf = (ctypes.c_int32 * 256)()
         cnt = ctypes.c_int32()
         _check(load().tn_plan_step_layout(self.handle, i, buf, 256, ctypes.byref(cnt)))
@@ -247,7 +249,14 @@ class Plan:
                        ("a_b", nb), ("b_b", nb), ("c_b", nb)):
             out[key] = v[pos:pos + n]
             pos += n
+        out["dep_flags"] = v[pos]
         return out
+
+    def chunk_launches(self) -> int:
+        """Kernels one chunk launches with the kernels chosen so far (after the first contract call)."""
+        n = ctypes.c_int32()
+        _check(load().tn_plan_chunk_launches(self.handle, ctypes.byref(n)))
+        return n.value
 
     def contract_slices(self, slice_first: int, slice_count: int, bitstrings: Sequence[int],
                         out, stream=None) -> None:

@@ -79,6 +79,35 @@ def test_c1_sliced_batches_and_ragged_ranges(env):
         assert _relerr(out.cpu().numpy().view(np.complex128), want) < FP32_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
+def test_prologue_reuse_across_calls_and_batches(env, prec):
+    """Steps that depend on no slice run once per plan (no closed output bit
+    either) or once per batch bitstring, and their results are reused: calls
+    that alternate bitstrings, repeat them, or accumulate still give the state
+    vector's amplitudes."""
+    tn, torch = env
+    circ, _, _ = rqcgen.config_circuit("c1")
+    om = 0b111100001111
+    psi = sv.simulate(circ)
+    bits = [0b000011110000, 0b000001010000]
+    want = [sv.batch_amplitudes(psi, circ.n_qubits, b, om) for b in bits]
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=30, min_log2_slices=4,
+                   log2_batch_slices=2, precision=prec, trials=8)
+    flags = [plan.step_layout(i)["dep_flags"] for i in range(plan.info()["n_steps"])]
+    assert 0 in flags and 1 in flags or 3 in flags   # the plan has prologue and per-chunk steps
+    n = 1 << plan.info()["log2_slices"]
+    for seq in ([0], [1], [0], [1, 0, 1], [0, 0]):
+        got = _run_plan(tn, torch, plan, 0, n, [bits[i] for i in seq], 8).reshape(len(seq), -1)
+        for row, i in zip(got, seq):
+            assert _relerr(row, want[i]) < PLAN_TOL[prec]
+    # accumulation into the same buffer over two calls
+    out = torch.zeros(2 << 8, dtype=torch.float64, device="cuda")
+    plan.contract_slices(0, n, [bits[1]], out)
+    plan.contract_slices(0, n, [bits[1]], out)
+    plan.sync()
+    assert _relerr(out.cpu().numpy().view(np.complex128), 2 * want[1]) < PLAN_TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_c1_forced_slices_sum_to_statevector(env, prec):
     """Caller-chosen sliced wires (kept as diagonal indices through the host
