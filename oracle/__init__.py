@@ -19,6 +19,8 @@ Contents, each written from the paper's statement of the problem:
   in the oracle's own greedy order.
 * `xeb` -- linear cross-entropy benchmarking and the Porter-Thomas density of
   Eq. (1) of the main text.
+* `sampling` -- frugal rejection sampling of one bitstring from a batch of
+  correlated amplitudes (main text, section III).
 
 Pins (tests/test_oracle_*.py): closed-form gate actions, a Kronecker-built dense
 circuit matrix, a Feynman path sum over all wire values on tiny circuits,

@@ -71,3 +71,26 @@ def test_planted_dropped_slice_is_caught():
     sliced = [(0, 3), (5, 4), (9, 2)]
     partial = net.contract(sliced, range(1, 8))        # slice 0 left out
     assert np.linalg.norm(partial - full) > 1e-6 * np.linalg.norm(full)
+
+
+@pytest.mark.parametrize("mistake", ["drop_N", "greater_equal_u_side", "ignore_imaginary"])
+def test_planted_frugal_sampling_mistakes_are_caught(monkeypatch, mistake):
+    """Accepting with p instead of N p, comparing the wrong way round, or
+    dropping Im a from p each breaks the frugal-sampling law pin."""
+    from oracle import sampling
+    from tests.test_oracle_pins import test_frugal_sampling_law_and_sampled_xeb as pin
+    orig = sampling.accept_mask
+
+    def mutated(amplitudes, n_qubits, m_bound, candidates, uniforms):
+        a = np.asarray(amplitudes, dtype=np.complex128).reshape(-1)
+        c, u = np.asarray(candidates), np.asarray(uniforms, dtype=np.float64)
+        if mistake == "drop_N":
+            return orig(a, 0, m_bound / 2 ** 6, c, u)   # N = 64 instead of 2^n
+        if mistake == "greater_equal_u_side":
+            return u * m_bound > np.ldexp(np.abs(a[c]) ** 2, n_qubits)
+        return u * m_bound < np.ldexp(a.real[c] ** 2, n_qubits)
+
+    pin()
+    monkeypatch.setattr(sampling, "accept_mask", mutated)
+    with pytest.raises(AssertionError):
+        pin()

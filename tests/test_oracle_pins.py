@@ -354,3 +354,57 @@ def test_porter_thomas_and_ideal_xeb():
     rng = np.random.default_rng(1)
     f0 = xeb.linear_xeb(psi[rng.integers(0, 1 << n, size=m)], n)
     assert abs(f0) < 4 * math.sqrt(1.0 / m)
+
+
+# ----------------------------------------------------------------- frugal sampling (main text, section III)
+def test_frugal_sampling_special_cases():
+    from oracle import sampling
+    n = 6
+    a = np.zeros(64, dtype=np.complex128)
+    a[37] = 1.0                                   # all weight on one member: N p = 64 > M
+    cand = np.array([3, 37, 37, 5])
+    u = np.array([0.0, 0.999999, 0.1, 0.0])
+    assert sampling.frugal_sample(a, n, 10.0, cand, u) == 1     # zero-probability proposals never pass
+    assert sampling.frugal_sample(a, n, 10.0, np.array([3, 5]), np.array([0.0, 0.0])) == -1
+    # N p exactly M: accepted for every u < 1
+    b = np.zeros(4, dtype=np.complex128)
+    b[2] = 0.75 + 0.25j                           # n = 4: N p = 16 * (0.5625 + 0.0625) = 10 exactly
+    assert sampling.accept_mask(b, 4, 10.0, np.array([2, 2]), np.array([0.0, np.nextafter(1.0, 0)])).all()
+    assert not sampling.accept_mask(b, 4, 10.0, np.array([2]), np.array([1.0]))[0]
+
+
+def test_frugal_sampling_law_and_sampled_xeb():
+    """Accepted members follow min(1, N p / M) (here = p / M, no member has
+    N p > M), the acceptance rate per draw is the mean of that law, and the
+    linear XEB of the samples from Porter-Thomas amplitudes is 1 (ideal)."""
+    from oracle import sampling
+    rng = np.random.default_rng(2024)
+    n, m_bound = 8, 40.0
+    a = (rng.normal(size=256) + 1j * rng.normal(size=256))
+    a /= np.linalg.norm(a)
+    assert np.max(np.ldexp(np.abs(a) ** 2, n)) < m_bound
+    law = sampling.acceptance_law(a, n, m_bound)
+    rate = law.sum()
+    trials, draws = 20000, 1000
+    counts = np.zeros(256)
+    used = 0
+    samples = []
+    for _ in range(trials):
+        cand = rng.integers(0, 256, size=draws)
+        u = rng.random(draws)
+        t = sampling.frugal_sample(a, n, m_bound, cand, u)
+        assert t >= 0                              # 1000 draws at rate ~1/40 fail with prob. e^-25
+        used += t + 1
+        counts[cand[t]] += 1
+        samples.append(cand[t])
+    # draws until acceptance: geometric with mean 1 / rate
+    mean_draws = used / trials
+    sd = math.sqrt((1 - rate) / rate ** 2 / trials)
+    assert abs(mean_draws - 1 / rate) < 5 * sd
+    # member frequencies against p (chi-square, 255 degrees of freedom)
+    expect = trials * law / rate
+    chi2 = np.sum((counts - expect) ** 2 / expect)
+    assert chi2 < 255 + 6 * math.sqrt(2 * 255)
+    # sampled linear XEB of an ideal sampler of Porter-Thomas amplitudes is ~1
+    f = xeb.linear_xeb(a[np.array(samples)], n)
+    assert abs(f - (256 * np.sum(np.abs(a) ** 4) - 1)) < 0.1
