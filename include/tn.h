@@ -240,6 +240,29 @@ tn_status tn_plan_sync(tn_plan_t* plan, void* stream);
 
 void tn_plan_destroy(tn_plan_t* plan);
 
+/* ---------------------------------------------------------------- frugal sampling */
+
+/* Frugal rejection sampling from one batch of correlated amplitudes (main
+ * text, section III: a 2^k-amplitude batch from one contraction, then frugal
+ * sampling, gives one sample with probability close to 1).  Sample s walks its
+ * n_draws draws: draw t proposes batch member candidates[s * n_draws + t] with
+ * uniform uniforms[s * n_draws + t] in [0, 1); the first draw with
+ *     u * m_bound < 2^n_qubits * |a|^2
+ * (products rounded separately, FP64) is accepted, so an accepted member is
+ * distributed as min(1, N p / M) over the batch.  The random numbers are the
+ * caller's (draw candidates uniformly from the batch).
+ *   amplitudes  DEVICE complex128 [count] (a batch of tn_contract_slices)
+ *   candidates  DEVICE int64 [n_samples * n_draws], each in [0, count)
+ *   uniforms    DEVICE double [n_samples * n_draws]
+ *   first_out   HOST int64 [n_samples]: the accepted draw t of each sample, or
+ *               -1 if none of its draws is accepted (the sample is
+ *               candidates[s * n_draws + first_out[s]]).
+ * Synchronises `stream`.  Empty inputs, m_bound <= 0 or a candidate outside
+ * [0, count) give TN_ERR_ARG (candidates are checked on the device). */
+tn_status tn_frugal_sample(const double* amplitudes, int64_t count, int32_t n_qubits, double m_bound,
+                           const int64_t* candidates, const double* uniforms, int64_t n_draws,
+                           int64_t n_samples, int64_t* first_out, void* stream);
+
 /* ---------------------------------------------------------------- XEB */
 
 /* Linear XEB (main text, Eq. (1): the mean of x = N p is 1 + F):

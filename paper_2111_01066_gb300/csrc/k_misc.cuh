@@ -98,6 +98,29 @@ __global__ void k_amax(const float2* __restrict__ x, int64_t n, float* out) {
   amax_update(out, m);   // blockDim is a multiple of 32
 }
 
+// Frugal rejection sampling (main text, section III): sample s walks its
+// draws t, draw t proposing batch member cand[s][t] with uniform u[s][t]; the
+// first draw with u * M < 2^n |a|^2 is the sample.  Every draw is tested in
+// parallel and the smallest accepted t per sample kept.  The products are
+// rounded separately (no fused multiply-add), as the decision's definition
+// states them.  A candidate outside [0, count) is skipped and flagged.
+__global__ void k_frugal(const double2* __restrict__ a, int64_t count, int n_qubits, double m_bound,
+                         const int64_t* __restrict__ cand, const double* __restrict__ u, int64_t n_draws,
+                         int64_t n_samples, unsigned long long* first, int32_t* bad) {
+  const int64_t total = n_draws * n_samples;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = cand[i];
+    if (c < 0 || c >= count) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    const double2 v = a[c];
+    const double p = __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y));
+    if (__dmul_rn(u[i], m_bound) < ldexp(p, n_qubits))
+      atomicMin(first + i / n_draws, (unsigned long long)(i % n_draws));
+  }
+}
+
 // sum_i |a_i|^2 in FP64 (one block; count is small)
 __global__ void k_xeb_sum(const double2* __restrict__ a, int64_t n, double* __restrict__ out) {
   __shared__ double red[1024];

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <array>
 #include <cstring>
 #include <mutex>
@@ -832,6 +833,9 @@ struct Scratch {
   double* xeb = nullptr;
   int32_t* err = nullptr;
   float* amax = nullptr;   // FP16X3 operand maxima of the last call (A, B)
+  unsigned long long* first = nullptr;   // frugal sampling: first accepted draw per sample
+  int64_t first_cap = 0;
+  int32_t* bad = nullptr;
   uint8_t* ws = nullptr;
   int64_t ws_bytes = 0;
 };
@@ -847,6 +851,7 @@ static Scratch& scratch_for_device() {
     CK(cudaMalloc(&s.err, sizeof(int32_t)));
     CK(cudaMemset(s.err, 0, sizeof(int32_t)));
     CK(cudaMalloc(&s.amax, 2 * sizeof(float)));
+    CK(cudaMalloc(&s.bad, sizeof(int32_t)));
   }
   return s;
 }
@@ -865,6 +870,41 @@ extern "C" tn_status tn_xeb(const double* amps, int64_t count, int32_t n_qubits,
   CK(cudaMemcpyAsync(&sum, scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *xeb_out = std::ldexp(sum / (double)count, n_qubits) - 1.0;
+  API_END
+}
+
+extern "C" tn_status tn_frugal_sample(const double* amps, int64_t count, int32_t n_qubits, double m_bound,
+                                     const int64_t* candidates, const double* uniforms, int64_t n_draws,
+                                     int64_t n_samples, int64_t* first_out, void* stream) {
+  API_BEGIN
+  if (!amps || !candidates || !uniforms || !first_out) fail(TN_ERR_ARG, "tn_frugal_sample: NULL argument");
+  if (count < 1 || n_draws < 1 || n_samples < 1) fail(TN_ERR_ARG, "tn_frugal_sample: empty batch, draws or samples");
+  if (n_qubits < 0 || n_qubits > 1000) fail(TN_ERR_ARG, "tn_frugal_sample: n_qubits out of range");
+  if (!(m_bound > 0.0) || !std::isfinite(m_bound)) fail(TN_ERR_ARG, "tn_frugal_sample: m_bound must be positive");
+  if (n_draws > ((int64_t)1 << 40) / n_samples) fail(TN_ERR_ARG, "tn_frugal_sample: too many draws");
+  Scratch& sc = scratch_for_device();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_samples > sc.first_cap) {
+    CK(cudaStreamSynchronize(s));
+    if (sc.first) CK(cudaFree(sc.first));
+    sc.first = nullptr;
+    CK(cudaMalloc(&sc.first, sizeof(unsigned long long) * (size_t)n_samples));
+    sc.first_cap = n_samples;
+  }
+  CK(cudaMemsetAsync(sc.first, 0xff, sizeof(unsigned long long) * (size_t)n_samples, s));
+  CK(cudaMemsetAsync(sc.bad, 0, sizeof(int32_t), s));
+  const int64_t total = n_draws * n_samples;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+  k_frugal<<<blocks, 256, 0, s>>>(reinterpret_cast<const double2*>(amps), count, n_qubits, m_bound, candidates,
+                                  uniforms, n_draws, n_samples, sc.first, sc.bad);
+  CK(cudaGetLastError());
+  std::vector<unsigned long long> f((size_t)n_samples);
+  int32_t bad = 0;
+  CK(cudaMemcpyAsync(f.data(), sc.first, sizeof(unsigned long long) * f.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&bad, sc.bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) fail(TN_ERR_ARG, "tn_frugal_sample: a candidate index is outside [0, count)");
+  for (int64_t i = 0; i < n_samples; ++i) first_out[i] = f[i] == ~0ULL ? -1 : (int64_t)f[i];
   API_END
 }
 

@@ -78,6 +78,9 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_step_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    "tn_frugal_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
     "tn_plan_chunk_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_step_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -319,3 +322,17 @@ def contract_pair(a, a_wires, b, b_wires, c, c_wires, batch: int = 1, precision:
                                    ctypes.c_void_p(b.data_ptr()), _i32(b_wires), len(b_wires),
                                    ctypes.c_void_p(c.data_ptr()), _i32(c_wires), len(c_wires),
                                    batch, p, complex_mult, _stream_handle(stream)))
+
+
+def frugal_sample(amplitudes, n_qubits: int, m_bound: float, candidates, uniforms, stream=None) -> List[int]:
+    """tn_frugal_sample: amplitudes complex128 CUDA tensor [count]; candidates
+    int64 and uniforms float64 CUDA tensors [n_samples, n_draws]; returns the
+    accepted draw of each sample (-1 if none)."""
+    n_samples, n_draws = (int(candidates.shape[0]), int(candidates.shape[1])) if candidates.dim() == 2 \
+        else (1, int(candidates.numel()))
+    out = (ctypes.c_int64 * n_samples)()
+    _check(load().tn_frugal_sample(ctypes.c_void_p(amplitudes.data_ptr()), amplitudes.numel(), n_qubits,
+                                   float(m_bound), ctypes.c_void_p(candidates.data_ptr()),
+                                   ctypes.c_void_p(uniforms.data_ptr()), n_draws, n_samples, out,
+                                   _stream_handle(stream)))
+    return list(out)

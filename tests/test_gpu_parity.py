@@ -360,6 +360,31 @@ def test_bounded_wait_times_out_and_context_survives(env):
     assert torch.equal(x, y)
 
 
+def test_frugal_sample_against_oracle(env):
+    """Frugal rejection sampling on the GPU takes the oracle's accept decisions
+    (same FP64 products) and returns the same first accepted draw per sample,
+    including draws placed exactly at the acceptance threshold."""
+    tn, torch = env
+    from oracle import sampling
+    rng = np.random.default_rng(77)
+    for n, count, m, n_draws, n_samples in ((12, 4096, 10.0, 64, 500), (6, 64, 10.0, 64, 300),
+                                             (20, 1024, 3.0, 16, 200), (6, 64, 1e6, 8, 50)):
+        a = (rng.normal(size=count) + 1j * rng.normal(size=count)) * 2 ** (-n / 2) / np.sqrt(2)
+        cand = rng.integers(0, count, size=(n_samples, n_draws))
+        u = rng.random((n_samples, n_draws))
+        thr = np.ldexp(a.real[cand[:, 0]] ** 2 + a.imag[cand[:, 0]] ** 2, n) / m
+        u[:, 0] = np.where(thr < 1, thr, u[:, 0])       # proposals on the threshold
+        got = tn.frugal_sample(torch.from_numpy(a).cuda(), n, m, torch.from_numpy(cand).cuda(),
+                               torch.from_numpy(u).cuda())
+        want = [sampling.frugal_sample(a, n, m, cand[s], u[s]) for s in range(n_samples)]
+        assert got == want
+    x = torch.zeros(8, dtype=torch.complex128, device="cuda")
+    with pytest.raises(tn.TnError) as e:
+        tn.frugal_sample(x, 3, 10.0, torch.tensor([[0, 8]], device="cuda"),
+                         torch.zeros((1, 2), dtype=torch.float64, device="cuda"))
+    assert e.value.status == tn.TN_ERR_ARG
+
+
 def test_xeb_against_oracle(env):
     tn, torch = env
     rng = np.random.default_rng(5)
