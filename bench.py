@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2
 WORKLOAD_RUN = {
     "c1": dict(step_slices=None, log2_batch=0),
     "c2": dict(step_slices=None, log2_batch=0),
-    "c3": dict(step_slices=None, log2_batch=0),
+    "c3": dict(step_slices=None, log2_batch=0, trials=128),
     # 2^20+ slices: one seeded aligned block of 1024 slices per step; every slice
     # has the same cost, so the full task's time is T_block * 2^S / 1024
     "c5": dict(step_slices=1024, log2_batch=10, trials=128, arena_gib=160),
@@ -375,6 +375,8 @@ def main() -> int:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(rqcgen.CONFIGS))
     ap.add_argument("--precision", default="auto")
+    ap.add_argument("--select", type=int, default=6,
+                    help="candidate plans timed by tn_plan_select before the run (<= 1: one plan)")
     ap.add_argument("--complex-mult", type=int, default=4, choices=[3, 4],
                     help="4M or 3M complex products on the tensor cores")
     ap.add_argument("--compare-fp32", type=int, default=1)
@@ -446,7 +448,18 @@ def main() -> int:
                    log2_batch_slices=run["log2_batch"], trials=run.get("trials", 64),
                    max_arena_bytes=int(run.get("arena_gib", 96)) << 30)
     t_plan = time.time()
-    plan = tn.Plan(net, precision=prec, complex_mult=args.complex_mult, **plan_kw)
+    selection = None
+    if args.select > 1:
+        # plan selection by measured time over candidate orders (untimed)
+        plan, est = tn.select_plan(net, args.select, bits, precision=prec, complex_mult=args.complex_mult,
+                                   **plan_kw)
+        ch = int(min(range(len(est)), key=lambda i: est[i] if est[i] > 0 else float("inf")))
+        selection = {"candidates": args.select, "estimated_seconds_all_slices": est, "chosen": ch}
+        # the chosen candidate's options (seed + i, memory weight 32 x (1, 1/4, 4)[i % 3]), so
+        # that the comparison paths below contract the same order
+        plan_kw = dict(plan_kw, seed=1 + ch, mem_weight=32.0 * (1.0, 0.25, 4.0)[ch % 3])
+    else:
+        plan = tn.Plan(net, precision=prec, complex_mult=args.complex_mult, **plan_kw)
     t_plan = time.time() - t_plan
     info = plan.info()
     all_slices = 1 << info["log2_slices"]
@@ -657,6 +670,7 @@ def main() -> int:
             "speedup_vs_fp32_path": (value / fp32["value"]) if fp32 else None,
             "error_vs_oracle": err,
             "xeb": f_xeb,
+            "plan_selection": selection,
             "frugal_sampling": frugal,
             "perfect_sample": per_sample,
             "roofline": roof,

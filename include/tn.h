@@ -125,6 +125,8 @@ typedef struct tn_plan_opts {
     int32_t  n_forced_slices;        /* wires the caller slices (0: the planner chooses them all) */
     const int32_t* forced_slice_qubit;  /* [n_forced_slices]: wire (qubit, t) of slice bit j, host */
     const int32_t* forced_slice_t;      /* internal wires only: 1 <= t < gates on that qubit */
+    double   mem_weight;             /* order-search cost = MACs + mem_weight * elements moved
+                                        (<= 0: 32) */
 } tn_plan_opts;
 
 /* Fill opts with defaults: no open qubits, bound 2^30, no forced slices, seed 1,
@@ -226,6 +228,20 @@ tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int3
  * fastest for later calls.  Synchronises `stream`; the arena contents are
  * overwritten (the next call recomputes them). */
 tn_status tn_plan_autotune(tn_plan_t* plan, int32_t reps, void* stream);
+
+/* Plan selection by measured time (SI, TN section: the order whose measured
+ * slice time is smallest is kept, not the one with the fewest flops).  Builds
+ * n_candidates plans from *opts with seeds seed, seed+1, ... and memory weights
+ * cycling through w, w/4, 4w (w = opts->mem_weight or 32), times one chunk of
+ * each on `stream` (after an untimed warm-up call with the same bitstring),
+ * estimates the time for all 2^S slices as chunk time x 2^(S-b), and returns
+ * the fastest plan in *out (its device state is released; the first contract
+ * call re-creates it).  cand_seconds (HOST, [n_candidates], may be NULL)
+ * receives each estimate, -1 for a candidate that could not be built or run
+ * (e.g. its arena does not fit).  Synchronises `stream`; TN_ERR_PLAN if no
+ * candidate ran.  Kernels are not autotuned during the selection. */
+tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                         uint64_t open_bitstring, void* stream, tn_plan_t** out, double* cand_seconds);
 
 /* Kernels one chunk launches with the kernels chosen so far (after the first
  * tn_contract_slices call; TN_ERR_ARG before): leaf select, every

@@ -780,6 +780,72 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   API_END
 }
 
+extern "C" tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                                    uint64_t bitstring, void* stream, tn_plan_t** out, double* cand_seconds) {
+  API_BEGIN
+  if (!net || !opts || !out) fail(TN_ERR_ARG, "tn_plan_select: NULL argument");
+  if (n_candidates < 1 || n_candidates > 1024) fail(TN_ERR_ARG, "tn_plan_select: n_candidates must be in [1, 1024]");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double w0 = opts->mem_weight > 0.0 ? opts->mem_weight : 32.0;
+  const double wmul[3] = {1.0, 0.25, 4.0};
+  tn_plan_t* best = nullptr;
+  double best_t = 0.0;
+  double* amps = nullptr;
+  size_t amps_bytes = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int i = 0; i < n_candidates; ++i) {
+    if (cand_seconds) cand_seconds[i] = -1.0;
+    tn_plan_opts o = *opts;
+    o.seed = opts->seed + (uint64_t)i;
+    o.mem_weight = w0 * wmul[i % 3];
+    tn_plan_t* h = nullptr;
+    if (tn_plan(net, &o, &h) != TN_OK || !h) continue;
+    Plan& p = h->plan;
+    const uint64_t chunk = 1ULL << p.log2_batch;
+    const size_t need = sizeof(double) * 2 * ((size_t)1 << p.root.rank);
+    if (need > amps_bytes) {
+      if (amps) CK(cudaFree(amps));
+      amps = nullptr;
+      CK(cudaMalloc(&amps, need));
+      amps_bytes = need;
+    }
+    double est = -1.0;
+    // warm-up (device state, prologues, graph capture), then one timed chunk
+    if (tn_contract_slices(h, 0, chunk, &bitstring, 1, amps, s) == TN_OK) {
+      CK(cudaEventRecord(e0, s));
+      const tn_status st = tn_contract_slices(h, 0, chunk, &bitstring, 1, amps, s);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (st == TN_OK && tn_plan_sync(h, s) == TN_OK)
+        est = (double)ms / 1e3 * std::ldexp(1.0, (int)p.sliced.size() - p.log2_batch);
+    }
+    CK(cudaStreamSynchronize(s));
+    destroy_device_state(&p);
+    cudaGetLastError();
+    clear_error();
+    if (cand_seconds) cand_seconds[i] = est;
+    if (est >= 0.0 && (!best || est < best_t)) {
+      if (best) tn_plan_destroy(best);
+      best = h;
+      best_t = est;
+    } else {
+      tn_plan_destroy(h);
+    }
+  }
+  if (amps) cudaFree(amps);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!best) fail(TN_ERR_PLAN, "tn_plan_select: no candidate plan could be built and run");
+  best->plan.sticky = TN_OK;
+  *out = best;
+  API_END
+}
+
 extern "C" tn_status tn_plan_chunk_launches(const tn_plan_t* h, int32_t* launches) {
   API_BEGIN
   if (!h || !launches) fail(TN_ERR_ARG, "tn_plan_chunk_launches: NULL argument");

@@ -13,6 +13,7 @@
 #include <new>
 #include <numeric>
 #include <random>
+#include <thread>
 #include <unordered_map>
 
 #include "tn_internal.h"
@@ -22,7 +23,9 @@ namespace {
 
 constexpr int MAXW = 4096;
 using WS = std::bitset<MAXW>;
-constexpr double ALPHA = 32.0;   // complex MACs charged per complex64 element moved
+// complex MACs charged per complex64 element moved (tn_plan_opts.mem_weight;
+// set for the duration of one build_plan on its thread)
+thread_local double g_alpha = 32.0;
 
 double pow2(int e) { return std::ldexp(1.0, e); }
 
@@ -155,7 +158,7 @@ struct Tree {
 struct CostModel {
   // cost of one pairwise step from log2 sizes: MACs + ALPHA * elements moved
   static double step(int u, int a, int b, int c) {
-    return pow2(u) + ALPHA * (pow2(a) + pow2(b) + pow2(c));
+    return pow2(u) + g_alpha * (pow2(a) + pow2(b) + pow2(c));
   }
 };
 
@@ -470,6 +473,29 @@ std::vector<int> post_order(const Tree& t) {
   return order;
 }
 
+// Work for all 2^S slices when every node is computed once per distinct value
+// of the sliced wires it depends on (the executor shares slice-independent
+// parts of a chunk's slices and runs slice-free subtrees once):
+// sum over steps of 2^|sliced wires below it| x its per-slice cost.
+double reuse_cost(const Tree& t, const WS& sl) {
+  if (t.merges.empty()) return 0.0;
+  const WS keep = ~sl;
+  std::vector<WS> dep(t.sets.size());
+  for (int i = 0; i < t.L; ++i) dep[i] = t.sets[i] & sl;
+  double c = 0;
+  for (int i : post_order(t)) {
+    const int x = t.merges[i].first, y = t.merges[i].second;
+    dep[t.L + i] = dep[x] | dep[y];
+    const WS& a = t.sets[x];
+    const WS& b = t.sets[y];
+    const WS& r = t.sets[t.L + i];
+    c += std::ldexp(CostModel::step((int)((a | b) & keep).count(), (int)(a & keep).count(),
+                                    (int)(b & keep).count(), (int)(r & keep).count()),
+                    (int)dep[t.L + i].count());
+  }
+  return c;
+}
+
 // --------------------------------------------------------- slicing
 // Main text, section II: slice wires until every intermediate fits the bound;
 // each pick minimises the total cost 2^S * cost(per slice).
@@ -618,44 +644,96 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   double best_total = std::numeric_limits<double>::infinity();
   std::vector<int> all(L);
   std::iota(all.begin(), all.end(), 0);
-  for (int tr = 0; tr < trials; ++tr) {
+  // Trials are independent (trial tr draws from seed * 1000003 + tr) and run
+  // on all host cores; the best by reuse-aware work wins, ties to the lowest
+  // trial index, so the result does not depend on the thread count.
+  struct TrialResult {
+    double total = std::numeric_limits<double>::infinity();
+    Tree tree;
+    std::vector<int> sl;
+  };
+  std::vector<TrialResult> res(trials);
+  auto run_trial = [&](int tr) {
     std::mt19937_64 rng(o.seed * 1000003ULL + (uint64_t)tr);
     const double eps_choices[4] = {0.05, 0.12, 0.2, 0.3};
     Bisector bis{adj, rng, eps_choices[(tr / 2) % 4], (tr % 2) ? 6 : 8, 3};
     Tree t = base;
-    if (L == 1) {
-      // single tensor: no merge
-    } else {
-      bis.build(t, all);
-    }
-    std::vector<int> sl = (L > 1) ? choose_slices(t, open_ws, bound, o.min_log2_slices)
-                                  : std::vector<int>{};
+    if (L > 1) bis.build(t, all);
+    std::vector<int> sl = (L > 1) ? choose_slices(t, open_ws, bound, o.min_log2_slices) : std::vector<int>{};
     WS slw;
     for (int w : sl) slw.set(w);
-    double total = pow2((int)sl.size()) * tree_cost(t, slw);
-    if (total < best_total) {
-      best_total = total;
-      best_tree = t;
-      best_sl = sl;
-    }
+    res[tr].total = reuse_cost(t, slw);
+    res[tr].tree = std::move(t);
+    res[tr].sl = std::move(sl);
+  };
+  {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nth = (int)std::min<unsigned>(hw, (unsigned)trials);
+    const double alpha = g_alpha;
+    std::vector<std::exception_ptr> errs(nth);
+    std::vector<std::thread> pool;
+    for (int th = 0; th < nth; ++th)
+      pool.emplace_back([&, th]() {
+        g_alpha = alpha;
+        try {
+          for (int tr = th; tr < trials; tr += nth) run_trial(tr);
+        } catch (...) {
+          errs[th] = std::current_exception();
+        }
+      });
+    for (auto& t : pool) t.join();
+    for (auto& e : errs)
+      if (e) std::rethrow_exception(e);
   }
+  // subtree reconfiguration with the slices in place (then re-slicing) on the
+  // best few trials, in parallel: its gains vary a lot from tree to tree, so
+  // the best trial before it is not always the best after it
   if (L == 1 && o.min_log2_slices > 0) fail(TN_ERR_PLAN, "a single-tensor network cannot be sliced");
-  // subtree reconfiguration with the slices in place, then re-slice if that helps
-  if (L > 2) {
-    WS slw;
-    for (int w : best_sl) slw.set(w);
-    Tree t2 = best_tree;
-    reconfigure(t2, slw, 3);
-    std::vector<int> sl2 = choose_slices(t2, open_ws, bound, o.min_log2_slices);
-    WS s2;
-    for (int w : sl2) s2.set(w);
-    const double tot2 = pow2((int)sl2.size()) * tree_cost(t2, s2);
-    if (tot2 < best_total) {
-      best_total = tot2;
-      best_tree = t2;
-      best_sl = sl2;
-    }
+  std::vector<int> rank_tr(trials);
+  std::iota(rank_tr.begin(), rank_tr.end(), 0);
+  std::stable_sort(rank_tr.begin(), rank_tr.end(), [&](int x, int y) { return res[x].total < res[y].total; });
+  const int n_reconf = L > 2 ? std::min(trials, 8) : 0;
+  std::vector<TrialResult> rec(n_reconf);
+  {
+    const double alpha = g_alpha;
+    std::vector<std::exception_ptr> errs(n_reconf);
+    std::vector<std::thread> pool;
+    for (int j = 0; j < n_reconf; ++j)
+      pool.emplace_back([&, j]() {
+        g_alpha = alpha;
+        try {
+          const TrialResult& r = res[rank_tr[j]];
+          WS slw;
+          for (int w : r.sl) slw.set(w);
+          Tree t2 = r.tree;
+          reconfigure(t2, slw, 3);
+          std::vector<int> sl2 = choose_slices(t2, open_ws, bound, o.min_log2_slices);
+          WS s2;
+          for (int w : sl2) s2.set(w);
+          rec[j].total = reuse_cost(t2, s2);
+          rec[j].tree = std::move(t2);
+          rec[j].sl = std::move(sl2);
+        } catch (...) {
+          errs[j] = std::current_exception();
+        }
+      });
+    for (auto& t : pool) t.join();
+    for (auto& e : errs)
+      if (e) std::rethrow_exception(e);
   }
+  // best of the trials and of their reconfigurations (ties: trials first, lower rank first)
+  for (int tr = 0; tr < trials; ++tr)
+    if (res[tr].total < best_total) {
+      best_total = res[tr].total;
+      best_tree = res[tr].tree;
+      best_sl = res[tr].sl;
+    }
+  for (int j = 0; j < n_reconf; ++j)
+    if (rec[j].total < best_total) {
+      best_total = rec[j].total;
+      best_tree = rec[j].tree;
+      best_sl = rec[j].sl;
+    }
   Tree& T = best_tree;
   WS SL;
   for (int w : best_sl) SL.set(w);
@@ -1104,6 +1182,7 @@ extern "C" tn_status tn_plan_default_opts(tn_plan_opts* o) {
   o->log2_batch_slices = 0;
   o->max_arena_bytes = (int64_t)96 << 30;
   o->fuse_permute = 1;
+  o->mem_weight = 0.0;
   return TN_OK;
 }
 
@@ -1112,7 +1191,17 @@ extern "C" tn_status tn_plan(const tn_network_t* net, const tn_plan_opts* opts, 
     clear_error();
     if (!net || !opts || !out) fail(TN_ERR_ARG, "tn_plan: NULL argument");
     *out = nullptr;
-    Plan* p = build_plan(net->net, *opts);
+    if (!(opts->mem_weight <= 0.0 || (opts->mem_weight >= 1e-6 && opts->mem_weight <= 1e9)))
+      fail(TN_ERR_ARG, "mem_weight must be <= 0 (default) or in [1e-6, 1e9]");
+    g_alpha = opts->mem_weight > 0.0 ? opts->mem_weight : 32.0;
+    Plan* p = nullptr;
+    try {
+      p = build_plan(net->net, *opts);
+    } catch (...) {
+      g_alpha = 32.0;
+      throw;
+    }
+    g_alpha = 32.0;
     auto* h = new (std::nothrow) tn_plan_s;
     if (!h) {
       delete p;

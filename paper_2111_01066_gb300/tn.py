@@ -51,7 +51,8 @@ class tn_plan_opts(ctypes.Structure):
                 ("max_arena_bytes", ctypes.c_int64), ("fuse_permute", ctypes.c_int32),
                 ("n_forced_slices", ctypes.c_int32),
                 ("forced_slice_qubit", ctypes.POINTER(ctypes.c_int32)),
-                ("forced_slice_t", ctypes.POINTER(ctypes.c_int32))]
+                ("forced_slice_t", ctypes.POINTER(ctypes.c_int32)),
+                ("mem_weight", ctypes.c_double)]
 
 
 class tn_plan_stats(ctypes.Structure):
@@ -81,6 +82,9 @@ _SIGS = {
     "tn_frugal_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
+    "tn_plan_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tn_plan_opts), ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "tn_plan_chunk_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_step_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -182,6 +186,29 @@ def default_opts() -> tn_plan_opts:
     return o
 
 
+def _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed, trials,
+               log2_batch_slices, max_arena_bytes, fuse_permute, forced_slices, mem_weight):
+    o = default_opts()
+    o.open_mask = open_mask
+    o.max_log2_intermediate = max_log2_intermediate
+    o.min_log2_slices = min_log2_slices
+    o.seed = seed
+    o.trials = trials
+    o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    o.complex_mult = complex_mult
+    o.log2_batch_slices = log2_batch_slices
+    if max_arena_bytes:
+        o.max_arena_bytes = max_arena_bytes
+    o.fuse_permute = fuse_permute
+    fq = _i32([q for q, _ in forced_slices])
+    ft = _i32([t for _, t in forced_slices])
+    o.n_forced_slices = len(forced_slices)
+    o.forced_slice_qubit = ctypes.cast(fq, ctypes.POINTER(ctypes.c_int32))
+    o.forced_slice_t = ctypes.cast(ft, ctypes.POINTER(ctypes.c_int32))
+    o.mem_weight = float(mem_weight)
+    return o, (fq, ft)
+
+
 class Plan:
     """tn_plan: contraction order + slice set + device step program (host only)."""
 
@@ -189,30 +216,18 @@ class Plan:
                  min_log2_slices: int = 0, precision: str = "fp32", complex_mult: int = 4,
                  seed: int = 1, trials: int = 64, log2_batch_slices: int = 0,
                  max_arena_bytes: int = 0, fuse_permute: int = 1,
-                 forced_slices: Sequence[Tuple[int, int]] = ()):
-        lib = load()
-        o = default_opts()
-        o.open_mask = open_mask
-        o.max_log2_intermediate = max_log2_intermediate
-        o.min_log2_slices = min_log2_slices
-        o.seed = seed
-        o.trials = trials
-        o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
-        o.complex_mult = complex_mult
-        o.log2_batch_slices = log2_batch_slices
-        if max_arena_bytes:
-            o.max_arena_bytes = max_arena_bytes
-        o.fuse_permute = fuse_permute
-        fq = _i32([q for q, _ in forced_slices])
-        ft = _i32([t for _, t in forced_slices])
-        o.n_forced_slices = len(forced_slices)
-        o.forced_slice_qubit = ctypes.cast(fq, ctypes.POINTER(ctypes.c_int32))
-        o.forced_slice_t = ctypes.cast(ft, ctypes.POINTER(ctypes.c_int32))
-        h = ctypes.c_void_p()
-        _check(lib.tn_plan(network.handle, ctypes.byref(o), ctypes.byref(h)))
-        self.handle = h
+                 forced_slices: Sequence[Tuple[int, int]] = (), mem_weight: float = 0.0,
+                 _handle=None):
         self.network = network
         self.open_mask = open_mask
+        if _handle is not None:
+            self.handle = _handle
+            return
+        o, keep = _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed,
+                             trials, log2_batch_slices, max_arena_bytes, fuse_permute, forced_slices, mem_weight)
+        h = ctypes.c_void_p()
+        _check(load().tn_plan(network.handle, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
 
     def info(self) -> dict:
         s = tn_plan_stats()
@@ -336,3 +351,19 @@ def frugal_sample(amplitudes, n_qubits: int, m_bound: float, candidates, uniform
                                    ctypes.c_void_p(uniforms.data_ptr()), n_draws, n_samples, out,
                                    _stream_handle(stream)))
     return list(out)
+
+
+def select_plan(network: Network, n_candidates: int, bitstring: int, stream=None, open_mask: int = 0,
+                max_log2_intermediate: int = 30, min_log2_slices: int = 0, precision: str = "fp32",
+                complex_mult: int = 4, seed: int = 1, trials: int = 64, log2_batch_slices: int = 0,
+                max_arena_bytes: int = 0, fuse_permute: int = 1, forced_slices: Sequence[Tuple[int, int]] = (),
+                mem_weight: float = 0.0) -> Tuple["Plan", List[float]]:
+    """tn_plan_select: the fastest of n_candidates plans by measured chunk time;
+    returns the plan and every candidate's estimated seconds for all slices."""
+    o, keep = _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed, trials,
+                         log2_batch_slices, max_arena_bytes, fuse_permute, forced_slices, mem_weight)
+    h = ctypes.c_void_p()
+    est = (ctypes.c_double * n_candidates)()
+    _check(load().tn_plan_select(network.handle, ctypes.byref(o), n_candidates, bitstring,
+                                 _stream_handle(stream), ctypes.byref(h), est))
+    return Plan(network, open_mask=open_mask, _handle=h), list(est)

@@ -128,3 +128,17 @@ def test_forced_slices_are_used_and_validated(tn):
         with pytest.raises(tn.TnError) as e:
             tn.Plan(net, open_mask=om, forced_slices=bad, trials=2)
         assert e.value.status == tn.TN_ERR_ARG
+
+
+def test_mem_weight_option(tn):
+    """The order search's memory weight is an option: validated, and a plan
+    built with the default weight equals one built with weight 32 explicitly."""
+    circ, om, _ = rqcgen.config_circuit("c2")
+    net = tn.Network(circ)
+    a = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3)
+    b = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3, mem_weight=32.0)
+    assert a.step_shapes() == b.step_shapes()
+    tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3, mem_weight=2.0)
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, mem_weight=1e12)
+    assert e.value.status == tn.TN_ERR_ARG

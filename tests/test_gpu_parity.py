@@ -171,6 +171,27 @@ def test_c2_against_golden(env, prec, cm):
     assert err < PLAN_TOL[prec]
 
 
+@pytest.mark.parametrize("cand", range(6))
+def test_c3_selection_candidates_against_golden(env, cand):
+    """Every plan that plan selection can hand the benchmark (candidate i: seed
+    1 + i, memory weight 32 x (1, 1/4, 4)[i % 3]) gives the oracle's C3
+    amplitudes at full size (all 4096 slices, BF16x3)."""
+    tn, torch = env
+    from tests.golden.make_golden import read
+    want = read("c3")
+    cfg = rqcgen.CONFIGS["c3"]
+    circ, om, cb = rqcgen.config_circuit("c3")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
+                   min_log2_slices=cfg["log2_slices"], precision="bf16x3", seed=1 + cand, trials=128,
+                   mem_weight=32.0 * (1.0, 0.25, 4.0)[cand % 3])
+    out = torch.zeros(2 << 12, dtype=torch.float64, device="cuda")
+    plan.contract_slices(0, 1 << plan.info()["log2_slices"], [cb], out)
+    plan.sync()
+    err = _relerr(out.cpu().numpy().view(np.complex128), want)
+    print(f"c3 candidate {cand}: rel amp err {err:.3e}")
+    assert err < PLAN_TOL["bf16x3"]
+
+
 @pytest.mark.parametrize("prec,cm", [("bf16x3", 4), ("bf16x3", 3), ("fp16x3", 4), ("fp16x3", 3), ("tf32", 4),
                                      ("fp32", 4)])
 def test_c3_all_slices_against_golden(env, prec, cm):
@@ -211,6 +232,21 @@ def test_c2_autotuned_plan_still_matches_golden(env, prec):
     for _ in range(2):   # eager chunk, then the re-captured graph
         got = _run_plan(tn, torch, plan, 0, 1, [cb], 10)
         assert _relerr(got, want) < PLAN_TOL[prec]
+
+
+def test_plan_selection_by_measured_time(env):
+    """tn_plan_select times one chunk of each candidate plan and keeps the
+    fastest; the chosen plan still gives the oracle's amplitudes."""
+    tn, torch = env
+    from tests.golden.make_golden import read
+    want = read("c2")
+    circ, om, cb = rqcgen.config_circuit("c2")
+    plan, est = tn.select_plan(tn.Network(circ), 5, cb, open_mask=om, max_log2_intermediate=24,
+                               precision="bf16x3", trials=8, seed=11)
+    assert len(est) == 5 and all(e > 0 for e in est)
+    n_sl = 1 << plan.info()["log2_slices"]
+    got = _run_plan(tn, torch, plan, 0, n_sl, [cb], 10)
+    assert _relerr(got, want) < PLAN_TOL["bf16x3"]
 
 
 SHAPES = [  # (m bits, k bits, n bits): several tiles, ragged (smaller than a tile), degenerate
