@@ -47,6 +47,7 @@ constexpr int TC_TK = 16;            // complex k per pipeline stage
 constexpr int TC_KP = 2 * TC_TK;     // real K' per stage
 constexpr int TC_MAX_A = 8;           // A ring slots
 constexpr int TC_MAX_B = 4;           // B' ring slots
+constexpr int TC_MAX_ACC = 8;         // TMEM accumulator sets
 constexpr int TC_EPI_WARPS = 4;
 constexpr int TC_MMA_WARP = 4;
 constexpr int TC_LOAD_WARPS = 8;
@@ -129,8 +130,8 @@ struct TcArgs {
   int32_t na;            // A ring slots (TcPl::A_SLOT bytes each)
   int32_t nbs;           // B' ring slots (one (n tile, k chunk) image each)
   int32_t fa_count;      // arrivals expected on an A slot's "full" barrier
-  int32_t n_acc;         // TMEM accumulator sets: 2 (the epilogue of a tile overlaps the
-                         // next tile's MMAs) or 1 (3M with 128-column tiles: 384 columns)
+  int32_t n_acc;         // TMEM accumulator sets (1..8), as many as fit 512 columns: the MMAs
+                         // run up to n_acc tiles ahead of the epilogue (3M 128-column tiles: 1)
   int32_t nmw;           // m bits that are tensor-map rows (contiguous after the k bits)
   int32_t hi_shift;      // storage position where tensor-map dimension 2 starts
   int64_t c2_inst_mul;   // dimension-2 step per linear instance (tn_contract_pair batches)
@@ -144,7 +145,24 @@ struct TcArgs {
   int32_t n_split;
   float2* c_part;
   int64_t c_part_stride;
+  int32_t ls_split, ls_nt, ls_mt;   // log2 of n_split, n_nt, n_mt (all powers of two)
 };
+
+// Work unit `tile` -> split index, n tile, m tile, instance: shifts and masks
+// (the extents are powers of two), cheap enough for one-chunk tiles.
+struct TileIdx {
+  int s, nt, mt, inst;
+};
+__device__ __forceinline__ TileIdx tile_decode(int64_t tile, const TcArgs& a) {
+  TileIdx r;
+  r.s = (int)(tile & (int64_t)(a.n_split - 1));
+  const int64_t otile = tile >> a.ls_split;
+  r.nt = (int)(otile & (int64_t)(a.n_nt - 1));
+  const int64_t rest = otile >> a.ls_nt;
+  r.mt = (int)(rest & (int64_t)(a.n_mt - 1));
+  r.inst = (int)(rest >> a.ls_mt);
+  return r;
+}
 constexpr int TC_EPI_STRIDE = 17;                                  // staging row stride (float2)
 constexpr int TC_EPI_BYTES = TC_EPI_WARPS * 32 * TC_EPI_STRIDE * 8;  // epilogue staging
 
@@ -575,8 +593,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   uint64_t* fullB = bars + 3 * TC_MAX_A;
   uint64_t* emptyB = fullB + TC_MAX_B;
   uint64_t* tfull = emptyB + TC_MAX_B;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* fin = tempty + 2;
+  uint64_t* tempty = tfull + TC_MAX_ACC;
+  uint64_t* fin = tempty + TC_MAX_ACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int64_t* offCm = reinterpret_cast<int64_t*>(tmem_slot + 4);
@@ -601,7 +619,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       mbar_init(smem_u32(&fullB[s]), 1);
       mbar_init(smem_u32(&emptyB[s]), 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < TC_MAX_ACC; ++i) {
       mbar_init(smem_u32(&tfull[i]), 1);
       mbar_init(smem_u32(&tempty[i]), TC_EPI_WARPS * 32);
     }
@@ -631,11 +649,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-        const int64_t otile = tile / a.n_split;
-        const int kc0 = (int)(tile % a.n_split) * kc_per;
-        const int64_t rest = otile / a.n_nt;
-        const int mt = (int)(rest % a.n_mt);
-        const int inst = (int)(rest / a.n_mt);
+        const TileIdx ti = tile_decode(tile, a);
+        const int kc0 = ti.s * kc_per;
+        const int mt = ti.mt, inst = ti.inst;
         // tensor-map coordinates of the tile: rows from the m bits after the
         // first tm, dimension 2 from the remaining m bits and the instance bits
         const int c1 = (mt & ((1 << (a.nmw - g.tm)) - 1)) << g.tm;
@@ -665,10 +681,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-        const int64_t otile = tile / a.n_split;
-        const int kc0 = (int)(tile % a.n_split) * kc_per;
-        const int nt = (int)(otile % a.n_nt);
-        const int inst = (int)(otile / a.n_nt / a.n_mt);
+        const TileIdx ti = tile_decode(tile, a);
+        const int kc0 = ti.s * kc_per;
+        const int nt = ti.nt, inst = ti.inst;
         const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * (int64_t)b_slot;
         for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
           if (!mbar_wait(smem_u32(&emptyB[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
@@ -781,9 +796,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         goff[i] = (rok && k < tkv) ? roff + deposit_hi((uint64_t)k, g.a_kpos, 0, g.tk) : -1;
       }
       auto tile_base = [&](int64_t tile) -> const float2* {
-        const int64_t rest = tile / a.n_split / a.n_nt;
-        const int mt = (int)(rest % a.n_mt);
-        const int inst = (int)(rest / a.n_mt);
+        const TileIdx ti = tile_decode(tile, a);
+        const int mt = ti.mt, inst = ti.inst;
         return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) +
                deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
       };
@@ -805,15 +819,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int slot = 0;
       uint32_t ph = 0;
       int64_t tile = blockIdx.x;
-      int kc = (int)(tile % a.n_split) * kc_per;
+      int kc = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
       const float2* An = tile < a.n_tiles ? tile_base(tile) : g.A;
       float2 v0[8], v1[8];
       auto body = [&](float2(&vc)[8], float2(&vn)[8]) -> bool {
         int64_t ntile = tile;
         int nkc = kc + 1;
-        if (nkc == (int)(tile % a.n_split) * kc_per + kc_per) {
+        if (nkc == (int)(tile & (int64_t)(a.n_split - 1)) * kc_per + kc_per) {
           ntile += gridDim.x;
-          nkc = (int)(ntile % a.n_split) * kc_per;
+          nkc = (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per;
           if (ntile < a.n_tiles) An = tile_base(ntile);
         }
         if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
@@ -868,9 +882,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         }
       }
       auto tile_base = [&](int64_t tile) -> const float2* {
-        const int64_t rest = tile / a.n_split / a.n_nt;
-        const int mt = (int)(rest % a.n_mt);
-        const int inst = (int)(rest / a.n_mt);
+        const TileIdx ti = tile_decode(tile, a);
+        const int mt = ti.mt, inst = ti.inst;
         return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) + deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
       };
       int slot = 0;
@@ -879,7 +892,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         bool ok = true;
         for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
           const float2* At = tile_base(tile);
-          const int kc0 = (int)(tile % a.n_split) * kc_per;
+          const int kc0 = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
           for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
             const float2* Ak = At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk);
             uint8_t* sa = aring + slot * P::A_SLOT;
@@ -927,15 +940,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
             }
         };
         int64_t tile = blockIdx.x;
-        int kc = (int)(tile % a.n_split) * kc_per;
+        int kc = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
         const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
         const float2* An = At;     // base of the tile of the prefetched slot
         auto body = [&](float4(&vc)[NCH][KPC / 2], float4(&vn)[NCH][KPC / 2]) -> bool {
           int64_t ntile = tile;
           int nkc = kc + 1;
-          if (nkc == (int)(tile % a.n_split) * kc_per + kc_per) {
+          if (nkc == (int)(tile & (int64_t)(a.n_split - 1)) * kc_per + kc_per) {
             ntile += gridDim.x;
-            nkc = (int)(ntile % a.n_split) * kc_per;
+            nkc = (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per;
             if (ntile < a.n_tiles) An = tile_base(ntile);
           }
           if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
@@ -988,8 +1001,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int64_t it = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++it) {
-        const int acc = a.n_acc == 2 ? (int)(it & 1) : 0;
-        const uint32_t aph = (uint32_t)((a.n_acc == 2 ? (it >> 1) : it) & 1);
+        const int acc = (int)((uint32_t)it % (uint32_t)a.n_acc);
+        const uint32_t aph = ((uint32_t)it / (uint32_t)a.n_acc) & 1u;
         if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * setw);
@@ -1098,17 +1111,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     const bool track = g.amax_c != nullptr && a.n_split == 1;
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-      const int acc = a.n_acc == 2 ? (int)(it & 1) : 0;
-      const uint32_t aph = (uint32_t)((a.n_acc == 2 ? (it >> 1) : it) & 1);
+      const int acc = (int)((uint32_t)it % (uint32_t)a.n_acc);
+      const uint32_t aph = ((uint32_t)it / (uint32_t)a.n_acc) & 1u;
       // warp-uniform decision: the TMEM loads and shuffles below need all 32 lanes
       if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, a.err))) break;
       tc_fence_after();
-      const int64_t otile = tile / a.n_split;
-      const int nt = (int)(otile % a.n_nt);
-      const int64_t rest = otile / a.n_nt;
-      const int mt = (int)(rest % a.n_mt);
-      const int inst = (int)(rest / a.n_mt);
-      float2* Cb = a.n_split > 1 ? a.c_part + (tile % a.n_split) * a.c_part_stride : g.C;
+      const TileIdx ti = tile_decode(tile, a);
+      const int nt = ti.nt, mt = ti.mt, inst = ti.inst;
+      float2* Cb = a.n_split > 1 ? a.c_part + ti.s * a.c_part_stride : g.C;
       float2* C = Cb + inst_offset(inst, g.c_istride, g.c_bpos, g.nb) +
                   deposit_hi((uint64_t)mt, g.c_mpos, g.tm, g.nm) +
                   deposit_hi((uint64_t)nt, g.c_npos, a.tnb, g.nn);

@@ -262,6 +262,9 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
     }
   }
   t.n_tiles *= t.n_split;
+  t.ls_split = __builtin_ctz((unsigned)t.n_split);
+  t.ls_nt = g.nn - g.tn;
+  t.ls_mt = g.nm - g.tm;
   setup_tma(L, a_bits, n_lin);
   // rings: B' slots first (3, or 4 when small), the rest of the budget to A slots
   const int b_slot = npl * b_plane;
@@ -269,8 +272,9 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.nbs = b_slot <= 16384 ? TC_MAX_B : 3;
   t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
   t.fa_count = (t.a_tma && kid == K_TC_TF32) ? 1 : TC_LOAD_THREADS;
-  // two accumulator sets when they fit the 512 TMEM columns
-  t.n_acc = 2 * (tc_is_3m(kid) ? 3 : 2) * t.tn_c <= TC_TMEM_COLS ? 2 : 1;
+  // as many accumulator sets as fit the 512 TMEM columns (at most 8): narrow
+  // tiles let the MMAs run several tiles ahead of the epilogue
+  t.n_acc = std::max(1, std::min(TC_MAX_ACC, TC_TMEM_COLS / ((tc_is_3m(kid) ? 3 : 2) * t.tn_c)));
   L.smem = std::max(t.na * geo.a_slot + t.nbs * b_slot + 4096 + TC_EPI_BYTES + 1024, TC_MIN_SMEM);
   // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
   t.epi_ok = 0;
