@@ -145,7 +145,7 @@ struct TcArgs {
   int32_t n_split;
   float2* c_part;
   int64_t c_part_stride;
-  int32_t ls_split, ls_nt, ls_mt;   // log2 of n_split, n_nt, n_mt (all powers of two)
+  int32_t ls_split, ls_nt, ls_mt, ls_kc;   // log2 of n_split, n_nt, n_mt, n_kc (powers of two)
 };
 
 // Work unit `tile` -> split index, n tile, m tile, instance: shifts and masks
@@ -432,17 +432,18 @@ __global__ void k_tc_prep_b(const TcArgs a) {
   const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
   const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
   const float sc = operand_scale<MODE>(g.amax_b);
+  const int lg_block = 31 - __clz(per_block);   // per_block is a power of two
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx % per_block);
-    const int64_t blk = idx / per_block;
+    const int q = (int)(idx & (per_block - 1));
+    const int64_t blk = idx >> lg_block;
     // q in image order: row within the 8-row group fastest, then chunk, then group
     const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
     const int row = rg * 8 + rlo;
     const int t = row & 1, nl = row >> 1;
-    const int kc = (int)(blk % a.n_kc);
-    const int nt = (int)((blk / a.n_kc) % a.n_nt);
-    const int inst = (int)(blk / ((int64_t)a.n_kc * a.n_nt));
+    const int kc = (int)(blk & (a.n_kc - 1));
+    const int nt = (int)((blk >> a.ls_kc) & (a.n_nt - 1));
+    const int inst = (int)(blk >> (a.ls_kc + a.ls_nt));
     float vals[2 * KPC];
     const bool n_ok = nl < tnv;
     int64_t base = 0;
@@ -491,17 +492,19 @@ __global__ void k_tc_prep_b3(const TcArgs a) {
   const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
   const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
   const float sc = operand_scale<MODE>(g.amax_b);
+  const int per_plane = rows * CPR;              // a power of two
+  const int lg_plane = 31 - __clz(per_plane);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t blk = idx / per_block;
-    const int pq = (int)(idx % per_block);
-    const int pl = pq / (rows * CPR), q = pq % (rows * CPR);
+    const int64_t pb = idx >> lg_plane;            // block * PLANES + plane
+    const int64_t blk = pb / P::PLANES;
+    const int pl = (int)(pb - blk * P::PLANES), q = (int)(idx & (per_plane - 1));
     const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
     const int n = rg * 8 + rlo;
     const int half = c / (CPR / 2), k0 = (c % (CPR / 2)) * EPC;   // k0.. within the half's 16 k
-    const int kc = (int)(blk % a.n_kc);
-    const int nt = (int)((blk / a.n_kc) % a.n_nt);
-    const int inst = (int)(blk / ((int64_t)a.n_kc * a.n_nt));
+    const int kc = (int)(blk & (a.n_kc - 1));
+    const int nt = (int)((blk >> a.ls_kc) & (a.n_nt - 1));
+    const int inst = (int)(blk >> (a.ls_kc + a.ls_nt));
     float2 b[8];
     const bool n_ok = n < tnv;
     int64_t base = 0;
@@ -736,6 +739,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     } else if constexpr (MODE != TC_TF32) {
       const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
       constexpr int NCH = TC_M * (TC_KP * T::ESZ / 16) / TC_LOAD_THREADS;
+      // this thread's raw-tile and plane offsets, the same in every slot
+      int roff[NCH][2], woff[NCH];
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int q = lt + j * TC_LOAD_THREADS;
+        const int row = q % TC_M, c = q / TC_M;     // 16-byte output chunk: 4 complex
+        roff[j][0] = tc_elem_off(row, 8 * c, 4);
+        roff[j][1] = tc_elem_off(row, 8 * c + 4, 4);
+        woff[j] = tc_elem_off(row, 8 * c, T::ESZ);
+      }
       int slot = 0;
       uint32_t ph = 0;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
@@ -746,26 +759,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           float4 x[NCH][2];
 #pragma unroll
           for (int j = 0; j < NCH; ++j) {
-            const int q = lt + j * TC_LOAD_THREADS;
-            const int row = q % TC_M, c = q / TC_M;     // 16-byte output chunk: 4 complex
-            x[j][0] = *reinterpret_cast<const float4*>(sa + tc_elem_off(row, 8 * c, 4));
-            x[j][1] = *reinterpret_cast<const float4*>(sa + tc_elem_off(row, 8 * c + 4, 4));
+            x[j][0] = *reinterpret_cast<const float4*>(sa + roff[j][0]);
+            x[j][1] = *reinterpret_cast<const float4*>(sa + roff[j][1]);
           }
           // every converter has read the tile; all agree whether to go on
           stop = named_barrier_or(1, TC_LOAD_THREADS, !got || *abort_flag);
           if (stop) break;
 #pragma unroll
           for (int j = 0; j < NCH; ++j) {
-            const int q = lt + j * TC_LOAD_THREADS;
-            const int row = q % TC_M, c = q / TC_M;
             const float xs[8] = {x[j][0].x, x[j][0].y, x[j][0].z, x[j][0].w,
                                  x[j][1].x, x[j][1].y, x[j][1].z, x[j][1].w};
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) split_pair<MODE>(xs[2 * i] * sc_a, xs[2 * i + 1] * sc_a, hi[i], lo[i]);
-            const int off = tc_elem_off(row, 8 * c, T::ESZ);
-            *reinterpret_cast<uint4*>(sa + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(sa + a_plane + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<uint4*>(sa + woff[j]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(sa + a_plane + woff[j]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
           fence_proxy_async();
           mbar_arrive(smem_u32(&fullA[slot]));
@@ -1119,9 +1127,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       const TileIdx ti = tile_decode(tile, a);
       const int nt = ti.nt, mt = ti.mt, inst = ti.inst;
       float2* Cb = a.n_split > 1 ? a.c_part + ti.s * a.c_part_stride : g.C;
-      float2* C = Cb + inst_offset(inst, g.c_istride, g.c_bpos, g.nb) +
-                  deposit_hi((uint64_t)mt, g.c_mpos, g.tm, g.nm) +
-                  deposit_hi((uint64_t)nt, g.c_npos, a.tnb, g.nn);
+      // the tile's base in C: its instance, m-tile and n-tile bits deposited at
+      // their positions in C, one bit per lane, summed over the warp
+      int64_t cb = (int64_t)inst * g.c_istride;
+      {
+        const int n_i = g.nb, n_m = g.nm - g.tm, n_all = g.nb + (g.nm - g.tm) + (g.nn - a.tnb);
+        for (int b0 = 0; b0 < n_all; b0 += 32) {
+          const int bi = b0 + lane;
+          int64_t v = 0;
+          if (bi < n_i) {
+            if ((inst >> bi) & 1) v = (int64_t)1 << g.c_bpos[bi];
+          } else if (bi < n_i + n_m) {
+            if ((mt >> (bi - n_i)) & 1) v = (int64_t)1 << g.c_mpos[g.tm + bi - n_i];
+          } else if (bi < n_all) {
+            if ((nt >> (bi - n_i - n_m)) & 1) v = (int64_t)1 << g.c_npos[a.tnb + bi - n_i - n_m];
+          }
+#pragma unroll
+          for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          cb += v;
+        }
+      }
+      float2* C = Cb + cb;
       const bool row_ok = row < tmv;
       const int64_t crow = offCm[row];
       float am = 0.f;

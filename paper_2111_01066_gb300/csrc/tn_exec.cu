@@ -265,6 +265,7 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.ls_split = __builtin_ctz((unsigned)t.n_split);
   t.ls_nt = g.nn - g.tn;
   t.ls_mt = g.nm - g.tm;
+  t.ls_kc = g.nk - g.tk;
   setup_tma(L, a_bits, n_lin);
   // rings: B' slots first (3, or 4 when small), the rest of the budget to A slots
   const int b_slot = npl * b_plane;
