@@ -127,6 +127,7 @@ struct TcArgs {
   int64_t n_tiles;
   int32_t* err;
   int32_t a_tma;         // 1: A tiles by tensor-map loads (A stored as [k..., m...])
+  int32_t a_box_bytes;   // bytes one A tensor-map load brings: 2^tm rows x 128 bytes
   int32_t na;            // A ring slots (TcPl::A_SLOT bytes each)
   int32_t nbs;           // B' ring slots (one (n tile, k chunk) image each)
   int32_t fa_count;      // arrivals expected on an A slot's "full" barrier
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
           // TF32 4M: the tile is the MMA operand; otherwise converted in place first
           const uint32_t bar = (MODE == TC_TF32 && CM == 4) ? smem_u32(&fullA[slot]) : smem_u32(&rawA[slot]);
-          mbar_arrive_expect_tx(bar, (uint32_t)P::RAW);
+          mbar_arrive_expect_tx(bar, (uint32_t)a.a_box_bytes);
           tma_load_3d(smem_u32(aring + slot * P::A_SLOT), &tma_a, kc * TC_KP, c1, (int)c2, bar);
           if (++slot == na) {
             slot = 0;

@@ -199,12 +199,13 @@ static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
   const GemmArgs& g = L.g;
   TcArgs& t = L.tc;
   t.a_tma = 0;
-  if (g.nk < 4 || g.tm != 7 || (reinterpret_cast<uintptr_t>(g.A) & 15)) return;
+  // tiles of 2^tm rows (tm <= 7; a 128-row MMA tile whose rows past 2^tm the epilogue drops)
+  if (g.nk < 4 || g.tm < 3 || g.tm > 7 || (reinterpret_cast<uintptr_t>(g.A) & 15)) return;
   for (int j = 0; j < g.nk; ++j)
     if (g.a_kpos[j] != j) return;
   int nmw = 0;
   while (nmw < g.nm && g.a_mpos[nmw] == g.nk + nmw) ++nmw;
-  if (nmw < 7) return;
+  if (nmw < g.tm) return;
   const int hi_shift = g.nk + nmw;
   if (a_bits < hi_shift) return;
   const uint64_t dim2 = ((uint64_t)1 << (a_bits - hi_shift)) * (uint64_t)n_lin;
@@ -213,13 +214,14 @@ static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
   if (!enc) return;
   cuuint64_t dims[3] = {(cuuint64_t)2 << g.nk, (cuuint64_t)1 << nmw, (cuuint64_t)dim2};
   cuuint64_t strides[2] = {((cuuint64_t)1 << g.nk) * 8, ((cuuint64_t)1 << hi_shift) * 8};
-  cuuint32_t box[3] = {(cuuint32_t)TC_KP, (cuuint32_t)TC_M, 1};
+  cuuint32_t box[3] = {(cuuint32_t)TC_KP, (cuuint32_t)1u << g.tm, 1};
   cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(&L.tma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(g.A), dims, strides, box,
                          es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return;
   t.a_tma = 1;
+  t.a_box_bytes = (TC_KP * 4) << g.tm;
   t.nmw = nmw;
   t.hi_shift = hi_shift;
   t.c2_inst_mul = n_lin > 1 ? ((int64_t)1 << (a_bits - hi_shift)) : 0;

@@ -356,6 +356,30 @@ def test_contract_pair_fp16x3_scaling(env, shape, mag, cm):
     assert np.array_equal(scaled, (base * np.float32(mag * mag_b)).astype(np.complex64))
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("shape", [(3, 12, 3, 64), (4, 10, 6, 16), (5, 8, 7, 8), (6, 15, 3, 32), (6, 9, 9, 4)])
+def test_contract_pair_short_tiles_by_tma(env, shape, prec):
+    """A stored [k, m] with fewer than 128 rows per instance: tensor-map tiles
+    of 2^m rows (the rest of the 128-row MMA tile is dropped), batched."""
+    tn, torch = env
+    nm, nk, nn, batch = shape
+    rng = np.random.default_rng(sum(shape))
+    wires = list(range(400, 400 + nm + nk + nn))
+    m_w, k_w, n_w = wires[:nm], wires[nm:nm + nk], wires[nm + nk:]
+    a_w, b_w, c_w = k_w + m_w, list(rng.permutation(k_w + n_w)), list(rng.permutation(m_w + n_w))
+    a = (rng.normal(size=(batch, 2 ** len(a_w))) + 1j * rng.normal(size=(batch, 2 ** len(a_w)))) / 2
+    b = (rng.normal(size=(batch, 2 ** len(b_w))) + 1j * rng.normal(size=(batch, 2 ** len(b_w)))) / 2
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    tc = torch.empty((batch, 2 ** len(c_w)), dtype=torch.complex64, device="cuda")
+    tn.contract_pair(dev(a), a_w, dev(b), b_w, tc, c_w, batch=batch, precision=prec)
+    torch.cuda.synchronize()
+    got = tc.cpu().numpy()
+    for i in range(batch):
+        want = pairwise.contract_pair(a[i], a_w, b[i], b_w, c_w)
+        scale = math.sqrt(2 ** nk) * np.sqrt(np.mean(np.abs(a[i]) ** 2) * np.mean(np.abs(b[i]) ** 2))
+        assert np.max(np.abs(got[i] - want)) <= PAIR_TOL[prec] * max(scale, 1e-30) * 8
+
+
 def test_contract_pair_3m_fp32_unsupported(env):
     tn, torch = env
     x = torch.zeros(1 << 10, dtype=torch.complex64, device="cuda")
