@@ -303,8 +303,9 @@ def _event_ms(fn, reps, flush, stream):
 
 def sweep_bench(args) -> int:
     """Kernel sweep: every (m, k, n) in {2^4, 2^6, ..., 2^14}^3 whose operands stay
-    within 2^30 complex elements, in FP32, TF32 and BF16x3 (A stored [k, m] so
-    tensor-core runs fetch it by TMA), or random permutations of rank 20..30
+    within 2^30 complex elements, in FP32, TF32, BF16x3, FP16x3 and BF16x3 3M (A
+    stored [k, m] so tensor-core runs fetch it by TMA), plus every distinct step
+    shape of the C2, C3 and C5 plans (BF16x3), or random permutations of rank 20..30
     (8 seeded permutations per rank plus the full reversal).  One JSON line per
     case goes to --sweep-out; stdout gets a summary line."""
     import numpy as np
@@ -318,28 +319,53 @@ def sweep_bench(args) -> int:
     peaks = load_peaks()
     rows = []
     if args.sweep == "gemm":
+        modes = [("fp32", 4), ("tf32", 4), ("bf16x3", 4), ("fp16x3", 4), ("bf16x3", 3)]
+        kname = {("fp32", 4): "simt", ("tf32", 4): "tc_tf32", ("bf16x3", 4): "tc_bf16x3",
+                 ("fp16x3", 4): "tc_fp16x3", ("bf16x3", 3): "tc_bf16x3_3m"}
+
+        def run_case(m, k, n, b, modes_here, source):
+            mw, kw, nw = list(range(m)), list(range(m, m + k)), list(range(m + k, m + k + n))
+            batch = 1 << b
+            a = torch.randn(batch, 2 ** (m + k), dtype=torch.complex64, device=dev)
+            bb = torch.randn(batch, 2 ** (k + n), dtype=torch.complex64, device=dev)
+            cc = torch.empty(batch, 2 ** (m + n), dtype=torch.complex64, device=dev)
+            for prec, cm in modes_here:
+                fn = lambda: tn.contract_pair(a, kw + mw, bb, kw + nw, cc, mw + nw, batch=batch, precision=prec,
+                                              complex_mult=cm, stream=stream)
+                ms = _event_ms(fn, 2, flush, stream)
+                kern = kname[(prec, cm)]
+                if prec != "fp32" and (m + k + n + b < 20 or m < 4):
+                    kern = "simt"
+                r = step_roofline((m, k, n, b), ms, kern, peaks)
+                rows.append({"case": "gemm", "source": source, "mknb_log2": [m, k, n, b], "precision": prec,
+                             "complex_mult": cm, "ms": ms,
+                             "complex_tflops": 8.0 * 2 ** (m + k + n + b) / ms / 1e9, "bound": r["bound"],
+                             "frac": r["frac"], "kernel": kern})
+            del a, bb, cc
+
         sizes = [4, 6, 8, 10, 12, 14]
         for m in sizes:
             for k in sizes:
                 for n in sizes:
                     if m + k > 30 or k + n > 30 or m + n > 30:
                         continue
-                    mw, kw, nw = list(range(m)), list(range(m, m + k)), list(range(m + k, m + k + n))
-                    a = torch.randn(2 ** (m + k), dtype=torch.complex64, device=dev)
-                    b = torch.randn(2 ** (k + n), dtype=torch.complex64, device=dev)
-                    c = torch.empty(2 ** (m + n), dtype=torch.complex64, device=dev)
-                    for prec in ("fp32", "tf32", "bf16x3"):
-                        fn = lambda: tn.contract_pair(a, kw + mw, b, kw + nw, c, mw + nw, precision=prec,
-                                                      stream=stream)
-                        ms = _event_ms(fn, 2, flush, stream)
-                        kern = {"fp32": "simt", "tf32": "tc_tf32", "bf16x3": "tc_bf16x3"}[prec]
-                        if prec != "fp32" and (m + k + n < 20 or m < 4):
-                            kern = "simt"
-                        r = step_roofline((m, k, n, 0), ms, kern, peaks)
-                        rows.append({"case": "gemm", "mkn_log2": [m, k, n], "precision": prec, "ms": ms,
-                                     "complex_tflops": 8.0 * 2 ** (m + k + n) / ms / 1e9, "bound": r["bound"],
-                                     "frac": r["frac"], "kernel": kern})
-                    del a, b, c
+                    run_case(m, k, n, 0, modes, "grid")
+        # every distinct step shape of the C2, C3 and C5 plans the benchmark uses (batched as in
+        # the plan), in the default BF16x3 4M mode
+        shapes = set()
+        for name in ("c2", "c3", "c5"):
+            cfg = rqcgen.CONFIGS[name]
+            run = WORKLOAD_RUN[name]
+            circ, om, _ = rqcgen.config_circuit(name)
+            pl = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
+                         min_log2_slices=cfg.get("log2_slices", 0), log2_batch_slices=run["log2_batch"],
+                         trials=run.get("trials", 64), max_arena_bytes=int(run.get("arena_gib", 96)) << 30,
+                         precision="bf16x3")
+            shapes |= {s for s in pl.step_shapes() if sum(s) >= 20 and s[0] >= 4}
+        for (m, k, n, b) in sorted(shapes):
+            if 2 ** (m + k + b) > 2 ** 31 or 2 ** (m + n + b) > 2 ** 31:
+                continue
+            run_case(m, k, n, b, [("bf16x3", 4)], "plans")
     else:
         rng = np.random.default_rng(4)
         for rank in (20, 22, 24, 26, 28, 30):
@@ -360,11 +386,17 @@ def sweep_bench(args) -> int:
     summ = {"metric": f"{args.sweep}_sweep", "cases": len(rows), "frac_median": statistics.median(fr),
             "frac_min": min(fr), "frac_max": max(fr)}
     if args.sweep == "gemm":
-        for prec in ("fp32", "tf32", "bf16x3"):
-            big = [r for r in rows if r["precision"] == prec and sum(r["mkn_log2"]) >= 30]
+        for prec, cm in (("fp32", 4), ("tf32", 4), ("bf16x3", 4), ("fp16x3", 4), ("bf16x3", 3)):
+            tag = prec if cm == 4 else prec + "_3m"
+            big = [r for r in rows if r["precision"] == prec and r["complex_mult"] == cm and r["source"] == "grid"
+                   and sum(r["mknb_log2"]) >= 30]
             if big:
-                summ[f"{prec}_median_frac_large"] = statistics.median(r["frac"] for r in big)
-                summ[f"{prec}_max_tflops"] = max(r["complex_tflops"] for r in big)
+                summ[f"{tag}_median_frac_large"] = statistics.median(r["frac"] for r in big)
+                summ[f"{tag}_max_tflops"] = max(r["complex_tflops"] for r in big)
+        pl_rows = [r for r in rows if r["source"] == "plans"]
+        if pl_rows:
+            summ["plan_shapes"] = len(pl_rows)
+            summ["plan_shapes_median_frac"] = statistics.median(r["frac"] for r in pl_rows)
     print(json.dumps(summ))
     return 0
 

@@ -166,42 +166,73 @@ __global__ void k_permute_gather(const float2* __restrict__ in, float2* __restri
 }
 
 // Tiled permutation (SI Eq. (2) as a standalone pass): a tile holds every
-// combination of the input's 5 lowest bits and of the input bits that feed the
-// output's 5 lowest positions (<= 10 bits, <= 1024 complex).  Threads read the
-// tile in input order (contiguous runs) into shared memory and write it back in
-// output order (contiguous runs); the remaining bits select the tile.
+// combination of nt <= 10 tile bits: the input's lowest bits and the input bits
+// that feed the output's lowest positions (so reads and writes both run along
+// memory).  Threads read the tile in input order into shared memory and write
+// it back in output order; the remaining nr bits select the tile.  Each
+// thread's in-tile offsets are fixed, so they are computed once; a tile's base
+// is a one-bit-per-lane warp sum.
 __global__ void __launch_bounds__(256) k_permute_tiled(const float2* __restrict__ in, float2* __restrict__ out,
                                                        int rank, const PermArgs pa, int64_t n_tiles_per_inst,
                                                        int64_t n_inst) {
   __shared__ float2 tile[1024];
   const int tsz = 1 << pa.nt;
-  for (int64_t t = blockIdx.x; t < n_tiles_per_inst * n_inst; t += gridDim.x) {
-    const int64_t inst = t / n_tiles_per_inst;
-    const int64_t r = t % n_tiles_per_inst;
-    int64_t ib = inst << rank, ob = inst << rank;
-    for (int q = 0; q < pa.nr; ++q)
-      if ((r >> q) & 1) {
-        ib += (int64_t)1 << pa.r_in[q];
-        ob += (int64_t)1 << pa.r_out[q];
-      }
-    for (int e = threadIdx.x; e < tsz; e += blockDim.x) {   // e: tile bits in input order
-      int64_t off = 0;
+  const int lane = threadIdx.x & 31;
+  int64_t ioff[4], ooff[4];
+  int sidx[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int e = threadIdx.x + 256 * j;   // element e in input order, element e in output order
+    ioff[j] = -1;
+    ooff[j] = 0;
+    sidx[j] = 0;
+    if (e < tsz) {
+      int64_t io = 0, oo = 0;
+      int si = 0;
       for (int q = 0; q < pa.nt; ++q)
-        if ((e >> q) & 1) off += (int64_t)1 << pa.t_in[q];
-      tile[e] = __ldg(in + ib + off);
+        if ((e >> q) & 1) {
+          io += (int64_t)1 << pa.t_in[q];
+          const int i = pa.t_out_order[q];
+          si |= 1 << i;
+          oo += (int64_t)1 << pa.t_out[i];
+        }
+      ioff[j] = io;
+      ooff[j] = oo;
+      sidx[j] = si;
+    }
+  }
+  const int64_t total = n_tiles_per_inst * n_inst;
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const int64_t inst = t >> pa.nr;
+    const int64_t r = t & (n_tiles_per_inst - 1);
+    int64_t bi = 0, bo = 0;
+    for (int q0 = 0; q0 < pa.nr; q0 += 32) {
+      const int q = q0 + lane;
+      int64_t vi = 0, vo = 0;
+      if (q < pa.nr && ((r >> q) & 1)) {
+        vi = (int64_t)1 << pa.r_in[q];
+        vo = (int64_t)1 << pa.r_out[q];
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+        vo += __shfl_xor_sync(0xffffffffu, vo, o);
+      }
+      bi += vi;
+      bo += vo;
+    }
+    const int64_t ib = (inst << rank) + bi, ob = (inst << rank) + bo;
+    // tile slot of element e: e ^ (bits 5-9 of e), so that runs along either
+    // order spread over the shared-memory banks
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = threadIdx.x + 256 * j;
+      if (ioff[j] >= 0) tile[e ^ ((e >> 5) & 31)] = __ldg(in + ib + ioff[j]);
     }
     __syncthreads();
-    for (int f = threadIdx.x; f < tsz; f += blockDim.x) {   // f: tile bits in output order
-      int e = 0;
-      int64_t off = 0;
-      for (int q = 0; q < pa.nt; ++q)
-        if ((f >> q) & 1) {
-          const int i = pa.t_out_order[q];
-          e |= 1 << i;
-          off += (int64_t)1 << pa.t_out[i];
-        }
-      out[ob + off] = tile[e];
-    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (ioff[j] >= 0) out[ob + ooff[j]] = tile[sidx[j] ^ ((sidx[j] >> 5) & 31)];
     __syncthreads();
   }
 }

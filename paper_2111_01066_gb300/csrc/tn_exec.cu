@@ -1008,6 +1008,25 @@ extern "C" tn_status tn_permute(const float* in, float* out, int32_t rank, const
     std::vector<char> in_tile(rank, 0);
     for (int i = 0; i < 5; ++i) in_tile[i] = 1;
     for (int p = 0; p < 5; ++p) in_tile[perm[p]] = 1;
+    // widen to 10 tile bits: alternately the next input bit and the source of
+    // the next output bit (longer contiguous runs on both sides)
+    {
+      int nt = 0;
+      for (int i = 0; i < rank; ++i) nt += in_tile[i];
+      int ni = 5, no = 5;
+      while (nt < 10 && (ni < rank || no < rank)) {
+        if (ni < rank && !in_tile[ni] && nt < 10) {
+          in_tile[ni] = 1;
+          ++nt;
+        }
+        ++ni;
+        if (no < rank && !in_tile[perm[no]] && nt < 10) {
+          in_tile[perm[no]] = 1;
+          ++nt;
+        }
+        ++no;
+      }
+    }
     pa.nt = 0;
     pa.nr = 0;
     for (int i = 0; i < rank; ++i) {
@@ -1026,7 +1045,7 @@ extern "C" tn_status tn_permute(const float* in, float* out, int32_t rank, const
     std::sort(ord.begin(), ord.end(), [&](int x, int y) { return pa.t_out[x] < pa.t_out[y]; });
     for (int q = 0; q < pa.nt; ++q) pa.t_out_order[q] = ord[q];
     const int64_t tiles = (int64_t)1 << pa.nr;
-    const int blocks = (int)std::min<int64_t>(tiles * batch, 152 * 16);
+    const int blocks = (int)std::min<int64_t>(tiles * batch, (int64_t)sm_count() * 8);
     k_permute_tiled<<<blocks, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float2*>(in),
                                                               reinterpret_cast<float2*>(out), rank, pa, tiles,
                                                               batch);

@@ -388,7 +388,7 @@ def test_contract_pair_3m_fp32_unsupported(env):
     assert e.value.status == tn.TN_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("rank", [1, 2, 5, 9, 14, 20])
+@pytest.mark.parametrize("rank", [1, 2, 5, 9, 10, 11, 14, 20, 24])
 def test_permute_bit_exact(env, rank):
     tn, torch = env
     rng = np.random.default_rng(rank)
