@@ -705,85 +705,84 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   } else if (warp >= TC_MMA_WARP + 1 && a.a_tma) {
     // ---------------------------------------------------------------- converters (TMA)
     // The fp32 tile (128 rows x 128 bytes, 128-byte swizzle) is read into
-    // registers by all converter threads, then -- after a barrier -- rewritten
-    // in place as the operand planes: 4M BF16X3 hi and lo (128 rows x 64 bytes
-    // each); 3M the planes of TcPl<MODE, 3>, one item (row, 8 complex k) per thread.
-    if constexpr (CM == 3) {
+    // registers, then -- after a barrier of the group -- rewritten in place as
+    // the operand planes: 4M BF16X3/FP16X3 hi and lo (128 rows x 64 bytes
+    // each); 3M the planes of TcPl<MODE, 3> by items (row, 8 complex k).  The 8
+    // warps form two groups of 4 that take alternate k chunks, so two chunks
+    // are converted at once; rows past the tile's 2^tm are left alone.
+    if constexpr (CM == 3 || MODE != TC_TF32) {
       const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
-      const int row = lt % TC_M, h = lt / TC_M;
+      constexpr int GT = TC_LOAD_THREADS / 2;                     // threads per group
+      const int grp = lt / GT, glt = lt % GT;
+      const int tmv = 1 << g.tm;
+      // 4M: 512 items (row, 16-byte output chunk c); 3M: 256 items (row, half h)
+      constexpr int NIT = CM == 3 ? 2 * TC_M / GT : TC_M * (TC_KP * T::ESZ / 16) / GT;
+      int roff[NIT][4], woff[NIT], irow[NIT], isub[NIT];
+#pragma unroll
+      for (int j = 0; j < NIT; ++j) {
+        const int q = glt + j * GT;
+        irow[j] = q % TC_M;
+        isub[j] = q / TC_M;
+        if constexpr (CM == 3) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) roff[j][r] = tc_elem_off(irow[j], 16 * isub[j] + 4 * r, 4);
+          woff[j] = 0;
+        } else {
+          roff[j][0] = tc_elem_off(irow[j], 8 * isub[j], 4);
+          roff[j][1] = tc_elem_off(irow[j], 8 * isub[j] + 4, 4);
+          roff[j][2] = roff[j][3] = 0;
+          woff[j] = tc_elem_off(irow[j], 8 * isub[j], T::ESZ);
+        }
+      }
       int slot = 0;
       uint32_t ph = 0;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        bool stop = false;
-        for (int kc = 0; kc < kc_per; ++kc) {
-          const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
-          uint8_t* sa = aring + slot * P::A_SLOT;
-          float2 x[8];
+      int64_t chunk = 0;
+      bool stop = false;
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles && !stop; tile += gridDim.x) {
+        for (int kc = 0; kc < kc_per; ++kc, ++chunk) {
+          if ((int)(chunk & 1) == grp) {
+            const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
+            uint8_t* sa = aring + slot * P::A_SLOT;
+            float4 x[NIT][CM == 3 ? 4 : 2];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {   // raw chunk 4h + j: complex k 8h + 2j, 8h + 2j + 1
-            const float4 r = *reinterpret_cast<const float4*>(sa + tc_elem_off(row, 16 * h + 4 * j, 4));
-            x[2 * j] = make_float2(r.x, r.y);
-            x[2 * j + 1] = make_float2(r.z, r.w);
+            for (int j = 0; j < NIT; ++j)
+              if (irow[j] < tmv) {
+#pragma unroll
+                for (int r = 0; r < (CM == 3 ? 4 : 2); ++r)
+                  x[j][r] = *reinterpret_cast<const float4*>(sa + roff[j][r]);
+              }
+            // every thread of the group has read the tile; all agree whether to go on
+            stop = named_barrier_or(1 + grp, GT, !got || *abort_flag);
+            if (stop) break;
+#pragma unroll
+            for (int j = 0; j < NIT; ++j) {
+              if (irow[j] >= tmv) continue;
+              if constexpr (CM == 3) {
+                float2 v[8];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {   // raw chunk 4h + r: complex k 8h + 2r, 8h + 2r + 1
+                  v[2 * r] = make_float2(x[j][r].x, x[j][r].y);
+                  v[2 * r + 1] = make_float2(x[j][r].z, x[j][r].w);
+                }
+                put3m<MODE>(sa, irow[j], isub[j], v, sc_a);
+              } else {
+                const float xs[8] = {x[j][0].x, x[j][0].y, x[j][0].z, x[j][0].w,
+                                     x[j][1].x, x[j][1].y, x[j][1].z, x[j][1].w};
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split_pair<MODE>(xs[2 * i] * sc_a, xs[2 * i + 1] * sc_a, hi[i], lo[i]);
+                *reinterpret_cast<uint4*>(sa + woff[j]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4*>(sa + a_plane + woff[j]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+              }
+            }
+            fence_proxy_async();
+            mbar_arrive(smem_u32(&fullA[slot]));
           }
-          stop = named_barrier_or(1, TC_LOAD_THREADS, !got || *abort_flag);
-          if (stop) break;
-          put3m<MODE>(sa, row, h, x, sc_a);
-          fence_proxy_async();
-          mbar_arrive(smem_u32(&fullA[slot]));
           if (++slot == na) {
             slot = 0;
             ph ^= 1;
           }
         }
-        if (stop) break;
-      }
-    } else if constexpr (MODE != TC_TF32) {
-      const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
-      constexpr int NCH = TC_M * (TC_KP * T::ESZ / 16) / TC_LOAD_THREADS;
-      // this thread's raw-tile and plane offsets, the same in every slot
-      int roff[NCH][2], woff[NCH];
-#pragma unroll
-      for (int j = 0; j < NCH; ++j) {
-        const int q = lt + j * TC_LOAD_THREADS;
-        const int row = q % TC_M, c = q / TC_M;     // 16-byte output chunk: 4 complex
-        roff[j][0] = tc_elem_off(row, 8 * c, 4);
-        roff[j][1] = tc_elem_off(row, 8 * c + 4, 4);
-        woff[j] = tc_elem_off(row, 8 * c, T::ESZ);
-      }
-      int slot = 0;
-      uint32_t ph = 0;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
-        bool stop = false;
-        for (int kc = 0; kc < kc_per; ++kc) {
-          const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
-          uint8_t* sa = aring + slot * P::A_SLOT;
-          float4 x[NCH][2];
-#pragma unroll
-          for (int j = 0; j < NCH; ++j) {
-            x[j][0] = *reinterpret_cast<const float4*>(sa + roff[j][0]);
-            x[j][1] = *reinterpret_cast<const float4*>(sa + roff[j][1]);
-          }
-          // every converter has read the tile; all agree whether to go on
-          stop = named_barrier_or(1, TC_LOAD_THREADS, !got || *abort_flag);
-          if (stop) break;
-#pragma unroll
-          for (int j = 0; j < NCH; ++j) {
-            const float xs[8] = {x[j][0].x, x[j][0].y, x[j][0].z, x[j][0].w,
-                                 x[j][1].x, x[j][1].y, x[j][1].z, x[j][1].w};
-            uint32_t hi[4], lo[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) split_pair<MODE>(xs[2 * i] * sc_a, xs[2 * i + 1] * sc_a, hi[i], lo[i]);
-            *reinterpret_cast<uint4*>(sa + woff[j]) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(sa + a_plane + woff[j]) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-          }
-          fence_proxy_async();
-          mbar_arrive(smem_u32(&fullA[slot]));
-          if (++slot == na) {
-            slot = 0;
-            ph ^= 1;
-          }
-        }
-        if (stop) break;
       }
     }
   } else if (warp >= TC_MMA_WARP + 1) {
