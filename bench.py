@@ -142,29 +142,37 @@ t0 = time.time()
 merges, extra = net.plan([], max_log2={maxlog!r}, method="bisect", trials={trials!r})
 plan_s = time.time() - t0
 budget = {budget!r}
-done, t_run = 0, 0.0
-while t_run < budget and done < (1 << len(extra)):
-    values = {{leg: (done >> j) & 1 for j, leg in enumerate(extra)}}
-    t1 = time.time()
-    net._run(merges, values)
-    t_run += time.time() - t1
-    done += 1
-print(json.dumps({{"sub_networks": 1 << len(extra), "timed": done, "seconds": t_run, "plan_s": plan_s}}))
+steps = []
+done = 0
+for s in range({n_steps!r}):
+    # one step: at least one sub-network, then more until the step's budget is spent
+    cnt, t_run = 0, 0.0
+    while (cnt == 0 or t_run < budget):
+        values = {{leg: ((done % (1 << len(extra))) >> j) & 1 for j, leg in enumerate(extra)}}
+        t1 = time.time()
+        net._run(merges, values)
+        t_run += time.time() - t1
+        done += 1
+        cnt += 1
+    steps.append([t_run, cnt])
+print(json.dumps({{"sub_networks": 1 << len(extra), "steps": steps, "plan_s": plan_s}}))
 """
 
 
-def oracle_timing(name: str, budget_s: float) -> dict:
-    """Time the FP64 oracle on a bounded sample: the oracle contracts the whole
-    batch as 2^E sub-networks of its own (its sub-slicing); `timed` of them are
-    run within the budget and the full-batch time is extrapolated."""
-    code = ORACLE_SNIPPET.format(root=ROOT, name=name, maxlog=26, trials=4, budget=budget_s)
+def oracle_timing(name: str, budget_s: float, n_steps: int = 1) -> dict:
+    """Time the FP64 oracle on bounded samples: the oracle contracts the whole
+    batch as 2^E sub-networks of its own (its sub-slicing); each of n_steps
+    samples runs at least one of them and more within budget_s, and its
+    full-batch time is extrapolated from the sample."""
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, maxlog=26, trials=4, budget=budget_s, n_steps=n_steps)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=3600)
     if r.returncode != 0:
         return {"error": r.stderr.strip()[-400:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    full = d["seconds"] / d["timed"] * d["sub_networks"]
-    return {"full_batch_seconds": full, "timed_sub_networks": d["timed"], "sub_networks": d["sub_networks"],
-            "seconds": d["seconds"]}
+    per_step = [sec / cnt * d["sub_networks"] for sec, cnt in d["steps"]]
+    return {"full_batch_seconds": per_step[-1], "step_full_batch_seconds": per_step,
+            "timed_sub_networks": sum(cnt for _, cnt in d["steps"]), "sub_networks": d["sub_networks"],
+            "seconds": sum(sec for sec, _ in d["steps"])}
 
 
 def cores_used() -> int:
@@ -439,21 +447,27 @@ def main() -> int:
     if args.impl == "reference":
         if rank != 0:
             return 0
-        t = oracle_timing(name, args.cpu_budget)
+        # W warm-up + K timed bounded samples, each at least one oracle sub-network,
+        # the whole run sized to a few minutes
+        n_all = args.warmup + args.steps
+        t = oracle_timing(name, max(1.0, min(args.cpu_budget, 180.0 / max(1, n_all))), n_all)
         total_slices = 1 << cfg["log2_slices"]
         steps = []
         if "error" not in t:
-            steps = [t["full_batch_seconds"]]
-        value = total_slices / t["full_batch_seconds"] if steps else None
+            steps = t["step_full_batch_seconds"][args.warmup:]
+        mean_s = statistics.mean(steps) if steps else None
+        value = total_slices / mean_s if steps else None
         line = {"impl": "reference", "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": 0,
-                "steps": 1, "warmup": 0, "ms_per_step": (steps[0] * 1e3 if steps else None),
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": (mean_s * 1e3 if steps else None),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": f"{name}: {circ.n_qubits}q {cfg['rows']}x{cfg['cols']} "
-                                                            f"d={cfg['cycles']}, 2^{cfg['log2_slices']} slices, "
-                                                            f"{cfg['k_open']} open qubits"},
+                "data": "synthetic",
+                "config": {"workload": f"{name}: {circ.n_qubits}-qubit {cfg['rows']}x{cfg['cols']} grid, "
+                                       f"{cfg['cycles']} cycles, 2^{cfg['log2_slices']} slices (<=2^"
+                                       f"{cfg['log2_bound']} per slice), {cfg['k_open']} open qubits"},
                 "cpu_baseline": {"value": value, "unit": "slices/s", "cores": cores_used(), "kind": "oracle",
-                                 "sample": f"{t.get('timed_sub_networks')} of {t.get('sub_networks')} oracle "
-                                           f"sub-networks of the full batch, extrapolated"},
+                                 "sample": f"{args.warmup} + {args.steps} samples, {t.get('timed_sub_networks')} of "
+                                           f"{t.get('sub_networks')} oracle sub-networks of the full {total_slices}-slice "
+                                           f"batch in all ({t.get('seconds', 0):.1f} s), each extrapolated"},
                 "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         if "error" in t:
             line["unavailable"] = "oracle failed: " + t["error"]
