@@ -68,17 +68,6 @@ __device__ __forceinline__ void amax_update(float* amax_c, float m) {
 }
 __device__ __forceinline__ float cabs_max(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
 
-__device__ __forceinline__ uint32_t pext_u32(uint32_t x, uint32_t mask) {
-  uint32_t r = 0, k = 0;
-  while (mask) {
-    const uint32_t low = mask & (0u - mask);
-    if (x & low) r |= 1u << k;
-    ++k;
-    mask ^= low;
-  }
-  return r;
-}
-
 // sum over bits i >= from of bit_{i-from}(x) << pos[i]
 __device__ __forceinline__ int64_t deposit_hi(uint64_t x, const int8_t* pos, int from, int to) {
   int64_t r = 0;

@@ -822,7 +822,6 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   auto layout = [&](int b, std::vector<NodeInfo>& info, std::vector<StepDesc>& steps,
                     int64_t& arena) -> bool {
     info.assign(L + nm, NodeInfo{});
-    const uint32_t lowmask = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
     for (int i = 0; i < L; ++i) {
       for (int w : S.leaves[i].wires)
         if (!S.fixed[w] && !SL.test(pw_of[w])) info[i].wires.push_back(pw_of[w]);
@@ -1060,7 +1059,6 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       steps.push_back(d);
     }
     arena = peak;
-    (void)lowmask;
     return peak * 8 <= cap_bytes;
   };
 
