@@ -421,7 +421,7 @@ __device__ __forceinline__ void put3m(uint8_t* sa, int row, int h, const float2 
 // Threads run in memory order of the image, so the writes are contiguous.
 // Padding (k or n beyond the operand) is zero.
 template <int MODE>
-__global__ void k_tc_prep_b(const TcArgs a) {
+__global__ void __launch_bounds__(256) k_tc_prep_b(const TcArgs a) {
   using T = TcT<MODE>;
   constexpr int KPC = 16 / (2 * T::ESZ);        // complex k per 16-byte chunk (2 or 4)
   constexpr int CPR = TC_KP * T::ESZ / 16;      // chunks per row (8 or 4)
@@ -430,48 +430,53 @@ __global__ void k_tc_prep_b(const TcArgs a) {
   const int plane = tc_plane_bytes(ncp, T::ESZ);
   const int64_t block_bytes = (int64_t)T::NPL * plane;
   const int per_block = ncp * CPR;              // chunks per plane
-  const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
   const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
   const float sc = operand_scale<MODE>(g.amax_b);
-  const int lg_block = 31 - __clz(per_block);   // per_block is a power of two
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx & (per_block - 1));
-    const int64_t blk = idx >> lg_block;
-    // q in image order: row within the 8-row group fastest, then chunk, then group
-    const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
-    const int row = rg * 8 + rlo;
-    const int t = row & 1, nl = row >> 1;
+  // offsets in B of the k inside a chunk and of the n inside a tile (-1: padding)
+  __shared__ int64_t koff[TC_TK];
+  __shared__ int64_t noff[128];
+  for (int i = threadIdx.x; i < TC_TK; i += blockDim.x) koff[i] = i < tkv ? deposit_hi((uint64_t)i, g.b_kpos, 0, g.tk) : -1;
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) noff[i] = i < tnv ? deposit_hi((uint64_t)i, g.b_npos, 0, a.tnb) : -1;
+  __syncthreads();
+  const int64_t n_blocks = (int64_t)g.n_inst << (a.ls_nt + a.ls_kc);
+  // one CTA per (instance, n tile, k chunk) block at a time; threads walk the
+  // block's 16-byte chunks in memory order of the image
+  for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     const int kc = (int)(blk & (a.n_kc - 1));
     const int nt = (int)((blk >> a.ls_kc) & (a.n_nt - 1));
     const int inst = (int)(blk >> (a.ls_kc + a.ls_nt));
-    float vals[2 * KPC];
-    const bool n_ok = nl < tnv;
-    int64_t base = 0;
-    if (n_ok)
-      base = inst_offset(inst, g.b_istride, g.b_bpos, g.nb) + deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk) +
-             deposit_hi((uint64_t)nl, g.b_npos, 0, a.tnb) + deposit_hi((uint64_t)nt, g.b_npos, a.tnb, g.nn);
+    const int64_t base = inst_offset(inst, g.b_istride, g.b_bpos, g.nb) + deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk) +
+                         deposit_hi((uint64_t)nt, g.b_npos, a.tnb, g.nn);
+    uint8_t* dblk = const_cast<uint8_t*>(a.bimg) + blk * block_bytes;
+    for (int q = threadIdx.x; q < per_block; q += blockDim.x) {
+      // q in image order: row within the 8-row group fastest, then chunk, then group
+      const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
+      const int row = rg * 8 + rlo;
+      const int t = row & 1, nl = row >> 1;
+      const int64_t no = noff[nl];
+      float vals[2 * KPC];
 #pragma unroll
-    for (int i = 0; i < KPC; ++i) {
-      const int kl = c * KPC + i;
-      float2 b = make_float2(0.f, 0.f);
-      if (n_ok && kl < tkv) b = g.B[base + deposit_hi((uint64_t)kl, g.b_kpos, 0, g.tk)];
-      // row (n, t), columns (k, u): t = 0 -> (Re, -Im), t = 1 -> (Im, Re)
-      vals[2 * i] = t ? b.y : b.x;
-      vals[2 * i + 1] = t ? b.x : -b.y;
-    }
-    uint8_t* dst = const_cast<uint8_t*>(a.bimg) + blk * block_bytes + tc_elem_off(row, c * KPC * 2, T::ESZ);
-    if constexpr (MODE == TC_TF32) {
-      uint32_t w[4];
+      for (int i = 0; i < KPC; ++i) {
+        const int64_t ko = koff[c * KPC + i];
+        float2 b = make_float2(0.f, 0.f);
+        if (no >= 0 && ko >= 0) b = g.B[base + no + ko];
+        // row (n, t), columns (k, u): t = 0 -> (Re, -Im), t = 1 -> (Im, Re)
+        vals[2 * i] = t ? b.y : b.x;
+        vals[2 * i + 1] = t ? b.x : -b.y;
+      }
+      uint8_t* dst = dblk + tc_elem_off(row, c * KPC * 2, T::ESZ);
+      if constexpr (MODE == TC_TF32) {
+        uint32_t w[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"(vals[i]));
-      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-    } else {
-      uint32_t hi[4], lo[4];
+        for (int i = 0; i < 4; ++i) w[i] = to_tf32(vals[i]);
+        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) split_pair<MODE>(vals[2 * i] * sc, vals[2 * i + 1] * sc, hi[i], lo[i]);
-      *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(dst + plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        for (int i = 0; i < 4; ++i) split_pair<MODE>(vals[2 * i] * sc, vals[2 * i + 1] * sc, hi[i], lo[i]);
+        *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(dst + plane) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
     }
   }
 }

@@ -305,8 +305,11 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
 
 template <int MODE, int CM>
 static void launch_tc(const TcArgs& t, const StepLaunch& L, int pblocks, int grid, cudaStream_t s) {
-  if constexpr (CM == 4)
-    k_tc_prep_b<MODE><<<pblocks, 256, 0, s>>>(t);
+  if constexpr (CM == 4) {
+    // one CTA per B' image block at a time
+    const int64_t n_blocks = (int64_t)t.g.n_inst * t.n_nt * t.n_kc;
+    k_tc_prep_b<MODE><<<(int)std::max<int64_t>(1, std::min<int64_t>(n_blocks, (int64_t)sm_count() * 16)), 256, 0, s>>>(t);
+  }
   else
     k_tc_prep_b3<MODE><<<pblocks, 256, 0, s>>>(t);
   static bool attr = false;
