@@ -142,3 +142,39 @@ def test_mem_weight_option(tn):
     with pytest.raises(tn.TnError) as e:
         tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, mem_weight=1e12)
     assert e.value.status == tn.TN_ERR_ARG
+
+
+@pytest.mark.parametrize("name", ["c2", "c3"])
+def test_layout_pass_guarantees(tn, name):
+    """The planner stores every streamed operand A as [its contracted wires,
+    its rows (free wires, then A-only batch bits)], shared batch bits on top,
+    so tiles of A are plain row-major blocks; every operand's positions form a
+    permutation; results that depend on no slice exist (reused prologue steps)
+    and the root depends on the slices when the plan is sliced."""
+    cfg = rqcgen.CONFIGS[name]
+    circ, om, _ = rqcgen.config_circuit(name)
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
+                   min_log2_slices=cfg["log2_slices"], trials=16, precision="bf16x3")
+    shapes = plan.step_shapes()
+    flags = []
+    for i, (m, k, n, b) in enumerate(shapes):
+        L = plan.step_layout(i)
+        assert L["a_k"] == list(range(k)), "contracted wires first in A"
+        assert L["a_m"] == list(range(k, k + m)), "A's rows contiguous after them"
+        assert all(p >= k + m for p in L["a_b"]), "shared batch bits on top of A"
+        assert sorted(L["a_k"] + L["a_m"] + L["a_b"]) == list(range(k + m + b))
+        assert sorted(L["b_k"] + L["b_n"] + L["b_b"]) == list(range(k + n + b))
+        assert sorted(L["c_m"] + L["c_n"] + L["c_b"]) == list(range(m + n + b))
+        flags.append(L["dep_flags"])
+    assert set(flags) <= {0, 1, 2, 3}
+    assert 0 in flags or 2 in flags
+    if plan.info()["log2_slices"] > 0:
+        assert flags[-1] & 1
+
+
+def test_chunk_launches_needs_device_state(tn):
+    circ, om, _ = rqcgen.config_circuit("c1")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, trials=2)
+    with pytest.raises(tn.TnError) as e:
+        plan.chunk_launches()
+    assert e.value.status == tn.TN_ERR_ARG
