@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(256) k_tc_prep_b(const TcArgs a) {
 // one plane row per complex column n; one thread per 16-byte chunk in memory
 // order of the image.  Padding (k or n beyond the operand) is zero.
 template <int MODE>
-__global__ void k_tc_prep_b3(const TcArgs a) {
+__global__ void __launch_bounds__(256) k_tc_prep_b3(const TcArgs a) {
   using P = TcPl<MODE, 3>;
   constexpr int ESZ = P::ESZ;
   constexpr int EPC = 16 / ESZ;                 // elements per 16-byte chunk (4 or 8)
@@ -495,63 +495,64 @@ __global__ void k_tc_prep_b3(const TcArgs a) {
   const int plane = tc_plane_bytes(rows, ESZ);
   const int64_t block_bytes = (int64_t)P::PLANES * plane;
   const int per_block = P::PLANES * rows * CPR;
-  const int64_t total = (int64_t)g.n_inst * a.n_nt * a.n_kc * per_block;
+  const int per_plane = rows * CPR;
   const int tkv = 1 << g.tk, tnv = 1 << a.tnb;
   const float sc = operand_scale<MODE>(g.amax_b);
-  const int per_plane = rows * CPR;              // a power of two
-  const int lg_plane = 31 - __clz(per_plane);
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pb = idx >> lg_plane;            // block * PLANES + plane
-    const int64_t blk = pb / P::PLANES;
-    const int pl = (int)(pb - blk * P::PLANES), q = (int)(idx & (per_plane - 1));
-    const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
-    const int n = rg * 8 + rlo;
-    const int half = c / (CPR / 2), k0 = (c % (CPR / 2)) * EPC;   // k0.. within the half's 16 k
+  __shared__ int64_t koff[TC_TK];
+  __shared__ int64_t noff[128];
+  for (int i = threadIdx.x; i < TC_TK; i += blockDim.x) koff[i] = i < tkv ? deposit_hi((uint64_t)i, g.b_kpos, 0, g.tk) : -1;
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) noff[i] = i < tnv ? deposit_hi((uint64_t)i, g.b_npos, 0, a.tnb) : -1;
+  __syncthreads();
+  const int64_t n_blocks = (int64_t)g.n_inst << (a.ls_nt + a.ls_kc);
+  for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     const int kc = (int)(blk & (a.n_kc - 1));
     const int nt = (int)((blk >> a.ls_kc) & (a.n_nt - 1));
     const int inst = (int)(blk >> (a.ls_kc + a.ls_nt));
-    float2 b[8];
-    const bool n_ok = n < tnv;
-    int64_t base = 0;
-    if (n_ok)
-      base = inst_offset(inst, g.b_istride, g.b_bpos, g.nb) + deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk) +
-             deposit_hi((uint64_t)n, g.b_npos, 0, a.tnb) + deposit_hi((uint64_t)nt, g.b_npos, a.tnb, g.nn);
+    const int64_t base = inst_offset(inst, g.b_istride, g.b_bpos, g.nb) + deposit_hi((uint64_t)kc, g.b_kpos, g.tk, g.nk) +
+                         deposit_hi((uint64_t)nt, g.b_npos, a.tnb, g.nn);
+    uint8_t* dblk = const_cast<uint8_t*>(a.bimg) + blk * block_bytes;
+    for (int pq = threadIdx.x; pq < per_block; pq += blockDim.x) {
+      const int pl = pq / per_plane, q = pq % per_plane;
+      const int rlo = q & 7, c = (q >> 3) % CPR, rg = (q >> 3) / CPR;
+      const int n = rg * 8 + rlo;
+      const int half = c / (CPR / 2), k0 = (c % (CPR / 2)) * EPC;   // k0.. within the half's 16 k
+      const int64_t no = noff[n];   // n < tn_c <= 128
+      float2 b[8];
 #pragma unroll
-    for (int i = 0; i < EPC; ++i) {
-      const int kl = k0 + i;
-      b[i] = (n_ok && kl < tkv) ? g.B[base + deposit_hi((uint64_t)kl, g.b_kpos, 0, g.tk)] : make_float2(0.f, 0.f);
-    }
-    uint8_t* dst = const_cast<uint8_t*>(a.bimg) + blk * block_bytes + (int64_t)pl * plane +
-                   tc_elem_off(n, c * EPC, ESZ);
-    if constexpr (MODE == TC_TF32) {
-      // plane 0: [Br | Bi]; plane 1: [Bs | 0]
-      uint32_t w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float v = pl == 0 ? (half == 0 ? b[i].x : b[i].y) : (half == 0 ? b[i].x + b[i].y : 0.f);
-        w[i] = to_tf32(v);
+      for (int i = 0; i < EPC; ++i) {
+        const int64_t ko = koff[k0 + i];
+        b[i] = (no >= 0 && ko >= 0) ? g.B[base + no + ko] : make_float2(0.f, 0.f);
       }
-      st16(dst, w[0], w[1], w[2], w[3]);
-    } else {
-      // plane 0: [Br_hi | Bi_hi]; plane 1: [Br_lo | Bi_lo]; plane 2: [Bs_hi | Bs_lo]
-      uint32_t w[4];
+      uint8_t* dst = dblk + (int64_t)pl * plane + tc_elem_off(n, c * EPC, ESZ);
+      if constexpr (MODE == TC_TF32) {
+        // plane 0: [Br | Bi]; plane 1: [Bs | 0]
+        uint32_t w[4];
 #pragma unroll
-      for (int q2 = 0; q2 < 4; ++q2) {
-        const float2 u = b[2 * q2], v = b[2 * q2 + 1];
-        float x0, x1;
-        if (pl < 2) {
-          x0 = half == 0 ? u.x : u.y;
-          x1 = half == 0 ? v.x : v.y;
-        } else {
-          x0 = u.x + u.y;
-          x1 = v.x + v.y;
+        for (int i = 0; i < 4; ++i) {
+          const float v = pl == 0 ? (half == 0 ? b[i].x : b[i].y) : (half == 0 ? b[i].x + b[i].y : 0.f);
+          w[i] = to_tf32(v);
         }
-        uint32_t hi, lo;
-        split_pair<MODE>(x0 * sc, x1 * sc, hi, lo);
-        w[q2] = (pl == 0 || (pl == 2 && half == 0)) ? hi : lo;
+        st16(dst, w[0], w[1], w[2], w[3]);
+      } else {
+        // plane 0: [Br_hi | Bi_hi]; plane 1: [Br_lo | Bi_lo]; plane 2: [Bs_hi | Bs_lo]
+        uint32_t w[4];
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          const float2 u = b[2 * q2], v = b[2 * q2 + 1];
+          float x0, x1;
+          if (pl < 2) {
+            x0 = half == 0 ? u.x : u.y;
+            x1 = half == 0 ? v.x : v.y;
+          } else {
+            x0 = u.x + u.y;
+            x1 = v.x + v.y;
+          }
+          uint32_t hi, lo;
+          split_pair<MODE>(x0 * sc, x1 * sc, hi, lo);
+          w[q2] = (pl == 0 || (pl == 2 && half == 0)) ? hi : lo;
+        }
+        st16(dst, w[0], w[1], w[2], w[3]);
       }
-      st16(dst, w[0], w[1], w[2], w[3]);
     }
   }
 }

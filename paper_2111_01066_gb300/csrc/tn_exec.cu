@@ -304,14 +304,14 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
 }
 
 template <int MODE, int CM>
-static void launch_tc(const TcArgs& t, const StepLaunch& L, int pblocks, int grid, cudaStream_t s) {
-  if constexpr (CM == 4) {
-    // one CTA per B' image block at a time
-    const int64_t n_blocks = (int64_t)t.g.n_inst * t.n_nt * t.n_kc;
-    k_tc_prep_b<MODE><<<(int)std::max<int64_t>(1, std::min<int64_t>(n_blocks, (int64_t)sm_count() * 16)), 256, 0, s>>>(t);
-  }
+static void launch_tc(const TcArgs& t, const StepLaunch& L, int grid, cudaStream_t s) {
+  // one CTA per B' image block at a time
+  const int64_t n_blocks = (int64_t)t.g.n_inst * t.n_nt * t.n_kc;
+  const int pgrid = (int)std::max<int64_t>(1, std::min<int64_t>(n_blocks, (int64_t)sm_count() * 16));
+  if constexpr (CM == 4)
+    k_tc_prep_b<MODE><<<pgrid, 256, 0, s>>>(t);
   else
-    k_tc_prep_b3<MODE><<<pblocks, 256, 0, s>>>(t);
+    k_tc_prep_b3<MODE><<<pgrid, 256, 0, s>>>(t);
   static bool attr = false;
   if (!attr) {
     CK(cudaFuncSetAttribute(k_cgemm_tc<MODE, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -331,27 +331,25 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
   t.err = err;
   if (t.n_split > 1) t.c_part = reinterpret_cast<float2*>(ws + L.split_off);
   if (t.n_tiles <= 0) return;
-  const int64_t prep_total = (int64_t)t.g.n_inst * t.n_nt * t.n_kc * TC_TK * t.tn_c;
-  const int pblocks = (int)std::min<int64_t>((prep_total + 255) / 256, (int64_t)sm_count() * 16);
   const int grid = (int)std::min<int64_t>(t.n_tiles, sm_count());
   switch (L.kid) {
     case K_TC_TF32:
-      launch_tc<TC_TF32, 4>(t, L, pblocks, grid, s);
+      launch_tc<TC_TF32, 4>(t, L, grid, s);
       break;
     case K_TC_BF16X3:
-      launch_tc<TC_BF16X3, 4>(t, L, pblocks, grid, s);
+      launch_tc<TC_BF16X3, 4>(t, L, grid, s);
       break;
     case K_TC_TF32_3M:
-      launch_tc<TC_TF32, 3>(t, L, pblocks, grid, s);
+      launch_tc<TC_TF32, 3>(t, L, grid, s);
       break;
     case K_TC_BF16X3_3M:
-      launch_tc<TC_BF16X3, 3>(t, L, pblocks, grid, s);
+      launch_tc<TC_BF16X3, 3>(t, L, grid, s);
       break;
     case K_TC_FP16X3:
-      launch_tc<TC_FP16X3, 4>(t, L, pblocks, grid, s);
+      launch_tc<TC_FP16X3, 4>(t, L, grid, s);
       break;
     default:
-      launch_tc<TC_FP16X3, 3>(t, L, pblocks, grid, s);
+      launch_tc<TC_FP16X3, 3>(t, L, grid, s);
       break;
   }
   if (t.n_split > 1) {
