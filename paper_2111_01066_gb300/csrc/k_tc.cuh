@@ -293,20 +293,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, uint3
   d |= (uint64_t)layout << 61;
   return d;
 }
+// One MMA; the operand descriptors are given as their low words (start
+// address) and the high word they share (stride, version, layout).
 template <int MODE>
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint32_t adesc_lo, uint32_t bdesc_lo, uint32_t desc_hi,
+                                       uint32_t idesc, uint32_t accumulate) {
   if constexpr (MODE == TC_TF32) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\tmov.b64 ad, {%1, %3};\n\tmov.b64 bd, {%2, %3};\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], ad, bd, %4, p;\n\t}" ::"r"(d_tmem),
+        "r"(adesc_lo), "r"(bdesc_lo), "r"(desc_hi), "r"(idesc), "r"(accumulate)
         : "memory");
   } else {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\tmov.b64 ad, {%1, %3};\n\tmov.b64 bd, {%2, %3};\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %4, p;\n\t}" ::"r"(d_tmem),
+        "r"(adesc_lo), "r"(bdesc_lo), "r"(desc_hi), "r"(idesc), "r"(accumulate)
         : "memory");
   }
 }
@@ -1008,15 +1012,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       const int mma_n = CM == 4 ? ncp : a.tn_c;
       const uint32_t idesc = (1u << 4) | ((uint32_t)T::FMT << 7) | ((uint32_t)T::FMT << 10) |
                              ((uint32_t)(mma_n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+      // operand descriptors of the ring bases: a slot, plane or K-step offset
+      // is added to the 14-bit start-address field in 16-byte units (shared
+      // addresses stay below 256 KB, so the field never carries)
       const uint32_t sbo = tc_sbo(T::ESZ);
       const uint32_t lay = T::ESZ == 4 ? 2u : 4u;
-      int sa_i = 0, sb_i = 0;
-      uint32_t pha = 0, phb = 0;
-      int64_t it = 0;
+      const uint64_t dfa = smem_desc(smem_u32(aring), sbo, lay), dfb = smem_desc(smem_u32(bring), sbo, lay);
+      const uint32_t da0 = (uint32_t)dfa, db0 = (uint32_t)dfb, dhi = (uint32_t)(dfa >> 32);
+      const uint32_t a_step = (uint32_t)(P::A_SLOT >> 4), b_step = (uint32_t)(b_slot >> 4);
+      const uint32_t ap = (uint32_t)(a_plane >> 4), bp = (uint32_t)(b_plane >> 4);
+      // generic-proxy operand writes are ordered before the MMAs by their
+      // writers, except the cp.async gathers of TF32 4M: fenced here
+      const bool fence_a = MODE == TC_TF32 && CM == 4 && !a.a_tma;
+      uint32_t da = da0, db = db0;
+      int sa_i = 0, sb_i = 0, acc = 0;
+      uint32_t pha = 0, phb = 0, aph = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x, ++it) {
-        const int acc = (int)((uint32_t)it % (uint32_t)a.n_acc);
-        const uint32_t aph = ((uint32_t)it / (uint32_t)a.n_acc) & 1u;
+      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
         if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * setw);
@@ -1026,23 +1038,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
             ok = false;
             break;
           }
-          fence_proxy_async();
+          if (fence_a) fence_proxy_async();
           tc_fence_after();
-          const uint32_t sa = smem_u32(aring + sa_i * P::A_SLOT);
-          const uint32_t sb = smem_u32(bring + sb_i * b_slot);
-          // one MMA K step = 32 bytes of every plane row: advance inside the swizzle atom
-          auto mma = [&](uint32_t d, uint32_t a_addr, uint32_t b_addr, uint32_t accumulate) {
-            tc_mma<MODE>(d, smem_desc(a_addr, sbo, lay), smem_desc(b_addr, sbo, lay), idesc, accumulate);
+          auto mma = [&](uint32_t d, uint32_t adesc, uint32_t bdesc, uint32_t accumulate) {
+            tc_mma<MODE>(d, adesc, bdesc, dhi, idesc, accumulate);
           };
+          // one MMA K step = 32 bytes of every plane row (2 descriptor units):
+          // the step advances inside the swizzle atom
           if constexpr (CM == 4) {
 #pragma unroll
             for (int j = 0; j < TC_KP * T::ESZ / 32; ++j) {
-              const uint32_t koff = (uint32_t)j * 32u;
+              const uint32_t ko = (uint32_t)(2 * j);
               const uint32_t first = (kc > 0 || j > 0) ? 1u : 0u;
-              mma(d_tmem, sa + koff, sb + koff, first);
+              mma(d_tmem, da + ko, db + ko, first);
               if constexpr (MODE != TC_TF32) {   // hi*hi + hi*lo + lo*hi
-                mma(d_tmem, sa + koff, sb + b_plane + koff, 1u);
-                mma(d_tmem, sa + a_plane + koff, sb + koff, 1u);
+                mma(d_tmem, da + ko, db + bp + ko, 1u);
+                mma(d_tmem, da + ap + ko, db + ko, 1u);
               }
             }
           } else {
@@ -1052,41 +1063,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
               // planes [Ar | Ai], [As | -] against [Br | Bi], [Bs | 0]: two K steps of 8
 #pragma unroll
               for (int j = 0; j < 2; ++j) {
-                const uint32_t ko = (uint32_t)j * 32u;
+                const uint32_t ko = (uint32_t)(2 * j);
                 const uint32_t first = (kc > 0 || j > 0) ? 1u : 0u;
-                mma(d1, sa + ko, sb + ko, first);
-                mma(d2, sa + 64u + ko, sb + 64u + ko, first);
-                mma(d3, sa + a_plane + ko, sb + b_plane + ko, first);
+                mma(d1, da + ko, db + ko, first);
+                mma(d2, da + 4u + ko, db + 4u + ko, first);
+                mma(d3, da + ap + ko, db + bp + ko, first);
               }
             } else {
               // planes H = [Ar_hi | Ai_hi], L = [Ar_lo | Ai_lo], S = [As_hi | As_lo]
               const uint32_t first = kc > 0 ? 1u : 0u;
-              const uint32_t H = sa, L = sa + a_plane, S = sa + 2 * a_plane;
-              const uint32_t BH = sb, BL = sb + b_plane, BS = sb + 2 * b_plane;
+              const uint32_t H = da, L = da + ap, S = da + 2u * ap;
+              const uint32_t BH = db, BL = db + bp, BS = db + 2u * bp;
               mma(d1, H, BH, first);
               mma(d1, H, BL, 1u);
               mma(d1, L, BH, 1u);
-              mma(d2, H + 32u, BH + 32u, first);
-              mma(d2, H + 32u, BL + 32u, 1u);
-              mma(d2, L + 32u, BH + 32u, 1u);
+              mma(d2, H + 2u, BH + 2u, first);
+              mma(d2, H + 2u, BL + 2u, 1u);
+              mma(d2, L + 2u, BH + 2u, 1u);
               mma(d3, S, BS, first);
-              mma(d3, S, BS + 32u, 1u);
-              mma(d3, S + 32u, BS, 1u);
+              mma(d3, S, BS + 2u, 1u);
+              mma(d3, S + 2u, BS, 1u);
             }
           }
           tc_commit(smem_u32(&emptyA[sa_i]));
           tc_commit(smem_u32(&emptyB[sb_i]));
+          da += a_step;
           if (++sa_i == na) {
             sa_i = 0;
             pha ^= 1;
+            da = da0;
           }
+          db += b_step;
           if (++sb_i == nbs) {
             sb_i = 0;
             phb ^= 1;
+            db = db0;
           }
         }
         if (!ok) break;
         tc_commit(smem_u32(&tfull[acc]));
+        if (++acc == a.n_acc) {
+          acc = 0;
+          aph ^= 1;
+        }
       }
       // drain: every MMA issued so far completes before the CTA frees TMEM
       tc_commit(smem_u32(fin));
@@ -1123,10 +1142,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     // the result's largest component, for its consumer's FP16 scaling (split-K
     // partials are not the result: the reduction records it)
     const bool track = g.amax_c != nullptr && a.n_split == 1;
-    int64_t it = 0;
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
-      const int acc = (int)((uint32_t)it % (uint32_t)a.n_acc);
-      const uint32_t aph = ((uint32_t)it / (uint32_t)a.n_acc) & 1u;
+    int acc = -1;
+    uint32_t aph = 1;
+    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+      if (++acc == a.n_acc) acc = 0;
+      if (acc == 0) aph ^= 1;
       // warp-uniform decision: the TMEM loads and shuffles below need all 32 lanes
       if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, a.err))) break;
       tc_fence_after();
