@@ -183,7 +183,7 @@ def cores_used() -> int:
 
 
 # ------------------------------------------------------------------ rooflines
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 x GHz
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 flops x GHz under load
 
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels,
 # keyed by (kernel, log2 m,k,n,batch); see profiles/ for the command and scaling.
