@@ -457,7 +457,10 @@ def main() -> int:
             steps = t["step_full_batch_seconds"][args.warmup:]
         mean_s = statistics.mean(steps) if steps else None
         value = total_slices / mean_s if steps else None
-        line = {"impl": "reference", "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": 0,
+        # n_gpus is the launch's N (the line pairs with this arm's own line at
+        # that N); the oracle itself runs on the host cores of rank 0 only
+        line = {"impl": "reference", "metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": args.gpus,
+                "device": "host cores (FP64 oracle)",
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": (mean_s * 1e3 if steps else None),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
