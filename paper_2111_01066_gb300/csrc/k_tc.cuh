@@ -9,9 +9,13 @@
 // so that D[m, (n,0)] = Re C and D[m, (n,1)] = Im C: the accumulator rows are
 // interleaved complex64 rows of C.  Four real products per complex product (4M).
 //
-// Precision modes: TF32 (kind::tf32, one MMA per K step) and BF16X3
-// (kind::f16 with bf16 hi/lo split operands: hi*hi + hi*lo + lo*hi, FP32
-// accumulation in TMEM).
+// Precision modes: TF32 (kind::tf32, one MMA per K step), BF16X3 (kind::f16
+// with bf16 hi/lo split operands: hi*hi + hi*lo + lo*hi, FP32 accumulation in
+// TMEM) and FP16X3 (the same with fp16 halves, each operand first scaled by a
+// power of two from its largest component; the epilogue undoes it exactly).
+// CM = 3 forms three real products instead (3M: T1 = Ar Br, T2 = Ai Bi,
+// T3 = (Ar + Ai)(Br + Bi) in three accumulators; Re = T1 - T2,
+// Im = T3 - T1 - T2), see TcPl.
 //
 // A (the large, streamed operand) is gathered by loader warps straight from
 // its tensor's storage order -- the index permutation of Eq. (2) is folded into
@@ -23,13 +27,14 @@
 //   warps 0-3  epilogue: TMEM -> registers -> C (lane = tile row)
 //   warp  4    TMEM allocation; lane 0 issues tcgen05.mma and commits
 //   warps 5-12 loaders: A gathers into the A ring, or, when A is fetched by
-//              TMA in BF16X3 mode, the fp32 -> hi/lo converters (in place)
+//              TMA (and is not the TF32 4M operand itself), the fp32 ->
+//              operand-plane converters (in place)
 //   warp  13   A producer: when A is stored as [contracted..., free...] its
 //              tiles are fetched by one tensor-map load per k chunk
 //   warp  14   B' producer: one bulk copy of the (n tile, k chunk) image per k chunk
-// Two rings decouple the operands: a deep ring of 16 KB A slots (more of the
-// streamed operand in flight for the memory-bound steps) and a shallow ring of
-// B' slots (B' comes from L2).
+// Two rings decouple the operands: a deep ring of 16-32 KB A slots (more of
+// the streamed operand in flight for the memory-bound steps) and a shallow
+// ring of B' slots (B' comes from L2).
 // Every mbarrier wait is bounded by a globaltimer deadline; on expiry the
 // kernel records TN_ERR_TIMEOUT in *err, every role leaves its loop, and the
 // CTA frees its TMEM and returns.
