@@ -188,8 +188,8 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 flops x G
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels,
 # keyed by (kernel, log2 m,k,n,batch); see profiles/ for the command and scaling.
 MEASURED_TRAFFIC = {
-    # 4 x the 8-instance proxy capture (profiles/tc_bf16x3_12x12x8_batch8.md: 1321.6 MB)
-    ("tc_bf16x3", (12, 12, 8, 5)): 5.2866e9,
+    # 4 x the 8-instance proxy capture (profiles/tc_bf16x3_12x12x8_batch8.md: 1320.1 MB)
+    ("tc_bf16x3", (12, 12, 8, 5)): 5.2804e9,
 }
 
 

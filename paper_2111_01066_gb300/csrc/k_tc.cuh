@@ -610,8 +610,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   uint64_t* emptyA = bars + TC_MAX_A;
   uint64_t* rawA = bars + 2 * TC_MAX_A;
   uint64_t* fullB = bars + 3 * TC_MAX_A;
-  uint64_t* emptyB = fullB + TC_MAX_B;
-  uint64_t* tfull = emptyB + TC_MAX_B;
+  uint64_t* tfull = fullB + TC_MAX_B;   // (B' slots are released through emptyA)
   uint64_t* tempty = tfull + TC_MAX_ACC;
   uint64_t* fin = tempty + TC_MAX_ACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
@@ -636,7 +635,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     }
     for (int s = 0; s < nbs; ++s) {
       mbar_init(smem_u32(&fullB[s]), 1);
-      mbar_init(smem_u32(&emptyB[s]), 1);
     }
     for (int i = 0; i < TC_MAX_ACC; ++i) {
       mbar_init(smem_u32(&tfull[i]), 1);
@@ -696,23 +694,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   } else if (warp == TC_B_WARP) {
     // ---------------------------------------------------------------- B' producer
     if (lane == 0) {
-      int slot = 0;
-      uint32_t ph = 0;
+      // B' slot q % nbs is free again once the MMAs of chunk q - nbs are done:
+      // the MMA thread's single commit per chunk arrives on emptyA of that
+      // chunk's A slot, whose completion for chunk j has parity (j / na) & 1
+      // (na >= nbs, so that barrier cannot have moved on by a further phase)
+      int slot = 0, ws = 0;
+      uint32_t wph = 0;
+      int64_t q = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
         const TileIdx ti = tile_decode(tile, a);
         const int kc0 = ti.s * kc_per;
         const int nt = ti.nt, inst = ti.inst;
         const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * (int64_t)b_slot;
-        for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
-          if (!mbar_wait(smem_u32(&emptyB[slot]), ph ^ 1, abort_flag, a.err)) { ok = false; break; }
+        for (int kc = kc0; kc < kc0 + kc_per; ++kc, ++q) {
+          if (q >= nbs) {
+            if (!mbar_wait(smem_u32(&emptyA[ws]), wph, abort_flag, a.err)) { ok = false; break; }
+            if (++ws == na) {
+              ws = 0;
+              wph ^= 1;
+            }
+          }
           const uint32_t fb = smem_u32(&fullB[slot]);
           mbar_arrive_expect_tx(fb, (uint32_t)b_slot);
           bulk_g2s(smem_u32(bring + slot * b_slot), bt + (int64_t)kc * b_slot, (uint32_t)b_slot, fb);
-          if (++slot == nbs) {
-            slot = 0;
-            ph ^= 1;
-          }
+          if (++slot == nbs) slot = 0;
         }
       }
     }
@@ -1091,7 +1097,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
             }
           }
           tc_commit(smem_u32(&emptyA[sa_i]));
-          tc_commit(smem_u32(&emptyB[sb_i]));
           da += a_step;
           if (++sa_i == na) {
             sa_i = 0;

@@ -274,6 +274,7 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   const int budget = 220 * 1024 - 4096 - TC_EPI_BYTES;
   t.nbs = b_slot <= 16384 ? TC_MAX_B : 3;
   t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
+  t.nbs = std::min(t.nbs, t.na);   // B' slots are released through the A slots' barriers
   // arrivals on an A slot: the TMA itself (TF32 4M), one converter group (TMA otherwise), all loaders
   t.fa_count = (t.a_tma && kid == K_TC_TF32) ? 1 : (t.a_tma ? TC_LOAD_THREADS / 2 : TC_LOAD_THREADS);
   // as many accumulator sets as fit the 512 TMEM columns (at most 8): narrow
