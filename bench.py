@@ -593,19 +593,23 @@ def main() -> int:
     # the other paths on the same workload: FP32 SIMT (the plain path) and TF32
     others = {}
     gold = None
+    # stored oracle results (text files written by tests/golden/make_golden.py):
+    # the batch's amplitudes and their linear XEB
     gold_path = os.path.join(ROOT, "tests", "golden", f"{name}_amplitudes.txt")
-    if rank == 0 and os.path.exists(gold_path):
-        from tests.golden.make_golden import read
-        gold = read(name)
+    gold_xeb_path = os.path.join(ROOT, "tests", "golden", f"{name}_xeb.txt")
+    gold_xeb = None
+    if rank == 0 and os.path.exists(gold_path) and os.path.exists(gold_xeb_path):
+        g = np.loadtxt(gold_path, comments="#")
+        gold = g[:, 0] + 1j * g[:, 1]
+        gold_xeb = float(np.loadtxt(gold_xeb_path, comments="#"))
 
     def amp_error(o):
         if gold is None or gold.size != (o.numel() // 2) or n_slices != all_slices:
             return None
-        from oracle import xeb as oxeb
         got = o.cpu().numpy().view(np.complex128)
         f = tn.xeb(o.view(torch.complex128), circ.n_qubits)
         return {"rel_amp_err": float(np.linalg.norm(got - gold) / np.linalg.norm(gold)),
-                "xeb_err": abs(f - oxeb.linear_xeb(gold, circ.n_qubits))}
+                "xeb_err": abs(f - gold_xeb)}
 
     if args.compare_fp32:
         # the plain FP32 path, TF32, and the other complex product (4M / 3M) of this precision

@@ -5,6 +5,9 @@ per workload, `<name>_amplitudes.txt`, with a header line and one amplitude per
 line ("re im", 17 significant digits), in the batch order sum_j b(open_j) 2^j.
 
     python tests/golden/make_golden.py c2 c3 c5
+
+With the amplitudes of c2 and c3 it also writes `<name>_xeb.txt`, their linear
+XEB computed by the oracle.
 """
 import os
 import sys
@@ -77,9 +80,28 @@ def read(name: str) -> np.ndarray:
     return data[:, 0] + 1j * data[:, 1]
 
 
+def write_xeb(name: str) -> None:
+    """The oracle's linear XEB (main text, Eq. (1) with F = N<p> - 1) of the
+    stored amplitudes of `name`, so that a reader of the amplitudes needs no
+    oracle import to compare an XEB with it."""
+    from oracle import xeb
+    circ, _, _ = rqcgen.config_circuit(name)
+    f_xeb = xeb.linear_xeb(read(name), circ.n_qubits)
+    path = os.path.join(HERE, f"{name}_xeb.txt")
+    with open(path, "w") as f:
+        f.write(f"# {name}: n={circ.n_qubits} linear XEB of {name}_amplitudes.txt (oracle.xeb.linear_xeb)\n")
+        f.write(f"{f_xeb:.17e}\n")
+    print(path, f_xeb)
+
+
+def read_xeb(name: str) -> float:
+    return float(np.loadtxt(os.path.join(HERE, f"{name}_xeb.txt"), comments="#"))
+
+
 if __name__ == "__main__":
     for n in sys.argv[1:] or ["c2"]:
         if n == "c5":
             write_sliced("c5", 2)
         else:
             write(n)
+            write_xeb(n)

@@ -408,3 +408,16 @@ def test_frugal_sampling_law_and_sampled_xeb():
     # sampled linear XEB of an ideal sampler of Porter-Thomas amplitudes is ~1
     f = xeb.linear_xeb(a[np.array(samples)], n)
     assert abs(f - (256 * np.sum(np.abs(a) ** 4) - 1)) < 0.1
+
+
+@pytest.mark.parametrize("name", ["c2", "c3"])
+def test_stored_xeb_is_the_oracle_xeb_of_the_stored_amplitudes(name):
+    """The stored XEB beside a workload's stored amplitudes is the oracle's
+    linear XEB of exactly those amplitudes (it is what the benchmark compares
+    the library's XEB with), and it obeys Eq. (1)'s range: F = N<p> - 1 > -1."""
+    from tests.golden import make_golden
+    circ, _, _ = rqcgen.config_circuit(name)
+    amps = make_golden.read(name)
+    stored = make_golden.read_xeb(name)
+    assert stored == pytest.approx(xeb.linear_xeb(amps, circ.n_qubits), rel=1e-15, abs=1e-17)
+    assert stored > -1.0
