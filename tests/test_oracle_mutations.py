@@ -94,3 +94,25 @@ def test_planted_frugal_sampling_mistakes_are_caught(monkeypatch, mistake):
     monkeypatch.setattr(sampling, "accept_mask", mutated)
     with pytest.raises(AssertionError):
         pin()
+
+
+def test_planted_pairwise_mistakes_are_caught(monkeypatch):
+    """A conjugated operand and a reversed storage order (wire 0 slowest) in the
+    pairwise oracle each fail its brute-force pin."""
+    from oracle import pairwise
+    from tests.test_oracle_pins import _bruteforce_pair
+    rng = np.random.default_rng(11)
+    a_w, b_w, c_w = [0, 10, 1], [10, 20], [1, 20, 0]
+    a = rng.normal(size=8) + 1j * rng.normal(size=8)
+    b = rng.normal(size=4) + 1j * rng.normal(size=4)
+    want = _bruteforce_pair(a, a_w, b, b_w, c_w)
+    assert np.max(np.abs(pairwise.contract_pair(a, a_w, b, b_w, c_w) - want)) < 1e-13
+    orig = pairwise.contract_pair
+
+    monkeypatch.setattr(pairwise, "contract_pair",
+                        lambda a_, aw, b_, bw, cw: orig(np.conj(a_), aw, b_, bw, cw))
+    assert np.max(np.abs(pairwise.contract_pair(a, a_w, b, b_w, c_w) - want)) > 1e-3
+    monkeypatch.setattr(pairwise, "to_axes",
+                        lambda flat, rank: np.asarray(flat).reshape((2,) * rank) if rank else np.asarray(flat).reshape(()))
+    monkeypatch.setattr(pairwise, "contract_pair", orig)
+    assert np.max(np.abs(pairwise.contract_pair(a, a_w, b, b_w, c_w) - want)) > 1e-3

@@ -421,3 +421,63 @@ def test_stored_xeb_is_the_oracle_xeb_of_the_stored_amplitudes(name):
     stored = make_golden.read_xeb(name)
     assert stored == pytest.approx(xeb.linear_xeb(amps, circ.n_qubits), rel=1e-15, abs=1e-17)
     assert stored > -1.0
+
+
+# ---------------------------------------------------------------- pairwise contraction / permutation
+# SI Eq. (2) and the storage convention of figure S7's caption: a tensor over
+# wires w_0..w_{r-1} is a flat array whose element sum_i b(w_i) 2^i holds the
+# entry with wire w_i set to b(w_i).  The brute force below walks every wire
+# assignment with plain integer loops (no einsum, no reshape).
+
+def _bruteforce_pair(a, a_wires, b, b_wires, c_wires):
+    wires = sorted(set(a_wires) | set(b_wires))
+    out = np.zeros(2 ** len(c_wires), dtype=np.complex128)
+    for assign in range(2 ** len(wires)):
+        val = {w: (assign >> i) & 1 for i, w in enumerate(wires)}
+        ia = sum(val[w] << i for i, w in enumerate(a_wires))
+        ib = sum(val[w] << i for i, w in enumerate(b_wires))
+        ic = sum(val[w] << i for i, w in enumerate(c_wires))
+        out[ic] += a[ia] * b[ib]
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pairwise_contraction_against_bruteforce(seed):
+    from oracle import pairwise
+    rng = np.random.default_rng(700 + seed)
+    m, k, n = (int(x) for x in rng.integers(0, 4, size=3))
+    free_a, shared, free_b = list(range(m)), list(range(10, 10 + k)), list(range(20, 20 + n))
+    a_w = [int(w) for w in rng.permutation(free_a + shared)]
+    b_w = [int(w) for w in rng.permutation(shared + free_b)]
+    c_w = [int(w) for w in rng.permutation(free_a + free_b)]
+    a = rng.normal(size=2 ** len(a_w)) + 1j * rng.normal(size=2 ** len(a_w))
+    b = rng.normal(size=2 ** len(b_w)) + 1j * rng.normal(size=2 ** len(b_w))
+    got = pairwise.contract_pair(a, a_w, b, b_w, c_w)
+    np.testing.assert_allclose(got, _bruteforce_pair(a, a_w, b, b_w, c_w), rtol=1e-13, atol=1e-13)
+
+
+def test_pairwise_contraction_is_a_column_major_matrix_product():
+    """Special case: A over wires (m, k) and B over (k, n), both 2^2 x 2^2
+    with the first listed wires fastest, give C = A B of the column-major
+    matrices (numpy's matmul on reshape(order='F'))."""
+    from oracle import pairwise
+    rng = np.random.default_rng(5)
+    a = rng.normal(size=16) + 1j * rng.normal(size=16)
+    b = rng.normal(size=16) + 1j * rng.normal(size=16)
+    got = pairwise.contract_pair(a, [0, 1, 2, 3], b, [2, 3, 4, 5], [0, 1, 4, 5])
+    want = (a.reshape(4, 4, order="F") @ b.reshape(4, 4, order="F")).reshape(-1, order="F")
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("rank", [1, 3, 5])
+def test_permute_against_bruteforce(rank):
+    from oracle import pairwise
+    rng = np.random.default_rng(rank)
+    perm = [int(p) for p in rng.permutation(rank)]
+    t = rng.normal(size=2 ** rank) + 1j * rng.normal(size=2 ** rank)
+    want = np.zeros_like(t)
+    for i in range(2 ** rank):
+        # output bit p is input bit perm[p]
+        o = sum(((i >> perm[p]) & 1) << p for p in range(rank))
+        want[o] = t[i]
+    np.testing.assert_array_equal(pairwise.permute(t, rank, perm), want)
