@@ -178,3 +178,66 @@ def test_chunk_launches_needs_device_state(tn):
     with pytest.raises(tn.TnError) as e:
         plan.chunk_launches()
     assert e.value.status == tn.TN_ERR_ARG
+
+
+def test_compute_calls_reject_bad_arguments_before_device_work(tn):
+    """The compute entry points validate their host-side arguments first and
+    return TN_ERR_ARG (TN_ERR_UNSUPPORTED for 3M on the FP32 path) with a
+    message, before any device memory is touched or kernel launched; the device
+    pointers below are never dereferenced."""
+    import ctypes
+    lib = tn.load()
+    ERR, UNS = tn.TN_ERR_ARG, tn.TN_ERR_UNSUPPORTED
+    dev = ctypes.c_void_p(1 << 20)   # stands for a device buffer
+    x = ctypes.c_double()
+
+    def i32(v):
+        return (ctypes.c_int32 * max(1, len(v)))(*v)
+
+    def expect(status, want):
+        assert status == want
+        assert lib.tn_last_error()
+
+    # tn_xeb: NULL, empty, qubit count
+    expect(lib.tn_xeb(None, 4, 10, ctypes.byref(x), None), ERR)
+    expect(lib.tn_xeb(dev, 0, 10, ctypes.byref(x), None), ERR)
+    expect(lib.tn_xeb(dev, 4, -1, ctypes.byref(x), None), ERR)
+    # tn_frugal_sample: bound, empty batch, draw count
+    first = (ctypes.c_int64 * 4)()
+    for m_bound in (0.0, -1.0, float("nan"), float("inf")):
+        expect(lib.tn_frugal_sample(dev, 64, 6, m_bound, dev, dev, 8, 4, first, None), ERR)
+    expect(lib.tn_frugal_sample(dev, 0, 6, 10.0, dev, dev, 8, 4, first, None), ERR)
+    expect(lib.tn_frugal_sample(dev, 64, 6, 10.0, dev, dev, 1 << 40, 4, first, None), ERR)
+    # tn_permute: rank range, not a permutation, negative batch
+    expect(lib.tn_permute(dev, dev, 35, i32(list(range(35))), 1, None), ERR)
+    expect(lib.tn_permute(dev, dev, 3, i32([0, 0, 2]), 1, None), ERR)
+    expect(lib.tn_permute(dev, dev, 3, i32([0, 3, 1]), 1, None), ERR)
+    expect(lib.tn_permute(dev, dev, 3, i32([2, 1, 0]), -1, None), ERR)
+
+    # tn_contract_pair: A(0,1,2) B(2,3) -> C(0,1,3) is valid; break one thing at a time
+    def pair(aw, bw, cw, batch=1, prec=tn.PREC["fp32"], cm=4):
+        return lib.tn_contract_pair(dev, i32(aw), len(aw), dev, i32(bw), len(bw), dev, i32(cw), len(cw),
+                                    batch, prec, cm, None)
+    expect(pair([0, 1, 1], [1, 3], [0, 3]), ERR)                    # repeated wire in A
+    expect(pair([0, 1, 2], [2, 2], [0, 1]), ERR)                    # repeated wire in B
+    expect(pair([0, 1, 2], [2, 3], [0, 1]), ERR)                    # C misses B's free wire
+    expect(pair([0, 1, 2], [2, 3], [0, 3, 7]), ERR)                 # C has a foreign wire
+    expect(pair([0, 1, 2], [2, 3], [0, 1, 3], batch=0), ERR)
+    expect(pair([0, 1, 2], [2, 3], [0, 1, 3], prec=17), ERR)
+    expect(pair([0, 1, 2], [2, 3], [0, 1, 3], cm=5), ERR)
+    expect(pair([0, 1, 2], [2, 3], [0, 1, 3], cm=3), UNS)           # 3M needs a tensor-core mode
+
+    # tn_contract_slices: NULL, no batch, slice range beyond 2^S (S = 5 here)
+    circ, om, _ = rqcgen.config_circuit("c1")
+    plan = tn.Plan(tn.Network(circ), open_mask=om & 0xFF, max_log2_intermediate=30, min_log2_slices=5, trials=4)
+    bits = (ctypes.c_uint64 * 1)(0)
+    expect(lib.tn_contract_slices(plan.handle, 0, 32, None, 1, dev, None), ERR)
+    expect(lib.tn_contract_slices(plan.handle, 0, 32, bits, 0, dev, None), ERR)
+    expect(lib.tn_contract_slices(plan.handle, 30, 3, bits, 1, dev, None), ERR)
+    expect(lib.tn_contract_slices(plan.handle, 33, 0, bits, 1, dev, None), ERR)
+    assert lib.tn_contract_slices(plan.handle, 32, 0, bits, 1, dev, None) == tn.TN_OK   # empty range: no work
+
+    # tn_plan_select: candidate count
+    o = tn.default_opts()
+    h = ctypes.c_void_p()
+    expect(lib.tn_plan_select(tn.Network(circ).handle, ctypes.byref(o), 0, 0, None, ctypes.byref(h), None), ERR)
