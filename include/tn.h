@@ -35,6 +35,13 @@
  *
  * Streams are passed as `void*` holding a cudaStream_t (NULL = legacy default
  * stream) so that this header needs no CUDA include.
+ *
+ * Concurrency: a plan is used by one host thread at a time; different plans may
+ * run on different streams.  tn_contract_pair, tn_xeb and tn_frugal_sample
+ * share one small per-device scratch area (result word, error word, B' images
+ * of tn_contract_pair, grown on demand), so calls of these that may overlap on
+ * the same device -- from several host threads, or queued on streams that run
+ * concurrently -- must be serialised by the caller.
  */
 #ifndef TN_GB300_H
 #define TN_GB300_H
