@@ -406,7 +406,7 @@ static int pick_kernel(int precision, int cmult, const StepDesc& d) {
 
 // Launch arguments of plan step d for kernel kid; FP16X3 plans also get the
 // maxima of the step's operands (to scale them) and of its result (to record).
-static GemmArgs step_args(const Plan& p, const DeviceState& ds, const StepDesc& d, int kid, int tn_log = -1) {
+static GemmArgs step_args(const DeviceState& ds, const StepDesc& d, int kid, int tn_log = -1) {
   GemmArgs g = make_args(d, kid, ds.arena + d.a_off, ds.arena + d.b_off, ds.arena + d.c_off, 1 << d.nb, 0, 0, 0,
                          tn_log);
   if (ds.amax) {
@@ -478,7 +478,7 @@ static void ensure_device(Plan& p) {
     if (!ok) fail(TN_ERR_PLAN, "internal: step operand outside its extent");
     const int kid = pick_kernel(p.opts.precision, p.opts.complex_mult, d);
     ds->launches.push_back(
-        make_launch(step_args(p, *ds, d, kid), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true));
+        make_launch(step_args(*ds, d, kid), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true));
   }
   int64_t ws = 16;
   for (const StepLaunch& L : ds->launches) ws = std::max(ws, L.ws_bytes);
@@ -742,7 +742,7 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   for (size_t i = 0; i < p.steps.size(); ++i) {
     const StepDesc& d = p.steps[i];
     auto build = [&](int kid, int tn_log, int epi) {
-      return make_launch(step_args(p, ds, d, kid, tn_log), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
+      return make_launch(step_args(ds, d, kid, tn_log), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
                          d.c_elems, true, epi);
     };
     double best = time_launch(ds.launches[i]);
