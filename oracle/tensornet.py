@@ -28,7 +28,6 @@ Test infrastructure only (see the package docstring).
 from __future__ import annotations
 
 import heapq
-import itertools
 from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
 import numpy as np

@@ -35,7 +35,7 @@ from __future__ import annotations
 import dataclasses
 import json
 import math
-from typing import List, Optional, Sequence, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 
