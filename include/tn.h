@@ -200,6 +200,18 @@ tn_status tn_plan_step_shape(const tn_plan_t* plan, int32_t step, int32_t* log2_
 tn_status tn_plan_step_layout(const tn_plan_t* plan, int32_t step, int32_t* out, int32_t cap,
                               int32_t* count);
 
+/* Modeled device time of one chunk of the plan on a roofline (host only; the
+ * cost model of plan selection, SI: the order with the fewest flops is not the
+ * fastest, so orders are compared by time): the sum over the steps that run in
+ * every chunk (those whose result depends on the slice id; the others run
+ * once per plan or per batch) of
+ *     max(8 m k n / peak_flops, 8 (|A| + |B| + |C|) / peak_bytes)
+ * with m, k, n the step's complex GEMM extents summed over its batch instances
+ * and |A|, |B|, |C| its operands' complex64 element counts.  peak_flops in
+ * algorithmic flop/s (8 per complex multiply-add) of the plan's precision,
+ * peak_bytes in B/s, both > 0.  Writes seconds to *seconds. */
+tn_status tn_plan_model_time(const tn_plan_t* plan, double peak_flops, double peak_bytes, double* seconds);
+
 /* Contract slices [slice_first, slice_first + slice_count) for n_batches
  * correlated batches and ADD the result into out_amplitudes (main text, section
  * II: the sliced network is the sum of the slices; section III: one run gives

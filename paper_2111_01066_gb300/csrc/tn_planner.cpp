@@ -1302,6 +1302,28 @@ extern "C" tn_status tn_plan_step_layout(const tn_plan_t* h, int32_t step, int32
   return TN_OK;
 }
 
+extern "C" tn_status tn_plan_model_time(const tn_plan_t* h, double peak_flops, double peak_bytes,
+                                        double* seconds) {
+  clear_error();
+  if (!h || !seconds) {
+    set_error("tn_plan_model_time: NULL argument");
+    return TN_ERR_ARG;
+  }
+  if (!(peak_flops > 0.0) || !(peak_bytes > 0.0) || !std::isfinite(peak_flops) || !std::isfinite(peak_bytes)) {
+    set_error("tn_plan_model_time: peaks must be positive and finite");
+    return TN_ERR_ARG;
+  }
+  double t = 0.0;
+  for (const StepDesc& d : h->plan.steps) {
+    if ((d.dep_flags & 1) == 0) continue;
+    const double flops = 8.0 * std::ldexp(1.0, d.nm + d.nk + d.nn + d.nb);
+    const double bytes = 8.0 * ((double)d.a_elems + (double)d.b_elems + (double)d.c_elems);
+    t += std::max(flops / peak_flops, bytes / peak_bytes);
+  }
+  *seconds = t;
+  return TN_OK;
+}
+
 extern "C" tn_status tn_plan_step_shape(const tn_plan_t* h, int32_t step, int32_t* lm, int32_t* lk,
                                         int32_t* ln, int32_t* lb) {
   clear_error();

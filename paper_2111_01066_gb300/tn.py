@@ -86,6 +86,8 @@ _SIGS = {
                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_double)]),
     "tn_plan_chunk_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "tn_plan_model_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_double)]),
     "tn_plan_step_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "tn_contract_slices": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
@@ -269,6 +271,13 @@ class Plan:
             pos += n
         out["dep_flags"] = v[pos]
         return out
+
+    def model_time(self, peak_flops: float, peak_bytes: float) -> float:
+        """tn_plan_model_time: modeled seconds of one chunk on a roofline
+        (peak_flops in algorithmic flop/s, peak_bytes in B/s)."""
+        s = ctypes.c_double()
+        _check(load().tn_plan_model_time(self.handle, peak_flops, peak_bytes, ctypes.byref(s)))
+        return s.value
 
     def chunk_launches(self) -> int:
         """Kernels one chunk launches with the kernels chosen so far (after the first contract call)."""

@@ -241,3 +241,28 @@ def test_compute_calls_reject_bad_arguments_before_device_work(tn):
     o = tn.default_opts()
     h = ctypes.c_void_p()
     expect(lib.tn_plan_select(tn.Network(circ).handle, ctypes.byref(o), 0, 0, None, ctypes.byref(h), None), ERR)
+
+
+def test_model_time_is_the_roofline_sum_over_chunk_steps(tn):
+    """tn_plan_model_time = sum over the steps that run every chunk (result
+    depends on the slice id) of max(8 m k n 2^b / P, 8 (|A|+|B|+|C|) / BW), with
+    |A| = 2^(m+k+b), |B| = 2^(k+n+b), |C| = 2^(m+n+b) from the step shapes; it
+    grows when either peak shrinks and rejects non-positive peaks."""
+    cfg = rqcgen.CONFIGS["c3"]
+    circ, om, _ = rqcgen.config_circuit("c3")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
+                   min_log2_slices=cfg["log2_slices"], trials=16, precision="bf16x3")
+    P, BW = 639.8e12, 6783.5e9
+    want = 0.0
+    for i, (m, k, n, b) in enumerate(plan.step_shapes()):
+        if plan.step_layout(i)["dep_flags"] & 1:
+            want += max(8.0 * 2 ** (m + k + n + b) / P,
+                        8.0 * (2 ** (m + k + b) + 2 ** (k + n + b) + 2 ** (m + n + b)) / BW)
+    got = plan.model_time(P, BW)
+    assert got == pytest.approx(want, rel=1e-12) and got > 0
+    assert plan.model_time(P / 2, BW) >= got and plan.model_time(P, BW / 2) >= got
+    assert plan.model_time(P / 2, BW / 2) == pytest.approx(2 * got, rel=1e-12)
+    for bad in ((0.0, BW), (P, -1.0), (float("nan"), BW)):
+        with pytest.raises(tn.TnError) as e:
+            plan.model_time(*bad)
+        assert e.value.status == tn.TN_ERR_ARG
