@@ -31,7 +31,9 @@
  * C++ exception crosses this boundary.  Errors found by device kernels after an
  * asynchronous launch (a bounded wait that ran out, a violated bound) are
  * sticky on the plan: they are returned by the plan's next call and by
- * tn_plan_sync().
+ * tn_plan_sync().  Calls without a plan (tn_contract_pair,
+ * tn_contract_pair_noalloc, tn_selftest_bounded_wait) record such errors in a
+ * per-device word that tn_device_sync() reads and clears.
  *
  * Streams are passed as `void*` holding a cudaStream_t (NULL = legacy default
  * stream) so that this header needs no CUDA include.
@@ -128,7 +130,6 @@ typedef struct tn_plan_opts {
                                         also serves the tiny steps of TF32/BF16X3 plans) */
     int32_t  log2_batch_slices;      /* slices contracted together per chunk (<= 0: auto) */
     int64_t  max_arena_bytes;        /* device arena cap for one chunk (<= 0: 96 GiB) */
-    int32_t  fuse_permute;           /* 1: permutes folded into operand gathers; 0: explicit permute pass */
     int32_t  n_forced_slices;        /* wires the caller slices (0: the planner chooses them all) */
     const int32_t* forced_slice_qubit;  /* [n_forced_slices]: wire (qubit, t) of slice bit j, host */
     const int32_t* forced_slice_t;      /* internal wires only: 1 <= t < gates on that qubit */
@@ -137,7 +138,9 @@ typedef struct tn_plan_opts {
 } tn_plan_opts;
 
 /* Fill opts with defaults: no open qubits, bound 2^30, no forced slices, seed 1,
- * 64 trials, FP32, 4M, automatic batch, 96 GiB arena, fused permutes.
+ * 64 trials, FP32, 4M, automatic batch, 96 GiB arena.  Index permutations are
+ * always folded into the contraction's operand loads and result stores (SI,
+ * figure S7a): there is no separate permute pass on the plan path.
  * Forced slices: the given wires take slice bits 0..n_forced_slices-1 (in the
  * given order) and the planner orders the rest of the network around them,
  * adding further slices only if the bound needs them; chunks then hold one
@@ -174,6 +177,10 @@ typedef struct tn_plan_stats {
                                               (tn_plan_chunk_launches gives the exact count) */
 } tn_plan_stats;
 
+/* Sizes and work of a plan (host only): the per-slice and per-chunk flop and
+ * byte counts behind the complexity figures of SI Table 1 (counted as 8 real
+ * flops per complex multiply-add) and the histogram of contracted sizes k of
+ * SI figure S4.  TN_ERR_ARG on a NULL argument. */
 tn_status tn_plan_info(const tn_plan_t* plan, tn_plan_stats* out);
 
 /* The sliced wires in slice-bit order: qubit[j], t[j] label slice bit j.
@@ -199,6 +206,20 @@ tn_status tn_plan_step_shape(const tn_plan_t* plan, int32_t step, int32_t* log2_
  * number of entries; at most `cap` are written (TN_ERR_ARG if cap is too small). */
 tn_status tn_plan_step_layout(const tn_plan_t* plan, int32_t step, int32_t* out, int32_t cap,
                               int32_t* count);
+
+/* The plan's contraction tree in terms of the circuit (host only; the SI's
+ * pairwise order as a list of two-tuples, over the simplified network): after
+ * simplification every circuit gate belongs to exactly one leaf tensor, and
+ * leaf_of_gate[g] (HOST [n_gates], n_gates >= the circuit's gate count)
+ * receives that leaf's index in [0, n_leaves); step_nodes (HOST [2 cap_steps])
+ * receives, for every step j in execution order, the two node ids it
+ * contracts (leaves 0..n_leaves-1; the result of step j is node n_leaves + j).
+ * The initial-state and output-projector tensors belong to the leaves that hold
+ * their qubit's first and last gate.  For reports and for checking a plan's
+ * partial sums against an independent contraction along the same tree.
+ * TN_ERR_ARG when n_gates or cap_steps is too small. */
+tn_status tn_plan_tree(const tn_plan_t* plan, int32_t* leaf_of_gate, int32_t n_gates, int32_t* step_nodes,
+                       int32_t cap_steps, int32_t* n_leaves, int32_t* n_steps);
 
 /* Modeled device time of one chunk of the plan on a roofline (host only; the
  * cost model of plan selection, SI: the order with the fewest flops is not the
@@ -234,9 +255,10 @@ tn_status tn_contract_slices(tn_plan_t* plan, uint64_t slice_first, uint64_t sli
  * `stream` between CUDA events, on the arena contents of the last chunk, and
  * writes the mean milliseconds per launch into ms_out[n_steps] (host array)
  * and, when kernel_out is not NULL, the kernel used by each step into
- * kernel_out[n_steps]: 0-2 FP32 SIMT tiles (64x64, 128x16, 256x4),
- * 3 tcgen05 TF32, 4 tcgen05 BF16x3.  Used for plan reports and roofline
- * measurements; synchronises `stream`. */
+ * kernel_out[n_steps]: 0-2 FP32 SIMT tiles (64x64, 128x16, 256x4), then the
+ * tcgen05 kernels 3 TF32 4M, 4 BF16x3 4M, 5 TF32 3M, 6 BF16x3 3M, 7 FP16x3 4M,
+ * 8 FP16x3 3M.  Used for plan reports and roofline measurements; synchronises
+ * `stream`. */
 tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int32_t* kernel_out,
                              void* stream);
 
@@ -251,16 +273,43 @@ tn_status tn_plan_autotune(tn_plan_t* plan, int32_t reps, void* stream);
 /* Plan selection by measured time (SI, TN section: the order whose measured
  * slice time is smallest is kept, not the one with the fewest flops).  Builds
  * n_candidates plans from *opts with seeds seed, seed+1, ... and memory weights
- * cycling through w, w/4, 4w (w = opts->mem_weight or 32), times one chunk of
- * each on `stream` (after an untimed warm-up call with the same bitstring),
- * estimates the time for all 2^S slices as chunk time x 2^(S-b), and returns
- * the fastest plan in *out (its device state is released; the first contract
- * call re-creates it).  cand_seconds (HOST, [n_candidates], may be NULL)
- * receives each estimate, -1 for a candidate that could not be built or run
- * (e.g. its arena does not fit).  Synchronises `stream`; TN_ERR_PLAN if no
- * candidate ran.  Kernels are not autotuned during the selection. */
+ * cycling through w, w/4, 4w (w = opts->mem_weight or 32), times chunks of
+ * each on `stream` (after an untimed warm-up call with the same bitstring, the
+ * fastest of three timed calls of one chunk), estimates the time for all 2^S
+ * slices as chunk time x 2^(S-b), and returns the fastest plan in *out (its
+ * device state is released; the first contract call re-creates it).
+ * cand_seconds (HOST, [n_candidates], may be NULL) receives each estimate, -1
+ * for a candidate that could not be built or run (e.g. its arena does not
+ * fit).  Synchronises `stream`; TN_ERR_PLAN if no candidate ran.  Kernels are
+ * not autotuned during the selection. */
 tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
                          uint64_t open_bitstring, void* stream, tn_plan_t** out, double* cand_seconds);
+
+/* tn_plan_select over a caller-given candidate list: candidate i is *opts with
+ * seed seeds[i] and memory weight mem_weights[i] (HOST arrays [n_candidates],
+ * n_candidates in [1, 1024]); timing, estimate, result and errors as in
+ * tn_plan_select.  With tn_plan_rank this is the two-stage selection of a plan
+ * pool: rank many orders by modeled time on the host, measure the best few. */
+tn_status tn_plan_select_list(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                              const uint64_t* seeds, const double* mem_weights, uint64_t open_bitstring,
+                              void* stream, tn_plan_t** out, double* cand_seconds);
+
+/* Host-only ranking of a plan pool (SI, TN section: many candidate orders are
+ * generated and compared by time, since the order with the fewest flops is not
+ * the fastest).  Candidate i is *opts with seed seeds[i] and memory weight
+ * mem_weights[i] (HOST arrays [n_candidates], n_candidates in [1, 100000]);
+ * each is planned (tn_plan) and model_seconds[i] (HOST) receives its modeled
+ * time for one batch over all 2^S slices -- tn_plan_model_time(peak_flops,
+ * peak_bytes) of one chunk x 2^(S-b), plus the same roofline sum over the
+ * steps that run once per batch bitstring (they depend on the closed output
+ * bits but on no slice) -- or -1 when the candidate cannot be planned (e.g. no
+ * batch fits the arena cap).  Steps that depend on neither run once per plan
+ * and are not counted.  Plans are built one after another, each on all host
+ * cores, and freed.  No CUDA call is made.  TN_ERR_PLAN if no candidate could
+ * be planned; TN_ERR_ARG on NULL arrays or non-positive peaks. */
+tn_status tn_plan_rank(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                       const uint64_t* seeds, const double* mem_weights, double peak_flops, double peak_bytes,
+                       double* model_seconds);
 
 /* Kernels one chunk launches with the kernels chosen so far (after the first
  * tn_contract_slices call; TN_ERR_ARG before): leaf select, every
@@ -269,6 +318,14 @@ tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts* opts, int3
  * advance.  Steps that depend on no slice run once per plan or per batch and
  * are not counted.  Host only. */
 tn_status tn_plan_chunk_launches(const tn_plan_t* plan, int32_t* launches);
+
+/* Kernels the per-batch prologue launches (after the first tn_contract_slices
+ * call; TN_ERR_ARG before): the steps that depend on the closed output bits
+ * but on no slice run once for every new batch bitstring (main text, section
+ * III: the part of the network shared by a batch's slices is contracted once),
+ * each with its kernels as in tn_plan_chunk_launches, after one leaf select;
+ * 0 when the plan has no such step.  Host only. */
+tn_status tn_plan_batch_launches(const tn_plan_t* plan, int32_t* launches);
 
 /* Wait for the plan's work on `stream` and return its sticky device error, if any. */
 tn_status tn_plan_sync(tn_plan_t* plan, void* stream);
@@ -322,7 +379,9 @@ tn_status tn_permute(const float* in, float* out, int32_t rank, const int32_t* p
  * arbitrary int32 ids, listed in storage order (position 0 fastest); a wire in
  * both A and B is contracted; c_wires must be the remaining wires in any order.
  * `batch` independent instances are stored back to back in each array.
- * precision and complex_mult as in tn_plan_opts.  Asynchronous on stream. */
+ * precision and complex_mult as in tn_plan_opts.  Asynchronous on stream; a
+ * device-side error (a bounded wait of the tensor-core kernel that ran out,
+ * leaving C incomplete) is reported by the next tn_device_sync(). */
 tn_status tn_contract_pair(const float* a, const int32_t* a_wires, int32_t a_rank,
                            const float* b, const int32_t* b_wires, int32_t b_rank,
                            float* c, const int32_t* c_wires, int32_t c_rank,
@@ -332,29 +391,46 @@ tn_status tn_contract_pair(const float* a, const int32_t* a_wires, int32_t a_ran
 /* Self-test of the bounded device waits that every tensor-core kernel uses:
  * launches one thread that waits on an mbarrier nothing ever arrives on, with
  * a limit of wait_ms milliseconds (1..5000), and writes the device error word
- * the kernel left into *device_status: TN_ERR_TIMEOUT when the wait gave up as
- * designed.  The kernel returns normally and the context stays usable.  The
- * paper has no counterpart (failure handling of this implementation).
- * Synchronises `stream`. */
+ * after the kernel into *device_status: TN_ERR_TIMEOUT when the wait gave up as
+ * designed.  The word is left set, exactly as a timed-out contraction leaves
+ * it, so the next tn_device_sync() reports TN_ERR_TIMEOUT and clears it.  The
+ * kernel returns normally and the context stays usable.  The paper has no
+ * counterpart (failure handling of this implementation).  Synchronises
+ * `stream`. */
 tn_status tn_selftest_bounded_wait(int32_t wait_ms, int32_t* device_status, void* stream);
+
+/* Wait for `stream`, then read and clear the current device's error word of
+ * the calls without a plan (tn_contract_pair, tn_contract_pair_noalloc,
+ * tn_selftest_bounded_wait): TN_OK when no kernel of theirs reported an error
+ * since the last tn_device_sync, else the recorded status (TN_ERR_TIMEOUT: a
+ * bounded wait ran out and that call's output is incomplete).  The paper has
+ * no counterpart (failure handling of this implementation).  Allocates
+ * nothing, so callers of tn_contract_pair_noalloc may use it. */
+tn_status tn_device_sync(void* stream);
 
 /* tn_contract_pair without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device
- * memory -- code running while a CUDA graph is captured, allocation-free
- * real-time or embedded hosts, programs whose memory pool belongs to someone
- * else.  Arguments, layouts and results are those of tn_contract_pair (same
- * kernels); the caller still provides A, B and C.
- *   - Scratch (an error word and the B' images of the tensor-core kernels)
- *     comes from one static device array of 32 MiB compiled into the library;
- *     every GPU that loads the library holds it until the process exits.  A
- *     contraction whose scratch exceeds it (tensor-core paths: about 16 bytes
- *     per complex entry of B per batch instance, after padding k to 16 and n
- *     to 8) fails with TN_ERR_ARG before anything is launched.
+ * memory -- programs whose device memory belongs to another allocator (a
+ * framework's caching pool, a fixed budget handed out at start-up), and
+ * real-time or embedded hosts that forbid allocation once they run, because
+ * an allocation can block, fail or fragment at a time they do not control.
+ * Arguments, layouts and results are those of tn_contract_pair (same kernels,
+ * same split-K choice while the partial sums fit the array); the caller still
+ * provides A, B and C.
+ *   - Scratch (an error word, the FP16X3 operand maxima, the B' images of the
+ *     tensor-core kernels and any split-K partial sums) comes from one static
+ *     device array of 32 MiB compiled into the library; every GPU that loads
+ *     the library holds it until the process exits.  A contraction whose
+ *     scratch exceeds it even without split-K (tensor-core paths: about 16
+ *     bytes per complex entry of B per batch instance, after padding k to 16
+ *     and n to 8) fails with TN_ERR_ARG before anything is launched.
  *   - No cudaMalloc, cudaFree or allocating library routine is called.  The
  *     first call on each device looks the array's device address up (with
  *     that device current); make that first call before any stream capture.
  *   - Every call shares the array, which keeps the previous call's contents;
- *     the error word is cleared on the stream at the start of each call.
+ *     what must start at zero (the operand maxima) is cleared on the stream by
+ *     each call.  The error word is zero at load, only ever set by a kernel
+ *     that gives up a bounded wait, and read and cleared by tn_device_sync().
  *     Calls that overlap on the GPU (other streams, other threads) race on the
  *     array and must be serialised by the caller.
  * Asynchronous on stream. */

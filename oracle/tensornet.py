@@ -145,13 +145,79 @@ class CircuitNetwork:
             merges, sets = _order.best_bisection_order(base, trials=trials, seed=seed)
         else:
             raise ValueError(f"unknown order method {method!r}")
+        return merges, self._extra_slices(sets, max_log2)
+
+    def tree_order(self, leaf_of_gate: Sequence[int],
+                   step_nodes: Sequence[Tuple[int, int]]) -> List[Tuple[int, int]]:
+        """A pairwise order given by its tree shape (SI, TN section: the order is
+        a list of two-tuples): gate g belongs to group leaf_of_gate[g]; every
+        rank-1 tensor (initial state, output projector) joins the group of the
+        gate that shares its wire; each group is first contracted to one tensor
+        with the oracle's own greedy order, then the groups are merged pairwise
+        as step_nodes says (ids: groups 0..L-1, the j-th pair creates L + j).
+        Returns the merge list over this network's tensors.  Any complete
+        binary tree gives the same contraction (only rounding differs), so the
+        tree only decides speed and memory; it is checked to be complete."""
+        n, n_gates = self.n_qubits, len(leaf_of_gate)
+        n_t = len(self.legs)
+        if n + n_gates > n_t:
+            raise ValueError("more gates than the network holds")
+        group: List[Optional[int]] = [None] * n_t
+        owner: Dict[Label, List[int]] = {}
+        for g in range(n_gates):
+            group[n + g] = int(leaf_of_gate[g])
+            for leg in self.legs[n + g]:
+                owner.setdefault(leg, []).append(n + g)
+        for i in range(n_t):
+            if group[i] is None:
+                if len(self.legs[i]) != 1 or len(owner.get(self.legs[i][0], [])) != 1:
+                    raise ValueError(f"tensor {i} touches no single gate")
+                group[i] = group[owner[self.legs[i][0]][0]]
+        n_groups = max(group) + 1
+        if min(group) < 0 or set(group) != set(range(n_groups)):
+            raise ValueError("groups must be numbered 0..L-1 without gaps")
+        merges: List[Tuple[int, int]] = []
+        node_id: Dict[int, int] = {}
+        for grp in range(n_groups):
+            members = [i for i in range(n_t) if group[i] == grp]
+            sub, _ = self.greedy_order([frozenset(self.legs[i]) for i in members])
+            ids = list(members)
+            for a, b in sub:
+                merges.append((ids[a], ids[b]))
+                ids.append(n_t + len(merges) - 1)
+            node_id[grp] = ids[-1]
+        for j, (x, y) in enumerate(step_nodes):
+            if x not in node_id or y not in node_id or x == y:
+                raise ValueError(f"step {j} merges an unknown node")
+            merges.append((node_id.pop(x), node_id.pop(y)))
+            node_id[n_groups + j] = n_t + len(merges) - 1
+        used = [i for m in merges for i in m]
+        if len(merges) != n_t - 1 or len(set(used)) != len(used) or len(node_id) != 1:
+            raise ValueError("the tree does not contract every tensor exactly once")
+        return merges
+
+    def plan_along_tree(self, fixed_legs: Iterable[Label], leaf_of_gate: Sequence[int],
+                        step_nodes: Sequence[Tuple[int, int]],
+                        max_log2: int = 27) -> Tuple[List[Tuple[int, int]], List[Label]]:
+        """tree_order() plus the extra wires the oracle slices itself so that no
+        tensor of that order (with `fixed_legs` removed) exceeds 2^max_log2."""
+        merges = self.tree_order(leaf_of_gate, step_nodes)
+        fixed = set(fixed_legs)
+        sets = [frozenset(l for l in legs if l not in fixed) for legs in self.legs]
+        for a, b in merges:
+            sets.append(sets[a] ^ sets[b])
+        return merges, self._extra_slices(sets, max_log2)
+
+    def _extra_slices(self, sets: Sequence[frozenset], max_log2: int) -> List[Label]:
+        """Wires the oracle slices so that no set exceeds max_log2 legs: the
+        wire shared by most oversized sets first (never an open wire)."""
         extra: List[Label] = []
         open_set = set(self.open_legs)
         while True:
             gone = frozenset(extra)
             big = [s - gone for s in sets if len(s - gone) > max_log2]
             if not big:
-                return merges, extra
+                return extra
             counts: Dict[Label, int] = {}
             for s in big:
                 for leg in s:
@@ -204,14 +270,19 @@ class CircuitNetwork:
         return np.transpose(final, perm).reshape(-1)
 
     def contract_in_order(self, merges: Sequence[Tuple[int, int]], sliced: Sequence[Label],
-                          slice_ids: Iterable[int]) -> np.ndarray:
+                          slice_ids: Iterable[int], extra: Sequence[Label] = ()) -> np.ndarray:
         """Sum over slice ids of the network with `sliced` fixed (slice id s sets
         sliced[j] to bit j of s), contracted along a given order of this network
-        (e.g. the order plan() returned together with these wires)."""
+        (e.g. the order plan() returned together with these wires); each slice
+        is itself the sum over every value of the `extra` wires."""
         total = np.zeros(1 << len(self.open_legs), dtype=np.complex128)
         for s in slice_ids:
             s = int(s)
-            total += self._run(merges, {leg: (s >> j) & 1 for j, leg in enumerate(sliced)})
+            base = {leg: (s >> j) & 1 for j, leg in enumerate(sliced)}
+            for sub in range(1 << len(extra)):
+                values = dict(base)
+                values.update({leg: (sub >> j) & 1 for j, leg in enumerate(extra)})
+                total += self._run(merges, values)
         return total
 
     def contract(self, sliced: Sequence[Label] = (), slice_ids: Optional[Iterable[int]] = None,

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <array>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -230,7 +231,8 @@ static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
 // epi_mode: -1 chooses the write-back by the coalesced run lengths, 0 forces
 // direct per-column stores, 1 the staged order (where the tile allows it)
 static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_lin, int64_t c_total = 0,
-                              bool allow_split = false, int epi_mode = -1) {
+                              bool allow_split = false, int epi_mode = -1,
+                              int64_t split_cap_bytes = (int64_t)256 << 20) {
   StepLaunch L;
   L.kid = kid;
   L.g = g;
@@ -255,7 +257,7 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
     int sp = 1;
     // enough tiles for several waves (tail below ~15%), each split >= 4 k chunks
     while (sp < 32 && t.n_tiles * sp * 2 <= 8 * (int64_t)sm_count() && t.n_kc / (sp * 2) >= 4) sp *= 2;
-    if (sp > 1 && (int64_t)sp * c_total * 8 <= ((int64_t)256 << 20)) {
+    if (sp > 1 && (int64_t)sp * c_total * 8 <= split_cap_bytes) {
       t.n_split = sp;
       t.c_part_stride = c_total;
       L.split_off = (L.ws_bytes + 255) / 256 * 256;
@@ -313,10 +315,16 @@ static void launch_tc(const TcArgs& t, const StepLaunch& L, int grid, cudaStream
     k_tc_prep_b<MODE><<<pgrid, 256, 0, s>>>(t);
   else
     k_tc_prep_b3<MODE><<<pgrid, 256, 0, s>>>(t);
-  static bool attr = false;
-  if (!attr) {
+  // the shared-memory opt-in is a per-device function attribute: one bit per
+  // device (ids < 64) records that it was set there; two threads racing on the
+  // same bit both set the same value, which is harmless
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const uint64_t bit = dev < 64 ? (1ULL << dev) : 0;
+  if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
     CK(cudaFuncSetAttribute(k_cgemm_tc<MODE, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr = true;
+    attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   k_cgemm_tc<MODE, CM><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
 }
@@ -790,15 +798,14 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   API_END
 }
 
-extern "C" tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
-                                    uint64_t bitstring, void* stream, tn_plan_t** out, double* cand_seconds) {
-  API_BEGIN
-  if (!net || !opts || !out) fail(TN_ERR_ARG, "tn_plan_select: NULL argument");
-  if (n_candidates < 1 || n_candidates > 1024) fail(TN_ERR_ARG, "tn_plan_select: n_candidates must be in [1, 1024]");
+// Time one chunk of every candidate (seed and memory weight per candidate, the
+// rest from *opts) after an untimed warm-up chunk, and keep the plan whose
+// estimate for all 2^S slices is smallest.
+static void select_among(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                         const uint64_t* seeds, const double* weights, uint64_t bitstring, void* stream,
+                         tn_plan_t** out, double* cand_seconds) {
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
-  const double w0 = opts->mem_weight > 0.0 ? opts->mem_weight : 32.0;
-  const double wmul[3] = {1.0, 0.25, 4.0};
   tn_plan_t* best = nullptr;
   double best_t = 0.0;
   double* amps = nullptr;
@@ -809,8 +816,8 @@ extern "C" tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts*
   for (int i = 0; i < n_candidates; ++i) {
     if (cand_seconds) cand_seconds[i] = -1.0;
     tn_plan_opts o = *opts;
-    o.seed = opts->seed + (uint64_t)i;
-    o.mem_weight = w0 * wmul[i % 3];
+    o.seed = seeds[i];
+    o.mem_weight = weights[i];
     tn_plan_t* h = nullptr;
     if (tn_plan(net, &o, &h) != TN_OK || !h) continue;
     Plan& p = h->plan;
@@ -823,16 +830,22 @@ extern "C" tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts*
       amps_bytes = need;
     }
     double est = -1.0;
-    // warm-up (device state, prologues, graph capture), then one timed chunk
+    // warm-up (device state, prologues, graph capture), then the fastest of
+    // three timed chunks
     if (tn_contract_slices(h, 0, chunk, &bitstring, 1, amps, s) == TN_OK) {
-      CK(cudaEventRecord(e0, s));
-      const tn_status st = tn_contract_slices(h, 0, chunk, &bitstring, 1, amps, s);
-      CK(cudaEventRecord(e1, s));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
+      float best_ms = -1.f;
+      tn_status st = TN_OK;
+      for (int r = 0; r < 3 && st == TN_OK; ++r) {
+        CK(cudaEventRecord(e0, s));
+        st = tn_contract_slices(h, 0, chunk, &bitstring, 1, amps, s);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best_ms < 0.f || ms < best_ms) best_ms = ms;
+      }
       if (st == TN_OK && tn_plan_sync(h, s) == TN_OK)
-        est = (double)ms / 1e3 * std::ldexp(1.0, (int)p.sliced.size() - p.log2_batch);
+        est = (double)best_ms / 1e3 * std::ldexp(1.0, (int)p.sliced.size() - p.log2_batch);
     }
     CK(cudaStreamSynchronize(s));
     destroy_device_state(&p);
@@ -850,9 +863,39 @@ extern "C" tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts*
   if (amps) cudaFree(amps);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!best) fail(TN_ERR_PLAN, "tn_plan_select: no candidate plan could be built and run");
+  if (!best) fail(TN_ERR_PLAN, "plan selection: no candidate plan could be built and run");
   best->plan.sticky = TN_OK;
   *out = best;
+}
+
+extern "C" tn_status tn_plan_select(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                                    uint64_t bitstring, void* stream, tn_plan_t** out, double* cand_seconds) {
+  API_BEGIN
+  if (!net || !opts || !out) fail(TN_ERR_ARG, "tn_plan_select: NULL argument");
+  if (n_candidates < 1 || n_candidates > 1024) fail(TN_ERR_ARG, "tn_plan_select: n_candidates must be in [1, 1024]");
+  const double w0 = opts->mem_weight > 0.0 ? opts->mem_weight : 32.0;
+  const double wmul[3] = {1.0, 0.25, 4.0};
+  std::vector<uint64_t> seeds(n_candidates);
+  std::vector<double> weights(n_candidates);
+  for (int i = 0; i < n_candidates; ++i) {
+    seeds[i] = opts->seed + (uint64_t)i;
+    weights[i] = w0 * wmul[i % 3];
+  }
+  select_among(net, opts, n_candidates, seeds.data(), weights.data(), bitstring, stream, out, cand_seconds);
+  API_END
+}
+
+extern "C" tn_status tn_plan_select_list(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                                         const uint64_t* seeds, const double* mem_weights, uint64_t bitstring,
+                                         void* stream, tn_plan_t** out, double* cand_seconds) {
+  API_BEGIN
+  if (!net || !opts || !out || !seeds || !mem_weights) fail(TN_ERR_ARG, "tn_plan_select_list: NULL argument");
+  if (n_candidates < 1 || n_candidates > 1024)
+    fail(TN_ERR_ARG, "tn_plan_select_list: n_candidates must be in [1, 1024]");
+  for (int i = 0; i < n_candidates; ++i)
+    if (!(mem_weights[i] <= 0.0 || (mem_weights[i] >= 1e-6 && mem_weights[i] <= 1e9)))
+      fail(TN_ERR_ARG, "tn_plan_select_list: mem_weight must be <= 0 (default) or in [1e-6, 1e9]");
+  select_among(net, opts, n_candidates, seeds, mem_weights, bitstring, stream, out, cand_seconds);
   API_END
 }
 
@@ -868,6 +911,21 @@ extern "C" tn_status tn_plan_chunk_launches(const tn_plan_t* h, int32_t* launche
     n += is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
   }
   *launches = n;
+  API_END
+}
+
+extern "C" tn_status tn_plan_batch_launches(const tn_plan_t* h, int32_t* launches) {
+  API_BEGIN
+  if (!h || !launches) fail(TN_ERR_ARG, "tn_plan_batch_launches: NULL argument");
+  const Plan& p = h->plan;
+  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_batch_launches: call after the first tn_contract_slices");
+  int n = 0;
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    if (p.steps[i].dep_flags != 2) continue;
+    const StepLaunch& L = p.dev->launches[i];
+    n += is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
+  }
+  *launches = n > 0 ? n + 1 : 0;   // + the leaf select ahead of them
   API_END
 }
 
@@ -915,13 +973,13 @@ struct Scratch {
   uint8_t* ws = nullptr;
   int64_t ws_bytes = 0;
 };
+static std::mutex g_scratch_mu;
+static std::unordered_map<int, Scratch> g_scratch;   // per device
 static Scratch& scratch_for_device() {
-  static std::mutex mu;
-  static std::unordered_map<int, Scratch> m;
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(mu);
-  Scratch& s = m[dev];
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  Scratch& s = g_scratch[dev];
   if (!s.xeb) {
     CK(cudaMalloc(&s.xeb, sizeof(double)));
     CK(cudaMalloc(&s.err, sizeof(int32_t)));
@@ -1137,14 +1195,12 @@ extern "C" tn_status tn_selftest_bounded_wait(int32_t wait_ms, int32_t* device_s
   if (wait_ms < 1 || wait_ms > 5000) fail(TN_ERR_ARG, "tn_selftest_bounded_wait: wait_ms must be in [1, 5000]");
   Scratch& sc = scratch_for_device();
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemsetAsync(sc.err, 0, sizeof(int32_t), s));
   k_selftest_wait<<<1, 32, 0, s>>>(sc.err, (uint64_t)wait_ms * 1000000ull);
   CK(cudaGetLastError());
   int32_t e = 0;
   CK(cudaMemcpyAsync(&e, sc.err, sizeof(e), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  CK(cudaMemsetAsync(sc.err, 0, sizeof(int32_t), s));
-  *device_status = e;
+  *device_status = e;   // the word stays set until tn_device_sync reads it
   API_END
 }
 
@@ -1160,19 +1216,20 @@ constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB
 constexpr size_t kNoAllocErrBytes = 256;                     // error word, then the B' images
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
+static std::mutex g_noalloc_mu;
+static std::unordered_map<int, void*> g_noalloc_addr;   // per device, found once with that device current
+
 static void* noalloc_scratch_address() {
-  static std::mutex mu;
-  static std::unordered_map<int, void*> addr;   // per device, found once with that device current
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(mu);
-  auto it = addr.find(dev);
-  if (it != addr.end()) return it->second;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(dev);
+  if (it != g_noalloc_addr.end()) return it->second;
   void* p = nullptr;
   const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess || !p)
     fail(TN_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") + cudaGetErrorString(e));
-  addr[dev] = p;
+  g_noalloc_addr[dev] = p;
   return p;
 }
 
@@ -1241,15 +1298,60 @@ extern "C" tn_status tn_contract_pair_noalloc(const float* a, const int32_t* aw,
     g.amax_a = amax;
     g.amax_b = amax + 1;
   }
-  StepLaunch L = make_launch(g, kid, ar, batch);
+  // split-K as tn_contract_pair chooses it, as long as the partial sums fit
+  // beside the B' images; otherwise one pass over k
+  StepLaunch L = make_launch(g, kid, ar, batch, batch * d.c_elems, true, -1, cap);
+  if (L.ws_bytes > cap) L = make_launch(g, kid, ar, batch);
   if (L.ws_bytes > cap)
     fail(TN_ERR_ARG, "tn_contract_pair_noalloc: this contraction needs " + std::to_string(L.ws_bytes) +
                          " bytes of scratch; the static array holds " + std::to_string(cap));
-  CK(cudaMemsetAsync(err, 0, sizeof(int32_t), s));   // the array keeps the last call's contents
+  // the error word is zero when the library loads and is cleared by
+  // tn_device_sync; kernels only ever set it, so it is not cleared here
   if (g.amax_a)
     operand_maxima(reinterpret_cast<const float2*>(a), batch << ar, reinterpret_cast<const float2*>(b),
                    batch << br, amax, s);
   launch_step(L, base + kNoAllocErrBytes, err, s);
   CK(cudaGetLastError());
+  API_END
+}
+
+// ---------------------------------------------------------------- device error word
+// Calls without a plan (tn_contract_pair, tn_contract_pair_noalloc,
+// tn_selftest_bounded_wait) leave device-side errors in a per-device word: the
+// scratch area's word, and the first word of the static array of the
+// no-allocation entry point.  This reads both, clears what was set, and
+// allocates nothing: a word that was never created cannot hold an error.
+extern "C" tn_status tn_device_sync(void* stream) {
+  API_BEGIN
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int32_t* words[2] = {nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    auto it = g_scratch.find(dev);
+    if (it != g_scratch.end()) words[0] = it->second.err;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) words[1] = static_cast<int32_t*>(it->second);
+  }
+  int32_t val[2] = {0, 0};
+  for (int i = 0; i < 2; ++i)
+    if (words[i]) CK(cudaMemcpyAsync(&val[i], words[i], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int32_t e = 0;
+  for (int i = 0; i < 2; ++i)
+    if (val[i] != 0) {
+      CK(cudaMemsetAsync(words[i], 0, sizeof(int32_t), s));
+      if (e == 0) e = val[i];
+    }
+  if (e != 0) {
+    CK(cudaStreamSynchronize(s));
+    const tn_status code = (e == TN_ERR_TIMEOUT || e == TN_ERR_DEVICE || e == TN_ERR_ARG) ? e : TN_ERR_DEVICE;
+    fail(code, "a device kernel of a call without a plan reported error " + std::to_string(e) +
+                   (e == TN_ERR_TIMEOUT ? " (a bounded wait expired; its result is incomplete)" : ""));
+  }
   API_END
 }

@@ -114,6 +114,7 @@ struct Plan {
   std::vector<LeafDesc> leaves;
   std::vector<float> leaf_amax;        // largest |re|, |im| of each leaf's data (FP16 scaling)
   std::vector<StepDesc> steps;
+  std::vector<std::vector<int>> leaf_gates;   // per leaf: circuit gates absorbed into it
   RootDesc root{};
   int64_t arena_elems = 0;
   PlanStats stats;

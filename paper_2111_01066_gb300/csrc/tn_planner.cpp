@@ -38,6 +38,7 @@ double pow2(int e) { return std::ldexp(1.0, e); }
 struct Simplified {
   std::vector<HTensor> leaves;   // wires: planning wires first, then fixed wires
   std::vector<char> fixed;       // per network wire id
+  std::vector<std::vector<int>> gates;   // per leaf: the circuit gates absorbed into it
 };
 
 Simplified simplify(const Network& net, uint64_t open_mask, const std::vector<int>& forced) {
@@ -45,6 +46,8 @@ Simplified simplify(const Network& net, uint64_t open_mask, const std::vector<in
   const int n = net.n_qubits;
   const int nw = (int)net.labels.size();
   std::vector<HTensor> ts = net.gates;
+  std::vector<std::vector<int>> members(ts.size());   // circuit gates held by each tensor
+  for (size_t g = 0; g < ts.size(); ++g) members[g] = {(int)g};
   // initial state |0> on every input wire
   for (int q = 0; q < n; ++q) {
     const int w = net.input_wire[q];
@@ -53,6 +56,7 @@ Simplified simplify(const Network& net, uint64_t open_mask, const std::vector<in
       t.wires = {w};
       t.data = {cd(1, 0), cd(0, 0)};
       ts.push_back(std::move(t));
+      members.emplace_back();
       continue;
     }
     for (auto& t : ts)
@@ -107,6 +111,7 @@ Simplified simplify(const Network& net, uint64_t open_mask, const std::vector<in
         if (best < 0) continue;
       }
       ts[best] = hcontract(ts[best], ts[i], &out.fixed);
+      members[best].insert(members[best].end(), members[i].begin(), members[i].end());
       alive[i] = 0;
       changed = true;
       own = owners();
@@ -130,6 +135,7 @@ Simplified simplify(const Network& net, uint64_t open_mask, const std::vector<in
       const int rc = (int)uni.size() - shared;
       if (rc <= std::max(prank(ts[a]), prank(ts[b]))) {
         ts[a] = hcontract(ts[a], ts[b], &out.fixed);
+        members[a].insert(members[a].end(), members[b].begin(), members[b].end());
         alive[b] = 0;
         changed = true;
         own = owners();
@@ -144,6 +150,8 @@ Simplified simplify(const Network& net, uint64_t open_mask, const std::vector<in
     for (int w : ts[i].wires)
       if (out.fixed[w]) order.push_back(w);
     out.leaves.push_back(hpermute(ts[i], order));
+    std::sort(members[i].begin(), members[i].end());
+    out.gates.push_back(members[i]);
   }
   return out;
 }
@@ -596,6 +604,7 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   Simplified S = simplify(net, o.open_mask, forced);
   const int L = (int)S.leaves.size();
   P->n_leaves = L;
+  P->leaf_gates = S.gates;
 
   // planning wire numbering
   std::vector<int> pw_of(net.labels.size(), -1);
@@ -1179,7 +1188,6 @@ extern "C" tn_status tn_plan_default_opts(tn_plan_opts* o) {
   o->complex_mult = 4;
   o->log2_batch_slices = 0;
   o->max_arena_bytes = (int64_t)96 << 30;
-  o->fuse_permute = 1;
   o->mem_weight = 0.0;
   return TN_OK;
 }
@@ -1302,6 +1310,15 @@ extern "C" tn_status tn_plan_step_layout(const tn_plan_t* h, int32_t step, int32
   return TN_OK;
 }
 
+// Roofline time of one step over its batch instances: max(flops / peak,
+// bytes / bandwidth), 8 flops per complex multiply-add, every operand read or
+// written once as complex64.
+static double step_model_seconds(const StepDesc& d, double peak_flops, double peak_bytes) {
+  const double flops = 8.0 * std::ldexp(1.0, d.nm + d.nk + d.nn + d.nb);
+  const double bytes = 8.0 * ((double)d.a_elems + (double)d.b_elems + (double)d.c_elems);
+  return std::max(flops / peak_flops, bytes / peak_bytes);
+}
+
 extern "C" tn_status tn_plan_model_time(const tn_plan_t* h, double peak_flops, double peak_bytes,
                                         double* seconds) {
   clear_error();
@@ -1314,13 +1331,88 @@ extern "C" tn_status tn_plan_model_time(const tn_plan_t* h, double peak_flops, d
     return TN_ERR_ARG;
   }
   double t = 0.0;
-  for (const StepDesc& d : h->plan.steps) {
-    if ((d.dep_flags & 1) == 0) continue;
-    const double flops = 8.0 * std::ldexp(1.0, d.nm + d.nk + d.nn + d.nb);
-    const double bytes = 8.0 * ((double)d.a_elems + (double)d.b_elems + (double)d.c_elems);
-    t += std::max(flops / peak_flops, bytes / peak_bytes);
-  }
+  for (const StepDesc& d : h->plan.steps)
+    if (d.dep_flags & 1) t += step_model_seconds(d, peak_flops, peak_bytes);
   *seconds = t;
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_rank(const tn_network_t* net, const tn_plan_opts* opts, int32_t n_candidates,
+                                  const uint64_t* seeds, const double* mem_weights, double peak_flops,
+                                  double peak_bytes, double* model_seconds) {
+  clear_error();
+  if (!net || !opts || !seeds || !mem_weights || !model_seconds) {
+    set_error("tn_plan_rank: NULL argument");
+    return TN_ERR_ARG;
+  }
+  if (n_candidates < 1 || n_candidates > 100000) {
+    set_error("tn_plan_rank: n_candidates must be in [1, 100000]");
+    return TN_ERR_ARG;
+  }
+  if (!(peak_flops > 0.0) || !(peak_bytes > 0.0) || !std::isfinite(peak_flops) || !std::isfinite(peak_bytes)) {
+    set_error("tn_plan_rank: peaks must be positive and finite");
+    return TN_ERR_ARG;
+  }
+  for (int i = 0; i < n_candidates; ++i)
+    if (!(mem_weights[i] <= 0.0 || (mem_weights[i] >= 1e-6 && mem_weights[i] <= 1e9))) {
+      set_error("tn_plan_rank: mem_weight must be <= 0 (default) or in [1e-6, 1e9]");
+      return TN_ERR_ARG;
+    }
+  int built = 0;
+  for (int i = 0; i < n_candidates; ++i) {
+    model_seconds[i] = -1.0;
+    tn_plan_opts o = *opts;
+    o.seed = seeds[i];
+    o.mem_weight = mem_weights[i];
+    tn_plan_t* h = nullptr;
+    if (tn_plan(net, &o, &h) != TN_OK || !h) continue;   // e.g. no batch fits the arena cap
+    double chunk = 0.0;
+    if (tn_plan_model_time(h, peak_flops, peak_bytes, &chunk) == TN_OK) {
+      // one batch: every chunk, plus the steps that run once per batch bitstring
+      double per_batch = 0.0;
+      for (const StepDesc& d : h->plan.steps)
+        if (d.dep_flags == 2) per_batch += step_model_seconds(d, peak_flops, peak_bytes);
+      model_seconds[i] = chunk * std::ldexp(1.0, (int)h->plan.sliced.size() - h->plan.log2_batch) + per_batch;
+    }
+    ++built;
+    tn_plan_destroy(h);
+  }
+  clear_error();
+  if (built == 0) {
+    set_error("tn_plan_rank: no candidate plan could be built");
+    return TN_ERR_PLAN;
+  }
+  return TN_OK;
+}
+
+extern "C" tn_status tn_plan_tree(const tn_plan_t* h, int32_t* leaf_of_gate, int32_t n_gates, int32_t* step_nodes,
+                                  int32_t cap_steps, int32_t* n_leaves, int32_t* n_steps) {
+  clear_error();
+  if (!h || !leaf_of_gate || !step_nodes || !n_leaves || !n_steps) {
+    set_error("tn_plan_tree: NULL argument");
+    return TN_ERR_ARG;
+  }
+  const Plan& p = h->plan;
+  int max_gate = -1;
+  for (const auto& v : p.leaf_gates)
+    for (int g : v) max_gate = std::max(max_gate, g);
+  if (n_gates <= max_gate || n_gates < 0) {
+    set_error("tn_plan_tree: n_gates is smaller than the circuit's gate count");
+    return TN_ERR_ARG;
+  }
+  *n_leaves = (int32_t)p.leaf_gates.size();
+  *n_steps = (int32_t)p.steps.size();
+  if (cap_steps < (int32_t)p.steps.size()) {
+    set_error("tn_plan_tree: cap_steps smaller than the plan's step count");
+    return TN_ERR_ARG;
+  }
+  for (int g = 0; g < n_gates; ++g) leaf_of_gate[g] = -1;
+  for (size_t l = 0; l < p.leaf_gates.size(); ++l)
+    for (int g : p.leaf_gates[l]) leaf_of_gate[g] = (int32_t)l;
+  for (size_t j = 0; j < p.steps.size(); ++j) {
+    step_nodes[2 * j] = p.steps[j].a_node;
+    step_nodes[2 * j + 1] = p.steps[j].b_node;
+  }
   return TN_OK;
 }
 

@@ -48,8 +48,7 @@ class tn_plan_opts(ctypes.Structure):
                 ("min_log2_slices", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("trials", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("complex_mult", ctypes.c_int32), ("log2_batch_slices", ctypes.c_int32),
-                ("max_arena_bytes", ctypes.c_int64), ("fuse_permute", ctypes.c_int32),
-                ("n_forced_slices", ctypes.c_int32),
+                ("max_arena_bytes", ctypes.c_int64), ("n_forced_slices", ctypes.c_int32),
                 ("forced_slice_qubit", ctypes.POINTER(ctypes.c_int32)),
                 ("forced_slice_t", ctypes.POINTER(ctypes.c_int32)),
                 ("mem_weight", ctypes.c_double)]
@@ -85,7 +84,18 @@ _SIGS = {
     "tn_plan_select": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tn_plan_opts), ctypes.c_int32,
                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_double)]),
+    "tn_plan_select_list": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tn_plan_opts), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "tn_plan_rank": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tn_plan_opts), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "tn_plan_tree": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_chunk_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "tn_plan_batch_launches": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
     "tn_plan_model_time": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(ctypes.c_double)]),
     "tn_plan_step_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
@@ -107,6 +117,7 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                         ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "tn_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "tn_device_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "tn_contract_pair_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                                 ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
@@ -189,7 +200,7 @@ def default_opts() -> tn_plan_opts:
 
 
 def _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed, trials,
-               log2_batch_slices, max_arena_bytes, fuse_permute, forced_slices, mem_weight):
+               log2_batch_slices, max_arena_bytes, forced_slices, mem_weight):
     o = default_opts()
     o.open_mask = open_mask
     o.max_log2_intermediate = max_log2_intermediate
@@ -201,7 +212,6 @@ def _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, com
     o.log2_batch_slices = log2_batch_slices
     if max_arena_bytes:
         o.max_arena_bytes = max_arena_bytes
-    o.fuse_permute = fuse_permute
     fq = _i32([q for q, _ in forced_slices])
     ft = _i32([t for _, t in forced_slices])
     o.n_forced_slices = len(forced_slices)
@@ -217,7 +227,7 @@ class Plan:
     def __init__(self, network: Network, open_mask: int = 0, max_log2_intermediate: int = 30,
                  min_log2_slices: int = 0, precision: str = "fp32", complex_mult: int = 4,
                  seed: int = 1, trials: int = 64, log2_batch_slices: int = 0,
-                 max_arena_bytes: int = 0, fuse_permute: int = 1,
+                 max_arena_bytes: int = 0,
                  forced_slices: Sequence[Tuple[int, int]] = (), mem_weight: float = 0.0,
                  _handle=None):
         self.network = network
@@ -226,7 +236,7 @@ class Plan:
             self.handle = _handle
             return
         o, keep = _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed,
-                             trials, log2_batch_slices, max_arena_bytes, fuse_permute, forced_slices, mem_weight)
+                             trials, log2_batch_slices, max_arena_bytes, forced_slices, mem_weight)
         h = ctypes.c_void_p()
         _check(load().tn_plan(network.handle, ctypes.byref(o), ctypes.byref(h)))
         self.handle = h
@@ -272,6 +282,16 @@ class Plan:
         out["dep_flags"] = v[pos]
         return out
 
+    def tree(self, n_gates: int) -> Tuple[List[int], List[Tuple[int, int]]]:
+        """tn_plan_tree: (leaf of every circuit gate, the two node ids of every
+        step in execution order; leaves first, step j creates node n_leaves + j)."""
+        n_steps = self.info()["n_steps"]
+        log = (ctypes.c_int32 * max(1, n_gates))()
+        nodes = (ctypes.c_int32 * max(2, 2 * n_steps))()
+        nl, ns = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().tn_plan_tree(self.handle, log, n_gates, nodes, n_steps, ctypes.byref(nl), ctypes.byref(ns)))
+        return list(log[:n_gates]), [(nodes[2 * j], nodes[2 * j + 1]) for j in range(ns.value)]
+
     def model_time(self, peak_flops: float, peak_bytes: float) -> float:
         """tn_plan_model_time: modeled seconds of one chunk on a roofline
         (peak_flops in algorithmic flop/s, peak_bytes in B/s)."""
@@ -283,6 +303,12 @@ class Plan:
         """Kernels one chunk launches with the kernels chosen so far (after the first contract call)."""
         n = ctypes.c_int32()
         _check(load().tn_plan_chunk_launches(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def batch_launches(self) -> int:
+        """Kernels the per-batch prologue launches for a new bitstring (after the first contract call)."""
+        n = ctypes.c_int32()
+        _check(load().tn_plan_batch_launches(self.handle, ctypes.byref(n)))
         return n.value
 
     def contract_slices(self, slice_first: int, slice_count: int, bitstrings: Sequence[int],
@@ -332,6 +358,24 @@ def selftest_bounded_wait(wait_ms: int = 200, stream=None) -> int:
     return st.value
 
 
+def device_sync(stream=None) -> None:
+    """tn_device_sync: wait for the stream and raise TnError if a kernel of a
+    call without a plan reported an error since the last call (the word is
+    cleared)."""
+    _check(load().tn_device_sync(_stream_handle(stream)))
+
+
+def contract_pair_noalloc(a, a_wires, b, b_wires, c, c_wires, batch: int = 1, precision: str = "fp32",
+                          complex_mult: int = 4, stream=None) -> None:
+    """tn_contract_pair_noalloc on complex64 CUDA tensors (scratch from the
+    library's static device array; nothing is allocated)."""
+    p = PREC[precision] if isinstance(precision, str) else int(precision)
+    _check(load().tn_contract_pair_noalloc(ctypes.c_void_p(a.data_ptr()), _i32(a_wires), len(a_wires),
+                                           ctypes.c_void_p(b.data_ptr()), _i32(b_wires), len(b_wires),
+                                           ctypes.c_void_p(c.data_ptr()), _i32(c_wires), len(c_wires),
+                                           batch, p, complex_mult, _stream_handle(stream)))
+
+
 def permute(inp, out, rank: int, perm: Sequence[int], batch: int = 1, stream=None) -> None:
     """tn_permute on complex64 CUDA tensors."""
     _check(load().tn_permute(ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()), rank,
@@ -365,14 +409,55 @@ def frugal_sample(amplitudes, n_qubits: int, m_bound: float, candidates, uniform
 def select_plan(network: Network, n_candidates: int, bitstring: int, stream=None, open_mask: int = 0,
                 max_log2_intermediate: int = 30, min_log2_slices: int = 0, precision: str = "fp32",
                 complex_mult: int = 4, seed: int = 1, trials: int = 64, log2_batch_slices: int = 0,
-                max_arena_bytes: int = 0, fuse_permute: int = 1, forced_slices: Sequence[Tuple[int, int]] = (),
+                max_arena_bytes: int = 0, forced_slices: Sequence[Tuple[int, int]] = (),
                 mem_weight: float = 0.0) -> Tuple["Plan", List[float]]:
     """tn_plan_select: the fastest of n_candidates plans by measured chunk time;
     returns the plan and every candidate's estimated seconds for all slices."""
     o, keep = _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed, trials,
-                         log2_batch_slices, max_arena_bytes, fuse_permute, forced_slices, mem_weight)
+                         log2_batch_slices, max_arena_bytes, forced_slices, mem_weight)
     h = ctypes.c_void_p()
     est = (ctypes.c_double * n_candidates)()
     _check(load().tn_plan_select(network.handle, ctypes.byref(o), n_candidates, bitstring,
                                  _stream_handle(stream), ctypes.byref(h), est))
+    return Plan(network, open_mask=open_mask, _handle=h), list(est)
+
+
+def rank_plans(network: Network, seeds: Sequence[int], mem_weights: Sequence[float], peak_flops: float,
+               peak_bytes: float, open_mask: int = 0, max_log2_intermediate: int = 30, min_log2_slices: int = 0,
+               precision: str = "fp32", complex_mult: int = 4, trials: int = 64, log2_batch_slices: int = 0,
+               max_arena_bytes: int = 0, forced_slices: Sequence[Tuple[int, int]] = ()) -> List[float]:
+    """tn_plan_rank: modeled seconds for all slices of every candidate (seed,
+    memory weight), -1 where a candidate cannot be planned (host only)."""
+    n = len(seeds)
+    if n != len(mem_weights):
+        raise ValueError("seeds and mem_weights differ in length")
+    o, keep = _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, 1, trials,
+                         log2_batch_slices, max_arena_bytes, forced_slices, 0.0)
+    sd = (ctypes.c_uint64 * n)(*[int(x) for x in seeds])
+    wt = (ctypes.c_double * n)(*[float(x) for x in mem_weights])
+    out = (ctypes.c_double * n)()
+    _check(load().tn_plan_rank(network.handle, ctypes.byref(o), n, sd, wt, float(peak_flops), float(peak_bytes),
+                               out))
+    return list(out)
+
+
+def select_plan_list(network: Network, seeds: Sequence[int], mem_weights: Sequence[float], bitstring: int,
+                     stream=None, open_mask: int = 0, max_log2_intermediate: int = 30, min_log2_slices: int = 0,
+                     precision: str = "fp32", complex_mult: int = 4, trials: int = 64, log2_batch_slices: int = 0,
+                     max_arena_bytes: int = 0, forced_slices: Sequence[Tuple[int, int]] = ()
+                     ) -> Tuple["Plan", List[float]]:
+    """tn_plan_select_list: the fastest of the given candidates (seed, memory
+    weight) by measured chunk time; returns the plan and every candidate's
+    estimated seconds for all slices (-1: could not run)."""
+    n = len(seeds)
+    if n != len(mem_weights):
+        raise ValueError("seeds and mem_weights differ in length")
+    o, keep = _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, 1, trials,
+                         log2_batch_slices, max_arena_bytes, forced_slices, 0.0)
+    sd = (ctypes.c_uint64 * n)(*[int(x) for x in seeds])
+    wt = (ctypes.c_double * n)(*[float(x) for x in mem_weights])
+    est = (ctypes.c_double * n)()
+    h = ctypes.c_void_p()
+    _check(load().tn_plan_select_list(network.handle, ctypes.byref(o), n, sd, wt, bitstring,
+                                      _stream_handle(stream), ctypes.byref(h), est))
     return Plan(network, open_mask=open_mask, _handle=h), list(est)

@@ -42,7 +42,7 @@ import numpy as np
 __all__ = [
     "sqrt_x", "sqrt_y", "sqrt_w", "fsim", "Circuit", "sycamore_style",
     "PATTERN_SEQUENCE", "pattern_pairs", "cycle_patterns", "CONFIGS",
-    "config_circuit", "random_bits", "slice_sample",
+    "config_circuit", "random_bits", "slice_sample", "timed_block_first",
 ]
 
 _S = math.sqrt(2.0) / 2.0
@@ -255,6 +255,16 @@ def slice_sample(n_slices_log2: int, count: int, seed: int) -> np.ndarray:
             got.update(int(x) for x in rng.integers(0, total, size=count - len(got)))
         ids = np.array(sorted(got)[:count])
     return np.sort(np.asarray(ids, dtype=np.uint64))
+
+
+def timed_block_first(n_slices_log2: int, block: int, seed: int) -> int:
+    """First slice id of a seeded aligned block of `block` consecutive slice ids
+    (block a power of two) in [0, 2^n_slices_log2): block index uniform,
+    drawn from a generator keyed by (seed, 13); 0 when the block covers all."""
+    total = 1 << n_slices_log2
+    if block >= total:
+        return 0
+    return int(np.random.default_rng([seed, 13]).integers(total // block)) * block
 
 
 # The synthetic workloads: grid, cycles, seed, removed sites, open qubits, bound.

@@ -4,11 +4,16 @@ Calls only `oracle/` (and the seeded generator `rqcgen`).  Output: one text file
 per workload, `<name>_amplitudes.txt`, with a header line and one amplitude per
 line ("re im", 17 significant digits), in the batch order sum_j b(open_j) 2^j.
 
-    python tests/golden/make_golden.py c2 c3 c5
+    python tests/golden/make_golden.py c2 c3 c5 c5block c3order
 
 With the amplitudes of c2 and c3 it also writes `<name>_xeb.txt`, their linear
-XEB computed by the oracle.
+XEB computed by the oracle.  "c5block" writes the partial sums over the first
+slices of each candidate plan's timed block (the plan parameters are read as
+data from `c5_block_plans.json`, written by make_plan_data.py); "c3order"
+stores the oracle's own contraction order for the 42-qubit batch, so that the
+oracle can be timed without re-planning.
 """
+import json
 import os
 import sys
 import time
@@ -74,6 +79,79 @@ def read_sliced(name: str):
     return wires, n, data[:, 0] + 1j * data[:, 1]
 
 
+def write_block(name: str) -> None:
+    """For every candidate plan in <name>_block_plans.json: the FP64 sum over
+    slice ids block_first .. block_first + check_slices - 1 of the network with
+    the candidate's sliced wires fixed (slice id s sets wire j to bit j of s),
+    contracted by the oracle along an order it builds from the candidate's tree
+    shape (tensornet.CircuitNetwork.tree_order), sub-sliced by the oracle
+    itself under 2^27 entries."""
+    with open(os.path.join(HERE, f"{name}_block_plans.json")) as f:
+        data = json.load(f)
+    circ, open_mask, closed = rqcgen.config_circuit(name)
+    assert data["closed_bits"] == closed and data["open_mask"] == open_mask
+    net = tensornet.CircuitNetwork(circ, closed, open_mask)
+    path = os.path.join(HERE, f"{name}_block_amplitudes.txt")
+    with open(path, "w") as f:
+        f.write(f"# {name}: n={circ.n_qubits} open_mask={open_mask:#x} closed={closed:#x} oracle=tensornet complex128; "
+                f"per candidate plan: partial sum over its first timed slices\n")
+        for c in data["candidates"]:
+            wires = [tuple(w) for w in c["sliced_wires"]]
+            t0 = time.time()
+            merges, extra = net.plan_along_tree(wires, c["leaf_of_gate"], [tuple(p) for p in c["step_nodes"]],
+                                                max_log2=27)
+            ids = range(c["block_first"], c["block_first"] + c["check_slices"])
+            amps = net.contract_in_order(merges, wires, ids, extra)
+            dt = time.time() - t0
+            f.write(f"# candidate seed={c['seed']} mem_weight={c['mem_weight']} slices={ids.start}..{ids.stop - 1} "
+                    f"count={amps.size} extra={len(extra)} ({dt:.1f} s)\n")
+            f.write("# wires " + " ".join(f"{q},{t}" for q, t in wires) + "\n")
+            for a in amps:
+                f.write(f"{a.real:.17e} {a.imag:.17e}\n")
+            print(f"seed {c['seed']} w {c['mem_weight']}: {dt:.1f} s", flush=True)
+    print(path)
+
+
+def read_block(name: str) -> dict:
+    """{(seed, mem_weight): (wires, first slice id, slice count, amplitudes)}."""
+    path = os.path.join(HERE, f"{name}_block_amplitudes.txt")
+    out = {}
+    cur = None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# candidate"):
+                kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+                lo, hi = (int(x) for x in kv["slices"].split(".."))
+                cur = {"key": (int(kv["seed"]), float(kv["mem_weight"])), "first": lo, "count": hi - lo + 1,
+                       "amps": []}
+                out[cur["key"]] = cur
+            elif line.startswith("# wires") and cur is not None:
+                cur["wires"] = [tuple(int(x) for x in w.split(",")) for w in line.split()[2:]]
+            elif not line.startswith("#") and line.strip() and cur is not None:
+                re_, im_ = line.split()
+                cur["amps"].append(float(re_) + 1j * float(im_))
+    for v in out.values():
+        v["amps"] = np.array(v["amps"])
+    return out
+
+
+def write_order(name: str) -> None:
+    """The oracle's own order for the whole batch of `name` (recursive
+    bisection, the same options as write()) and the extra wires it slices
+    itself under 2^27 entries, stored as data."""
+    circ, open_mask, closed = rqcgen.config_circuit(name)
+    net = tensornet.CircuitNetwork(circ, closed, open_mask)
+    t0 = time.time()
+    opts = ORDER[name]
+    merges, extra = net.plan([], max_log2=27, method=opts["method"], trials=opts.get("trials", 8),
+                             seed=opts.get("seed", 0))
+    path = os.path.join(HERE, f"{name}_oracle_order.json")
+    with open(path, "w") as f:
+        json.dump({"workload": name, "order": opts, "max_log2": 27, "n_tensors": len(net.legs),
+                   "merges": merges, "extra": extra, "plan_seconds": time.time() - t0}, f, separators=(",", ":"))
+    print(path, f"{len(extra)} extra wires")
+
+
 def read(name: str) -> np.ndarray:
     path = os.path.join(HERE, f"{name}_amplitudes.txt")
     data = np.loadtxt(path, comments="#")
@@ -102,6 +180,10 @@ if __name__ == "__main__":
     for n in sys.argv[1:] or ["c2"]:
         if n == "c5":
             write_sliced("c5", 2)
+        elif n == "c5block":
+            write_block("c5")
+        elif n == "c3order":
+            write_order("c3")
         else:
             write(n)
             write_xeb(n)

@@ -266,3 +266,99 @@ def test_model_time_is_the_roofline_sum_over_chunk_steps(tn):
         with pytest.raises(tn.TnError) as e:
             plan.model_time(*bad)
         assert e.value.status == tn.TN_ERR_ARG
+
+
+def test_plan_rank_models_every_candidate(tn):
+    """tn_plan_rank gives each (seed, memory weight) candidate the modeled time
+    of one batch of the plan tn_plan builds from the same options: the chunk's
+    tn_plan_model_time x 2^(S - b) plus the roofline sum over the steps that
+    run once per batch (dependence flags 2); a candidate that cannot be planned
+    (no batch fits the arena cap) gets -1, and a pool where none can is
+    TN_ERR_PLAN."""
+    circ, om, _ = rqcgen.config_circuit("c2")
+    net = tn.Network(circ)
+    kw = dict(open_mask=om, max_log2_intermediate=22, min_log2_slices=4, trials=8, precision="bf16x3")
+    P, BW = 631.6e12, 6786.9e9
+    seeds, weights = [3, 4, 3], [32.0, 8.0, 128.0]
+    got = tn.rank_plans(net, seeds, weights, P, BW, **kw)
+    for s, w, g in zip(seeds, weights, got):
+        p = tn.Plan(net, seed=s, mem_weight=w, **kw)
+        i = p.info()
+        per_batch = 0.0
+        for j, (m, k, n, b) in enumerate(p.step_shapes()):
+            if p.step_layout(j)["dep_flags"] == 2:
+                per_batch += max(8.0 * 2 ** (m + k + n + b) / P,
+                                 8.0 * (2 ** (m + k + b) + 2 ** (k + n + b) + 2 ** (m + n + b)) / BW)
+        assert per_batch > 0
+        want = p.model_time(P, BW) * 2.0 ** (i["log2_slices"] - i["log2_batch_slices"]) + per_batch
+        assert g == pytest.approx(want, rel=1e-12) and g > 0
+    with pytest.raises(tn.TnError) as e:
+        tn.rank_plans(net, [1], [32.0], P, BW, max_arena_bytes=1 << 10, **kw)
+    assert e.value.status == tn.TN_ERR_PLAN
+    with pytest.raises(tn.TnError) as e:
+        tn.rank_plans(net, [1], [1e12], P, BW, **kw)
+    assert e.value.status == tn.TN_ERR_ARG
+    with pytest.raises(tn.TnError) as e:
+        tn.rank_plans(net, [1], [32.0], 0.0, BW, **kw)
+    assert e.value.status == tn.TN_ERR_ARG
+
+
+def test_pool_ranking_is_sorted_and_reproducible(tn):
+    """The pool helper plans the seed x weight grid, drops nothing that
+    planned, sorts by modeled time, and gives the same ranking twice."""
+    from paper_2111_01066_gb300 import pool
+    circ, om, _ = rqcgen.config_circuit("c2")
+    net = tn.Network(circ)
+    kw = dict(open_mask=om, max_log2_intermediate=22, trials=4)
+    assert pool.candidate_grid(5) == [(1, 8.0), (1, 32.0), (1, 128.0), (2, 8.0), (2, 32.0)]
+    a = pool.rank_pool(net, 6, "bf16x3", 4, **kw)
+    b = pool.rank_pool(net, 6, "bf16x3", 4, **kw)
+    assert a == b and len(a) == 6
+    assert [r["model_seconds"] for r in a] == sorted(r["model_seconds"] for r in a)
+    assert {(r["seed"], r["mem_weight"]) for r in a} == set(pool.candidate_grid(6))
+
+
+@pytest.mark.parametrize("name", ["c1", "c3"])
+def test_plan_tree_is_a_complete_tree_over_the_circuit(tn, name):
+    """tn_plan_tree: every gate sits in exactly one leaf, every leaf holds a
+    gate, and the steps merge every node exactly once into one root; each
+    step's operands are the nodes whose wires its layout reads (leaf or earlier
+    step), so the tree is the one the executor runs."""
+    cfg = rqcgen.CONFIGS[name]
+    circ, om, _ = rqcgen.config_circuit(name)
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
+                   min_log2_slices=cfg["log2_slices"], trials=8)
+    leaf_of_gate, nodes = plan.tree(circ.n_gates)
+    n_leaves = plan.info()["n_leaves"]
+    assert sorted(set(leaf_of_gate)) == list(range(n_leaves))
+    assert len(nodes) == n_leaves - 1 == plan.info()["n_steps"]
+    alive = set(range(n_leaves))
+    for j, (x, y) in enumerate(nodes):
+        assert x in alive and y in alive and x != y
+        alive -= {x, y}
+        alive.add(n_leaves + j)
+    assert alive == {2 * n_leaves - 2}
+    with pytest.raises(tn.TnError):
+        plan.tree(circ.n_gates - 1)
+
+
+def test_select_list_and_device_sync_validate_before_device_work(tn):
+    import ctypes
+    lib = tn.load()
+    circ, om, _ = rqcgen.config_circuit("c1")
+    net = tn.Network(circ)
+    o = tn.default_opts()
+    h = ctypes.c_void_p()
+    seeds = (ctypes.c_uint64 * 2)(1, 2)
+    w = (ctypes.c_double * 2)(32.0, 8.0)
+    bad_w = (ctypes.c_double * 2)(32.0, 1e12)
+    assert lib.tn_plan_select_list(net.handle, ctypes.byref(o), 0, seeds, w, 0, None, ctypes.byref(h),
+                                   None) == tn.TN_ERR_ARG
+    assert lib.tn_plan_select_list(net.handle, ctypes.byref(o), 2, None, w, 0, None, ctypes.byref(h),
+                                   None) == tn.TN_ERR_ARG
+    assert lib.tn_plan_select_list(net.handle, ctypes.byref(o), 2, seeds, bad_w, 0, None, ctypes.byref(h),
+                                   None) == tn.TN_ERR_ARG
+    plan = tn.Plan(net, open_mask=om, trials=2)
+    with pytest.raises(tn.TnError) as e:
+        plan.batch_launches()
+    assert e.value.status == tn.TN_ERR_ARG

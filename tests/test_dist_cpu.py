@@ -59,33 +59,62 @@ def test_bench_ranks_take_distinct_batches_and_max_time():
     assert bits[0] == cb and all(b & om == 0 for b in bits)
 
 
-def _shard_slices(rank, world, port, q):
+def _shard_slices(rank, world, port, q, first, count, log2_chunk):
     from oracle import tensornet
+    from paper_2111_01066_gb300 import shard
     _init(rank, world, port)
     circ, _, _ = rqcgen.config_circuit("c1")
     open_mask, closed = 0b111100001111, 0b000010100000
     net = tensornet.CircuitNetwork(circ, closed, open_mask)
     sliced = [(0, 3), (4, 5), (7, 2), (9, 4), (11, 6)]
-    ids = [s for s in range(1 << len(sliced)) if s % world == rank]
-    part = net.contract(sliced, ids)
+    a, n = shard.slice_ranges(first, count, log2_chunk, world)[rank]
+    part = net.contract(sliced, range(a, a + n))          # this rank's contiguous slice range
     buf = torch.from_numpy(np.ascontiguousarray(part.view(np.float64)))
-    dist.all_reduce(buf, op=dist.ReduceOp.SUM)
-    if rank == 0:
-        q.put(buf.numpy().view(np.complex128).copy())
+    shard.allreduce_amplitudes(buf)
+    q.put((rank, buf.numpy().view(np.complex128).copy()))
     dist.destroy_process_group()
 
 
 def test_slice_sharding_sum_equals_unsliced():
+    """Ranks contract contiguous chunk-aligned slice ranges of one batch and
+    one FP64 all-reduce gives every rank the unsliced amplitudes (all 32
+    slices), or the partial sum of a ragged sub-range."""
     from oracle import tensornet
     world = 2
-    port = _free_port()
-    ctx = mp.get_context("spawn")
-    q = ctx.SimpleQueue()
-    mp.start_processes(_shard_slices, args=(world, port, q), nprocs=world, start_method="spawn")
-    total = q.get()
     circ, _, _ = rqcgen.config_circuit("c1")
+    net = tensornet.CircuitNetwork(circ, 0b000010100000, 0b111100001111)
+    sliced = [(0, 3), (4, 5), (7, 2), (9, 4), (11, 6)]
+    for first, count, log2_chunk in ((0, 32, 2), (3, 21, 3)):
+        port = _free_port()
+        ctx = mp.get_context("spawn")
+        q = ctx.SimpleQueue()
+        mp.start_processes(_shard_slices, args=(world, port, q, first, count, log2_chunk), nprocs=world,
+                           start_method="spawn")
+        got = dict(q.get() for _ in range(world))
+        want = net.contract(sliced, range(first, first + count))
+        for r in range(world):
+            assert np.linalg.norm(got[r] - want) <= 1e-12 * np.linalg.norm(want)
     want = tensornet.batch_amplitudes(circ, 0b000010100000, 0b111100001111)
-    assert np.linalg.norm(total - want) <= 1e-12 * np.linalg.norm(want)
+    assert np.linalg.norm(net.contract(sliced) - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_slice_ranges_partition_at_chunk_boundaries():
+    from paper_2111_01066_gb300 import shard
+    for first, count, lc, world in ((0, 4096, 10, 4), (0, 4096, 12, 2), (100, 1000, 6, 3), (0, 0, 4, 2),
+                                    (772096, 1024, 8, 8), (5, 7, 0, 16)):
+        rs = shard.slice_ranges(first, count, lc, world)
+        assert len(rs) == world
+        pos = first
+        for a, n in rs:
+            if n:
+                assert a == pos
+                pos = a + n
+                assert a == first or a % (1 << lc) == 0           # starts on a chunk boundary
+        assert pos == first + count                                 # covers the range in order
+        chunks = [len(range((a >> lc), ((a + n - 1) >> lc) + 1)) if n else 0 for a, n in rs]
+        assert max(chunks) - min(chunks) <= 1                       # chunks dealt out evenly
+    # one chunk cannot be split: the second rank idles
+    assert shard.slice_ranges(0, 4096, 12, 2) == [(0, 4096), (4096, 0)]
 
 
 def _lost_rank(rank, world, port, q):

@@ -1,8 +1,15 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (relative, norm-wise over a batch): FP32 SIMT path 1e-5; every path
-must stay within the stated 1e-3 amplitude target.  Kernel-level checks use
-the same element-wise bound scaled by the operands' norms.
+Plan-level checks use two metrics against the oracle's amplitudes a_ref of a
+batch of N = 2^n-qubit amplitudes:
+  * norm-wise: ||a - a_ref|| / ||a_ref|| over the batch;
+  * element-wise, as in Table 2 of the paper: |a_i - a_ref,i| / |a_ref,i|, its
+    maximum and median over the amplitudes with N |a_ref,i|^2 >= 0.01 (the
+    relative error of a near-zero amplitude says nothing about the method).
+Every path must stay within the stated 1e-3 amplitude target except TF32
+(10 mantissa bits), which is reported and bounded so that one wrong amplitude
+(relative error >= 1) fails.  Kernel-level checks use an element-wise bound
+scaled by the operands' norms.
 """
 import math
 
@@ -46,13 +53,46 @@ def _relerr(got, want):
     return float(np.linalg.norm(got - want) / np.linalg.norm(want))
 
 
+# element-wise bounds (max, median) over amplitudes with N |a_ref|^2 >= 0.01.
+# The weakest of them sit at 0.1 x the batch's rms amplitude, so the maximum
+# runs 4-15 x the norm-wise error (measured: C3 TF32 3.1e-2 at 8.9e-3
+# norm-wise, BF16x3 up to 1.2e-3 on the longest-k plan); a single wrong
+# amplitude (relative error about 1 or more) fails every bound, TF32's included.
+ELEM_TOL = {"fp32": (2e-4, 1e-5), "tf32": (0.1, 2e-2), "bf16x3": (3e-3, 2e-4), "fp16x3": (3e-3, 2e-4)}
+
+
+def _elementwise(got, want, n_qubits, partial=False):
+    """(max, median, count) of |a - a_ref| / |a_ref| over amplitudes with
+    2^n |a_ref|^2 >= 0.01 (the paper's Table 2 relative error, per amplitude).
+    For a partial sum over a few slices (whose amplitudes are far smaller than
+    the batch's) the same cut is taken relative to the batch's mean,
+    |a_ref|^2 >= 0.01 mean |a_ref|^2; for a full batch of Porter-Thomas
+    amplitudes 2^n mean |a|^2 is about 1 and the two cuts agree."""
+    p = np.abs(want) ** 2
+    sel = (p >= 0.01 * np.mean(p)) if partial else (np.ldexp(p, n_qubits) >= 0.01)
+    assert sel.any()
+    r = np.abs(got[sel] - want[sel]) / np.abs(want[sel])
+    return float(r.max()), float(np.median(r)), int(sel.sum())
+
+
+def _check_plan(got, want, n_qubits, prec, tag, norm_tol=None, partial=False):
+    """Norm-wise and element-wise checks of a plan's amplitudes; prints both."""
+    err = _relerr(got, want)
+    emax, emed, cnt = _elementwise(got, want, n_qubits, partial)
+    print(f"{tag}: norm-wise {err:.3e}, element-wise max {emax:.3e} median {emed:.3e} over {cnt}")
+    assert err < (norm_tol if norm_tol is not None else PLAN_TOL[prec])
+    assert emax < ELEM_TOL[prec][0]
+    assert emed < ELEM_TOL[prec][1]
+    return err
+
+
 def test_c1_fp32_all_amplitudes(env):
     tn, torch = env
     circ, om, cb = rqcgen.config_circuit("c1")
     want = sv.batch_amplitudes(sv.simulate(circ), circ.n_qubits, cb, om)
     plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=30)
     got = _run_plan(tn, torch, plan, 0, 1, [cb], 12)
-    assert _relerr(got, want) < FP32_TOL
+    _check_plan(got, want, circ.n_qubits, "fp32", "c1 fp32", FP32_TOL)
 
 
 def test_c1_sliced_batches_and_ragged_ranges(env):
@@ -70,13 +110,14 @@ def test_c1_sliced_batches_and_ragged_ranges(env):
         s = plan.info()["log2_slices"]
         assert s == 5
         got = _run_plan(tn, torch, plan, 0, 1 << s, bits, 8)
-        assert _relerr(got, want) < FP32_TOL
+        _check_plan(got, want, circ.n_qubits, "fp32", f"c1 sliced b={lb}", FP32_TOL)
         # ragged split of the slice range, accumulated into one buffer
         out = torch.zeros(len(bits) * (2 << 8), dtype=torch.float64, device="cuda")
         for first, count in ((0, 3), (3, 10), (13, 1), (14, 18)):
             plan.contract_slices(first, count, bits, out)
         plan.sync()
-        assert _relerr(out.cpu().numpy().view(np.complex128), want) < FP32_TOL
+        _check_plan(out.cpu().numpy().view(np.complex128), want, circ.n_qubits, "fp32", f"c1 ragged b={lb}",
+                    FP32_TOL)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
@@ -99,13 +140,13 @@ def test_prologue_reuse_across_calls_and_batches(env, prec):
     for seq in ([0], [1], [0], [1, 0, 1], [0, 0]):
         got = _run_plan(tn, torch, plan, 0, n, [bits[i] for i in seq], 8).reshape(len(seq), -1)
         for row, i in zip(got, seq):
-            assert _relerr(row, want[i]) < PLAN_TOL[prec]
+            _check_plan(row, want[i], circ.n_qubits, prec, f"c1 reuse {prec} {seq}")
     # accumulation into the same buffer over two calls
     out = torch.zeros(2 << 8, dtype=torch.float64, device="cuda")
     plan.contract_slices(0, n, [bits[1]], out)
     plan.contract_slices(0, n, [bits[1]], out)
     plan.sync()
-    assert _relerr(out.cpu().numpy().view(np.complex128), 2 * want[1]) < PLAN_TOL[prec]
+    _check_plan(out.cpu().numpy().view(np.complex128) / 2, want[1], circ.n_qubits, prec, f"c1 reuse {prec} x2")
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -121,7 +162,7 @@ def test_c1_forced_slices_sum_to_statevector(env, prec):
                    precision=prec, trials=8)
     n = 1 << plan.info()["log2_slices"]
     got = _run_plan(tn, torch, plan, 0, n, [cb], 8)
-    assert _relerr(got, want) < PLAN_TOL[prec]
+    _check_plan(got, want, circ.n_qubits, prec, f"c1 forced {prec}")
 
 
 def test_c5_oracle_slices_against_golden(env):
@@ -136,9 +177,7 @@ def test_c5_oracle_slices_against_golden(env):
                    precision="bf16x3", trials=16)
     assert plan.sliced_wires()[:len(wires)] == wires
     got = _run_plan(tn, torch, plan, 0, n, [cb], 6)
-    err = _relerr(got, want)
-    print(f"c5 bf16x3 slices 0..{n - 1}: rel amp err {err:.3e}")
-    assert err < PLAN_TOL["bf16x3"]
+    _check_plan(got, want, circ.n_qubits, "bf16x3", f"c5 bf16x3 oracle slices 0..{n - 1}", partial=True)
 
 
 def test_c1_range_errors(env):
@@ -166,9 +205,7 @@ def test_c2_against_golden(env, prec, cm):
     plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=26, precision=prec, complex_mult=cm)
     n_sl = 1 << plan.info()["log2_slices"]
     got = _run_plan(tn, torch, plan, 0, n_sl, [cb], 10)
-    err = _relerr(got, want)
-    print(f"c2 {prec} {cm}M: rel amp err {err:.3e}")
-    assert err < PLAN_TOL[prec]
+    _check_plan(got, want, circ.n_qubits, prec, f"c2 {prec} {cm}M")
 
 
 @pytest.mark.parametrize("cand", range(6))
@@ -187,11 +224,10 @@ def test_c3_selection_candidates_against_golden(env, cand):
     out = torch.zeros(2 << 12, dtype=torch.float64, device="cuda")
     plan.contract_slices(0, 1 << plan.info()["log2_slices"], [cb], out)
     plan.sync()
-    err = _relerr(out.cpu().numpy().view(np.complex128), want)
-    print(f"c3 candidate {cand}: rel amp err {err:.3e}")
     # plans with longer contracted dimensions accumulate more in the tensor
     # cores' FP32 (1.3e-4 seen); all stay well inside the 1e-3 target
-    assert err < 5e-4
+    _check_plan(out.cpu().numpy().view(np.complex128), want, circ.n_qubits, "bf16x3", f"c3 candidate {cand}",
+                5e-4)
 
 
 @pytest.mark.parametrize("prec,cm", [("bf16x3", 4), ("bf16x3", 3), ("fp16x3", 4), ("fp16x3", 3), ("tf32", 4),
@@ -213,11 +249,10 @@ def test_c3_all_slices_against_golden(env, prec, cm):
     plan.contract_slices(0, 1 << 12, [cb], out)
     plan.sync()
     got = out.cpu().numpy().view(np.complex128)
-    err = _relerr(got, want)
+    _check_plan(got, want, circ.n_qubits, prec, f"c3 {prec} {cm}M")
     f = tn.xeb(out.view(torch.complex128), circ.n_qubits)
     xerr = abs(f - oxeb.linear_xeb(want, circ.n_qubits))
-    print(f"c3 {prec} {cm}M: rel amp err {err:.3e}, xeb err {xerr:.3e}")
-    assert err < PLAN_TOL[prec]
+    print(f"c3 {prec} {cm}M: xeb err {xerr:.3e}")
     assert xerr < (1e-3 if prec != "tf32" else 5e-2)
 
 
@@ -233,7 +268,7 @@ def test_c2_autotuned_plan_still_matches_golden(env, prec):
     plan.autotune(reps=1)
     for _ in range(2):   # eager chunk, then the re-captured graph
         got = _run_plan(tn, torch, plan, 0, 1, [cb], 10)
-        assert _relerr(got, want) < PLAN_TOL[prec]
+        _check_plan(got, want, circ.n_qubits, prec, f"c2 autotuned {prec}")
 
 
 def test_plan_selection_by_measured_time(env):
@@ -248,7 +283,7 @@ def test_plan_selection_by_measured_time(env):
     assert len(est) == 5 and all(e > 0 for e in est)
     n_sl = 1 << plan.info()["log2_slices"]
     got = _run_plan(tn, torch, plan, 0, n_sl, [cb], 10)
-    assert _relerr(got, want) < PLAN_TOL["bf16x3"]
+    _check_plan(got, want, circ.n_qubits, "bf16x3", "c2 selected plan")
 
 
 SHAPES = [  # (m bits, k bits, n bits): several tiles, ragged (smaller than a tile), degenerate
@@ -281,7 +316,7 @@ def test_contract_pair(env, shape, batch, prec):
     ta, tb = dev(a), dev(b)
     tc = torch.empty((batch, 2 ** len(c_w)), dtype=torch.complex64, device="cuda")
     tn.contract_pair(ta, a_w, tb, b_w, tc, c_w, batch=batch, precision=prec)
-    torch.cuda.synchronize()
+    tn.device_sync()     # synchronises; raises if a bounded device wait ran out
     got = tc.cpu().numpy()
     for i in range(batch):
         want = pairwise.contract_pair(a[i], a_w, b[i], b_w, c_w)
@@ -415,6 +450,12 @@ def test_bounded_wait_times_out_and_context_survives(env):
     dt = time.time() - t0
     assert st == tn.TN_ERR_TIMEOUT
     assert 0.15 < dt < 5.0
+    # the word stays set until tn_device_sync reports and clears it, as after a
+    # pairwise contraction whose wait ran out
+    with pytest.raises(tn.TnError) as e:
+        tn.device_sync()
+    assert e.value.status == tn.TN_ERR_TIMEOUT
+    tn.device_sync()
     x = torch.ones(1 << 10, dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
     tn.permute(x, y, 10, list(range(10)))

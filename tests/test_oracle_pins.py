@@ -290,6 +290,66 @@ def test_contract_in_order_sums_slices_of_its_own_order():
     assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
 
 
+def _random_tree(rng, n_gates, n_groups):
+    """A random grouping of gates (every group non-empty) and a random binary
+    merge order over the groups (ids: groups first, merge j creates n_groups + j)."""
+    leaf = np.concatenate([np.arange(n_groups), rng.integers(0, n_groups, size=n_gates - n_groups)])
+    rng.shuffle(leaf)
+    alive = list(range(n_groups))
+    pairs = []
+    while len(alive) > 1:
+        i, j = sorted(rng.choice(len(alive), size=2, replace=False))
+        pairs.append((alive[i], alive[j]))
+        alive = [x for k, x in enumerate(alive) if k not in (i, j)] + [n_groups + len(pairs) - 1]
+    return [int(x) for x in leaf], pairs
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_tree_order_against_statevector(seed):
+    """An order given by its tree shape (random groups of gates, random merges
+    of the groups, some groups not even connected) contracts the same network:
+    sliced or not, the amplitudes are the state vector's."""
+    n = 7
+    circ = _random_circuit(n, 22, seed)
+    rng = np.random.default_rng(seed)
+    open_mask = int(rng.integers(1 << n)) | 1
+    closed = int(rng.integers(1 << n))
+    want = sv.batch_amplitudes(sv.simulate(circ), n, closed, open_mask)
+    net = tn.CircuitNetwork(circ, closed, open_mask)
+    leaf, pairs = _random_tree(rng, circ.n_gates, 6)
+    internal = [(q, t) for q in range(n) for t in range(1, net.wire_count[q])]
+    pick = [internal[i] for i in rng.choice(len(internal), size=3, replace=False)]
+    for sliced, max_log2 in (([], 27), (pick, 27), (pick, 8)):
+        merges, extra = net.plan_along_tree(sliced, leaf, pairs, max_log2=max_log2)
+        got = net.contract_in_order(merges, sliced, range(1 << len(sliced)), extra)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+    # a partial sum over a slice range is the sum of its parts
+    merges, extra = net.plan_along_tree(pick, leaf, pairs)
+    a = net.contract_in_order(merges, pick, [0, 1, 2], extra)
+    b = net.contract_in_order(merges, pick, [3, 4, 5, 6, 7], extra)
+    assert np.linalg.norm(a + b - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_tree_order_rejects_incomplete_trees():
+    """A tree that merges a node twice, leaves a group out, or names an unknown
+    node is not a contraction of the network."""
+    circ = _random_circuit(6, 20, 3)
+    net = tn.CircuitNetwork(circ, 0, 0b111)
+    rng = np.random.default_rng(3)
+    leaf, pairs = _random_tree(rng, circ.n_gates, 5)
+    net.tree_order(leaf, pairs)
+    with pytest.raises(ValueError):
+        net.tree_order(leaf, pairs[:-1])                       # two nodes left
+    with pytest.raises(ValueError):
+        net.tree_order(leaf, pairs[:-1] + [(pairs[-1][0], pairs[-1][0])])
+    with pytest.raises(ValueError):
+        net.tree_order(leaf, pairs + [(0, 1)])                 # merged twice
+    bad = list(leaf)
+    bad[bad.index(4)] = 9                                      # a gap in the group ids
+    with pytest.raises(ValueError):
+        net.tree_order(bad, pairs)
+
+
 def test_oracle_subslicing_changes_nothing():
     circ, om, cb = rqcgen.config_circuit("c1")
     net = tn.CircuitNetwork(circ, cb, om)
