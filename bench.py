@@ -153,7 +153,7 @@ class ClockSampler:
 # contraction order is data, computed beforehand by the oracle itself
 # (tests/golden/make_golden.py c3order: the order its stored amplitudes were
 # computed with) or built by the oracle from a candidate plan's tree shape
-# (tests/golden/<name>_block_plans.json), so the timed samples hold
+# (tests/golden/<name>_plans.json), so the timed samples hold
 # contractions only.  A sample is a whole number of the oracle's sub-networks
 # (the batch, or one slice, split by the extra wires the oracle slices itself).
 ORACLE_SNIPPET = r"""
@@ -202,7 +202,7 @@ def oracle_timing(name: str, budget_s: float, n_steps: int = 1, cand=None) -> di
     if cand is None:
         src = os.path.join(ROOT, "tests", "golden", f"{name}_oracle_order.json")
     else:
-        src = os.path.join(ROOT, "tests", "golden", f"{name}_block_plans.json")
+        src = os.path.join(ROOT, "tests", "golden", f"{name}_plans.json")
     if not os.path.exists(src):
         return {"error": f"no stored oracle order for {name} ({os.path.basename(src)})"}
     code = ORACLE_SNIPPET.format(root=ROOT, name=name, src=src, cand=list(cand) if cand else None,
@@ -580,7 +580,9 @@ def run_workload(name: str, args, ctx: dict, prec: str, cm: int, pool_n: int, n_
     selection = None
     cand = (1, 32.0)
     plan = None
-    if pool_n > 1 and n_select >= 1:
+    if ctx.get("plan_choice"):   # a given candidate (seed, memory weight): no pool
+        cand = ctx["plan_choice"]
+    elif pool_n > 1 and n_select >= 1:
         if rank == 0:
             # host: rank the pool by modeled time; GPU: time the best few, keep the fastest
             t0 = time.time()
@@ -761,6 +763,10 @@ def run_workload(name: str, args, ctx: dict, prec: str, cm: int, pool_n: int, n_
     path_roof = {"t_roof_ms": t_roof, "t_steps_ms": sum(r["ms"] for r in rows),
                  "frac": t_roof / sum(r["ms"] for r in rows)}
     top = sorted(rows, key=lambda r: -r["ms"])[:8]
+    if ctx.get("step_report") and rank == 0:
+        with open(ctx["step_report"], "w") as f:
+            for i, row in enumerate(rows):
+                f.write(json.dumps(dict(row, step=i, dep_flags=plan.step_layout(i)["dep_flags"])) + "\n")
 
     # frugal sampling within the batch (main text, section III): with the whole
     # slice sum in hand, draw 2^k samples (128 uniform proposals each, M = 10)
@@ -876,6 +882,9 @@ def main() -> int:
     ap.add_argument("--pool", type=int, default=102,
                     help="candidate plans (seeds x memory weights 8, 32, 128) ranked by modeled time on the host "
                          "(<= 1: one plan, seed 1, weight 32)")
+    ap.add_argument("--plan", default=None,
+                    help="seed,mem_weight: use this candidate plan (no pool ranking or selection)")
+    ap.add_argument("--step-report", default=None, help="file for every step's timing and roofline (JSON lines)")
     ap.add_argument("--select", type=int, default=None,
                     help="best-modeled candidates timed on the GPU (default: per workload)")
     ap.add_argument("--complex-mult", type=int, default=4, choices=[3, 4],
@@ -922,7 +931,12 @@ def main() -> int:
     tn.load()
 
     prec = args.precision if args.precision != "auto" else "bf16x3"
+    plan_choice = None
+    if args.plan:
+        sd, wt = args.plan.split(",")
+        plan_choice = (int(sd), float(wt))
     ctx = {"tn": tn, "rank": rank, "world": world, "local": local, "dev": dev, "shard": args.shard,
+           "plan_choice": plan_choice, "step_report": args.step_report,
            "stream": torch.cuda.current_stream(),
            "flush": torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)}
     n_select = args.select if args.select is not None else WORKLOAD_RUN[name].get("select", 6)
@@ -936,7 +950,7 @@ def main() -> int:
     if args.c5 and name == "c3" and world == 1:
         del r["plan"]
         torch.cuda.empty_cache()
-        r5 = run_workload("c5", args, ctx, prec, args.complex_mult, args.pool, WORKLOAD_RUN["c5"]["select"], False,
+        r5 = run_workload("c5", args, dict(ctx, plan_choice=None, step_report=None), prec, args.complex_mult, args.pool, WORKLOAD_RUN["c5"]["select"], False,
                           min(args.cpu_budget, 10.0), args.c5_steps, args.warmup)
         c5 = {"workload": workload_string("c5", r5["circ"], r5["cfg"], r5["info"]["log2_slices"], r5["k_open"]),
               "metric": "slices/s", "value": r5["value"], "ms_per_block": r5["ms"], "steps": args.c5_steps,

@@ -200,7 +200,10 @@ tn_status tn_plan_step_shape(const tn_plan_t* plan, int32_t step, int32_t* log2_
  * Writes to out[0..] in this order: nm, nk, nn, nb, then a_m[nm], a_k[nk],
  * b_k[nk], b_n[nn], c_m[nm], c_n[nn], a_b[nb], b_b[nb], c_b[nb], then the
  * step's dependence flags (bit 0: its result depends on the slice id, bit 1:
- * on the closed output bits; 0 = the same tensor in every chunk): where A is
+ * on the closed output bits; 0 = the same tensor in every chunk), then its
+ * group id (steps sharing an id >= 0 are consecutive, independent, and none
+ * writes where another of the group reads, so they run concurrently; -1: the
+ * step runs alone): where A is
  * the streamed operand, B the small one, C the result, and a_m[j] / c_m[j] the
  * positions of row bit j in A and in C (and so on).  `count` receives the
  * number of entries; at most `cap` are written (TN_ERR_ARG if cap is too small). */

@@ -40,31 +40,81 @@ __global__ void k_leaf_select(const float2* __restrict__ leaf_data, const LeafDe
 // the slices of group g (slices g*per .. g*per+per-1 of the chunk) for every
 // amplitude j into part[g][j]; k_root_finish adds the groups in order into
 // out[batch][j].  Slices outside the call's range are skipped.
-__global__ void k_root_partial(const float2* __restrict__ arena, const RootDesc r, int b, int groups,
-                               double2* __restrict__ part, const ChunkParam* __restrict__ params,
-                               const unsigned* __restrict__ counter) {
+__global__ void __launch_bounds__(256) k_root_partial(const float2* __restrict__ arena, const RootDesc r, int b,
+                                                     int groups, double2* __restrict__ part,
+                                                     const ChunkParam* __restrict__ params,
+                                                     const unsigned* __restrict__ counter) {
+  // the group's slices in rounds of 256: their instance offsets in the root
+  // (or -1 outside the call's range) are found once per block, then every
+  // thread adds its amplitudes over them with four independent FP64
+  // accumulators (slice i of a round goes to accumulator i % 4), combined in a
+  // fixed order, so the sum is deterministic
+  __shared__ int64_t s_off[256];
   const ChunkParam p = params[*counter];
   const int k = r.rank;
   const int64_t nout = (int64_t)1 << k;
   const uint32_t per = (1u << b) / (uint32_t)groups;
   const int g = blockIdx.y;
   const int nbat = __popc(r.bmask);
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nout;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    int64_t ri = 0;
-    for (int q = 0; q < k; ++q)
-      if ((j >> q) & 1) ri |= (int64_t)1 << r.pos_of_open[q];
-    double sr = 0.0, si = 0.0;
-    for (uint32_t s = (uint32_t)g * per; s < (uint32_t)(g + 1) * per; ++s) {
-      const uint64_t sid = p.slice_base + s;
-      if (sid < p.valid_lo || sid >= p.valid_hi) continue;
-      uint32_t inst = 0;
-      for (int t = 0; t < nbat; ++t) inst |= ((s >> r.bslice[t]) & 1u) << t;
-      const float2 v = arena[r.off + ((int64_t)inst << k) + ri];
-      sr += (double)v.x;
-      si += (double)v.y;
+  const int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t jstep = (int64_t)gridDim.x * blockDim.x;
+  // every thread of the block takes part in the rounds (the barriers) the same
+  // number of times, even where it has no amplitude: the pass count depends
+  // on the grid only
+  const int my_n = j0 < nout ? (int)((nout - 1 - j0) / jstep) + 1 : 0;
+  constexpr int MAXJ = 4;   // amplitudes per thread held in registers
+  const int64_t max_n = (nout + jstep - 1) / jstep;
+  const int passes = (int)((max_n + MAXJ - 1) / MAXJ);
+  double ar[MAXJ][4], ai[MAXJ][4];
+  int64_t ri[MAXJ];
+  for (int pass = 0; pass < passes; ++pass) {
+    const int jj0 = pass * MAXJ;
+    const int nj = my_n - jj0 < 0 ? 0 : (my_n - jj0 < MAXJ ? my_n - jj0 : MAXJ);
+#pragma unroll
+    for (int t = 0; t < MAXJ; ++t) {
+      ri[t] = 0;
+      if (t < nj) {
+        const int64_t j = j0 + (int64_t)(jj0 + t) * jstep;
+        for (int q = 0; q < k; ++q)
+          if ((j >> q) & 1) ri[t] |= (int64_t)1 << r.pos_of_open[q];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ar[t][u] = ai[t][u] = 0.0;
     }
-    part[(int64_t)g * nout + j] = make_double2(sr, si);
+    for (uint32_t s0 = (uint32_t)g * per; s0 < (uint32_t)(g + 1) * per; s0 += 256) {
+      const uint32_t cnt = min(256u, (uint32_t)(g + 1) * per - s0);
+      __syncthreads();
+      if (threadIdx.x < cnt) {
+        const uint32_t sl = s0 + threadIdx.x;
+        const uint64_t sid = p.slice_base + sl;
+        int64_t o = -1;
+        if (sid >= p.valid_lo && sid < p.valid_hi) {
+          uint32_t inst = 0;
+          for (int t = 0; t < nbat; ++t) inst |= ((sl >> r.bslice[t]) & 1u) << t;
+          o = r.off + ((int64_t)inst << k);
+        }
+        s_off[threadIdx.x] = o;
+      }
+      __syncthreads();
+      for (uint32_t i = 0; i < cnt; ++i) {
+        const int64_t o = s_off[i];
+        if (o < 0) continue;
+#pragma unroll
+        for (int t = 0; t < MAXJ; ++t)
+          if (t < nj) {
+            const float2 v = arena[o + ri[t]];
+            ar[t][i & 3] += (double)v.x;
+            ai[t][i & 3] += (double)v.y;
+          }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < MAXJ; ++t)
+      if (t < nj) {
+        const int64_t j = j0 + (int64_t)(jj0 + t) * jstep;
+        part[(int64_t)g * nout + j] = make_double2((ar[t][0] + ar[t][1]) + (ar[t][2] + ar[t][3]),
+                                                   (ai[t][0] + ai[t][1]) + (ai[t][2] + ai[t][3]));
+      }
   }
 }
 

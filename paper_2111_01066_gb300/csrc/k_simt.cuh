@@ -8,9 +8,10 @@
 
 namespace tnx {
 
+// One (m tile bx, n tile by) of a GEMM for instances bz, bz + gz, ... (the
+// body of both kernels below; every thread of the block calls it).
 template <int TM, int TN, int TK, int RM, int RN>
-__global__ void __launch_bounds__((TM / RM) * (TN / RN))
-k_cgemm_simt(const GemmArgs g) {
+__device__ __forceinline__ void simt_tile(const GemmArgs& g, int bx, int by, int bz, int gz) {
   constexpr int NTX = TM / RM, NTY = TN / RN, NT = NTX * NTY;
   constexpr int AE = (TM * TK + NT - 1) / NT;
   constexpr int BE = (TK * TN + NT - 1) / NT;
@@ -76,13 +77,13 @@ k_cgemm_simt(const GemmArgs g) {
 
   const int nkc = 1 << (g.nk - g.tk);
   float am = 0.f;   // largest component written (for the FP16 split's scaling)
-  for (int inst = blockIdx.z; inst < g.n_inst; inst += gridDim.z) {
+  for (int inst = bz; inst < g.n_inst; inst += gz) {
     const float2* A = g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) +
-                      deposit_hi(blockIdx.x, g.a_mpos, g.tm, g.nm);
+                      deposit_hi((uint64_t)bx, g.a_mpos, g.tm, g.nm);
     const float2* B = g.B + inst_offset(inst, g.b_istride, g.b_bpos, g.nb) +
-                      deposit_hi(blockIdx.y, g.b_npos, g.tn, g.nn);
+                      deposit_hi((uint64_t)by, g.b_npos, g.tn, g.nn);
     float2* C = g.C + inst_offset(inst, g.c_istride, g.c_bpos, g.nb) +
-                deposit_hi(blockIdx.x, g.c_mpos, g.tm, g.nm) + deposit_hi(blockIdx.y, g.c_npos, g.tn, g.nn);
+                deposit_hi((uint64_t)bx, g.c_mpos, g.tm, g.nm) + deposit_hi((uint64_t)by, g.c_npos, g.tn, g.nn);
     float2 acc[RM][RN];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
@@ -140,6 +141,44 @@ k_cgemm_simt(const GemmArgs g) {
       }
   }
   if (g.amax_c) amax_update(g.amax_c, am);   // every thread reaches here (NT is a multiple of 32)
+}
+
+// One GEMM: grid (m tiles, n tiles, min(instances, 65535)).
+template <int TM, int TN, int TK, int RM, int RN>
+__global__ void __launch_bounds__((TM / RM) * (TN / RN))
+k_cgemm_simt(const GemmArgs g) {
+  simt_tile<TM, TN, TK, RM, RN>(g, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z);
+}
+
+// Several independent GEMMs in one launch (a group of small steps that
+// neither read nor write what another of the group writes): block b runs
+// block b - start[i] of GEMM i, where start[i] <= b < start[i + 1] (start[n]
+// is the grid size), decoded as (m tile, n tile, instance) with the m tile
+// fastest, exactly as that GEMM's own grid would.
+template <int TM, int TN, int TK, int RM, int RN>
+__global__ void __launch_bounds__((TM / RM) * (TN / RN))
+k_cgemm_simt_multi(const GemmArgs* __restrict__ gs, const int32_t* __restrict__ start, int32_t n) {
+  __shared__ GemmArgs sg;
+  __shared__ int s_i;
+  const int b = blockIdx.x;
+  if (threadIdx.x == 0) {
+    int i = 0;
+    while (i + 1 < n && start[i + 1] <= b) ++i;
+    s_i = i;
+  }
+  __syncthreads();
+  const int i = s_i;
+  {
+    const int words = (int)(sizeof(GemmArgs) / 4);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(gs + i);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sg);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  const int gx = 1 << (sg.nm - sg.tm), gy = 1 << (sg.nn - sg.tn);
+  const int gz = sg.n_inst < 65535 ? sg.n_inst : 65535;
+  const int lb = b - start[i];
+  simt_tile<TM, TN, TK, RM, RN>(sg, lb % gx, (lb / gx) % gy, lb / (gx * gy), gz);
 }
 
 }  // namespace tnx

@@ -47,6 +47,8 @@ struct GemmArgs {
   float* amax_c;
 };
 
+static_assert(sizeof(GemmArgs) % 4 == 0, "GemmArgs is copied to shared memory in 4-byte words");
+
 // Exponent s of the power-of-two scale 2^s that maps a tensor's largest
 // component into [2^14, 2^15), inside the FP16 range (|s| <= 126; 0 when the
 // maximum is zero, subnormal or not recorded).

@@ -382,6 +382,24 @@ struct DeviceState {
   float* amax = nullptr;          // FP16X3: largest component of every node (leaves, then steps)
   int root_groups = 1;
   std::vector<StepLaunch> launches;
+  // groups of small independent steps (StepDesc::group): per group, the steps
+  // [first, end) and the launches that run them -- one multi-step launch per
+  // CUDA-core kernel variant used by two or more of its steps, single launches
+  // for the rest; rebuilt whenever the kernels are chosen again
+  struct GroupRun {
+    int first = 0, end = 0;
+    std::vector<int> singles;                  // steps launched alone
+    struct Multi {
+      int kid = 0, blocks = 0, n = 0;
+      GemmArgs* args = nullptr;                // device: n GemmArgs
+      int32_t* start = nullptr;                // device: n + 1 block offsets
+      std::vector<float*> amax;                // FP16X3: result maxima to clear first
+    };
+    std::vector<Multi> multi;
+  };
+  std::vector<GroupRun> groups;
+  std::vector<int> group_at;                   // per step: its group run's index, or -1
+  uint8_t* group_buf = nullptr;                // device memory of every Multi's arrays
   cudaEvent_t done = nullptr;
   bool have_done = false;
   // the chunk's launch sequence as one CUDA graph, captured after the first
@@ -423,6 +441,101 @@ static GemmArgs step_args(const DeviceState& ds, const StepDesc& d, int kid, int
     g.amax_c = ds.amax + d.c_node;
   }
   return g;
+}
+
+static void launch_simt_multi(const DeviceState::GroupRun::Multi& m, cudaStream_t s) {
+  for (float* am : m.amax) CK(cudaMemsetAsync(am, 0, sizeof(float), s));
+  switch (m.kid) {
+    case K_SIMT_64x64:
+      k_cgemm_simt_multi<64, 64, 8, 4, 4><<<m.blocks, 256, 0, s>>>(m.args, m.start, m.n);
+      break;
+    case K_SIMT_128x16:
+      k_cgemm_simt_multi<128, 16, 16, 4, 2><<<m.blocks, 256, 0, s>>>(m.args, m.start, m.n);
+      break;
+    case K_SIMT_256x4:
+      k_cgemm_simt_multi<256, 4, 16, 4, 1><<<m.blocks, 256, 0, s>>>(m.args, m.start, m.n);
+      break;
+    default:
+      fail(TN_ERR_UNSUPPORTED, "kernel variant not built");
+  }
+}
+
+// Group runs from the plan's step groups and the kernels chosen so far.
+static void build_groups(Plan& p, DeviceState& ds) {
+  if (ds.group_buf) {
+    CK(cudaFree(ds.group_buf));
+    ds.group_buf = nullptr;
+  }
+  ds.groups.clear();
+  ds.group_at.assign(p.steps.size(), -1);
+  std::vector<std::pair<size_t, std::vector<int>>> pending;   // (group run, steps) of each Multi
+  for (size_t i = 0; i < p.steps.size();) {
+    const int gid = p.steps[i].group;
+    size_t j = i + 1;
+    if (gid >= 0)
+      while (j < p.steps.size() && p.steps[j].group == gid) ++j;
+    if (gid < 0 || j - i < 2) {
+      i = j;
+      continue;
+    }
+    DeviceState::GroupRun gr;
+    gr.first = (int)i;
+    gr.end = (int)j;
+    std::vector<std::vector<int>> by_kid(K_COUNT);
+    for (size_t t = i; t < j; ++t) {
+      const int kid = ds.launches[t].kid;
+      if (is_tc(kid)) gr.singles.push_back((int)t);
+      else by_kid[kid].push_back((int)t);
+    }
+    for (int kid = 0; kid < K_COUNT; ++kid) {
+      if (by_kid[kid].size() == 1) gr.singles.push_back(by_kid[kid][0]);
+      if (by_kid[kid].size() < 2) continue;
+      DeviceState::GroupRun::Multi m;
+      m.kid = kid;
+      m.n = (int)by_kid[kid].size();
+      gr.multi.push_back(m);
+      pending.push_back({ds.groups.size(), by_kid[kid]});
+    }
+    for (size_t t = i; t < j; ++t) ds.group_at[t] = (int)ds.groups.size();
+    ds.groups.push_back(gr);
+    i = j;
+  }
+  if (pending.empty()) return;
+  // one device buffer: every Multi's GemmArgs, then its block offsets
+  size_t bytes = 0;
+  for (auto& pm : pending) {
+    bytes = (bytes + 255) / 256 * 256 + sizeof(GemmArgs) * pm.second.size();
+    bytes = (bytes + 15) / 16 * 16 + sizeof(int32_t) * (pm.second.size() + 1);
+  }
+  std::vector<uint8_t> host(bytes, 0);
+  CK(cudaMalloc(&ds.group_buf, bytes));
+  size_t off = 0;
+  std::vector<size_t> next_multi(ds.groups.size(), 0);
+  for (auto& pm : pending) {
+    auto& m = ds.groups[pm.first].multi[next_multi[pm.first]++];
+    off = (off + 255) / 256 * 256;
+    const size_t args_off = off;
+    off += sizeof(GemmArgs) * pm.second.size();
+    off = (off + 15) / 16 * 16;
+    const size_t start_off = off;
+    off += sizeof(int32_t) * (pm.second.size() + 1);
+    int32_t blocks = 0;
+    for (size_t q = 0; q < pm.second.size(); ++q) {
+      const GemmArgs& g = ds.launches[pm.second[q]].g;
+      std::memcpy(host.data() + args_off + q * sizeof(GemmArgs), &g, sizeof(GemmArgs));
+      const int64_t nb = ((int64_t)1 << (g.nm - g.tm)) * ((int64_t)1 << (g.nn - g.tn)) *
+                         std::min<int64_t>(g.n_inst, 65535);
+      if (blocks + nb > 0x7fffffff) fail(TN_ERR_UNSUPPORTED, "step group grid too large");
+      std::memcpy(host.data() + start_off + q * sizeof(int32_t), &blocks, sizeof(int32_t));
+      blocks += (int32_t)nb;
+      if (g.amax_c) m.amax.push_back(g.amax_c);
+    }
+    std::memcpy(host.data() + start_off + pm.second.size() * sizeof(int32_t), &blocks, sizeof(int32_t));
+    m.blocks = blocks;
+    m.args = reinterpret_cast<GemmArgs*>(ds.group_buf + args_off);
+    m.start = reinterpret_cast<int32_t*>(ds.group_buf + start_off);
+  }
+  CK(cudaMemcpy(ds.group_buf, host.data(), bytes, cudaMemcpyHostToDevice));
 }
 
 static void ensure_device(Plan& p) {
@@ -498,6 +611,7 @@ static void ensure_device(Plan& p) {
   CK(cudaMalloc(&ds->root_part, sizeof(double2) * (size_t)ds->root_groups << p.root.rank));
   if (!in_arena(p.root.off, (int64_t)1 << p.root.rank, 1 << __builtin_popcount(p.root.bmask)))
     fail(TN_ERR_PLAN, "internal: root outside the arena");
+  build_groups(p, *ds);
 }
 
 void destroy_device_state(Plan* p) {
@@ -516,6 +630,7 @@ void destroy_device_state(Plan* p) {
   cudaFree(ds->ws);
   cudaFree(ds->root_part);
   cudaFree(ds->amax);
+  cudaFree(ds->group_buf);
   if (ds->graph) cudaGraphExecDestroy(ds->graph);
   if (ds->done) cudaEventDestroy(ds->done);
   cudaSetDevice(cur);
@@ -528,8 +643,19 @@ static void run_chunk(Plan& p, cudaStream_t s) {
   const int nl = (int)p.leaves.size();
   k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
                                                                  ds.params, ds.counter);
-  for (size_t i = 0; i < p.steps.size(); ++i)
-    if (p.steps[i].dep_flags & 1) launch_step(ds.launches[i], ds.ws, ds.err, s);   // slice-dependent steps
+  for (size_t i = 0; i < p.steps.size(); ++i) {   // slice-dependent steps
+    if (!(p.steps[i].dep_flags & 1)) continue;
+    const int gi = ds.group_at.empty() ? -1 : ds.group_at[i];
+    if (gi < 0) {
+      launch_step(ds.launches[i], ds.ws, ds.err, s);
+      continue;
+    }
+    // a group of independent small steps: its multi-step launches, then the rest alone
+    const DeviceState::GroupRun& gr = ds.groups[gi];
+    for (const auto& m : gr.multi) launch_simt_multi(m, s);
+    for (int t : gr.singles) launch_step(ds.launches[t], ds.ws, ds.err, s);
+    i = (size_t)gr.end - 1;
+  }
   const int64_t nout = (int64_t)1 << p.root.rank;
   const int blocks = (int)std::min<int64_t>((nout + 255) / 256, 4096);
   k_root_partial<<<dim3(blocks, ds.root_groups), 256, 0, s>>>(ds.arena, p.root, p.log2_batch, ds.root_groups,
@@ -787,6 +913,7 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   CK(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  build_groups(p, ds);   // kernels may have changed
   if (ds.graph) {
     cudaGraphExecDestroy(ds.graph);
     ds.graph = nullptr;
@@ -905,10 +1032,21 @@ extern "C" tn_status tn_plan_chunk_launches(const tn_plan_t* h, int32_t* launche
   const Plan& p = h->plan;
   if (!p.dev) fail(TN_ERR_ARG, "tn_plan_chunk_launches: call after the first tn_contract_slices");
   int n = 4;
+  auto kernels_of = [&](int i) {
+    const StepLaunch& L = p.dev->launches[i];
+    return is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
+  };
   for (size_t i = 0; i < p.steps.size(); ++i) {
     if ((p.steps[i].dep_flags & 1) == 0) continue;
-    const StepLaunch& L = p.dev->launches[i];
-    n += is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
+    const int gi = p.dev->group_at.empty() ? -1 : p.dev->group_at[i];
+    if (gi < 0) {
+      n += kernels_of((int)i);
+      continue;
+    }
+    const auto& gr = p.dev->groups[gi];
+    n += (int)gr.multi.size();
+    for (int t : gr.singles) n += kernels_of(t);
+    i = (size_t)gr.end - 1;
   }
   *launches = n;
   API_END

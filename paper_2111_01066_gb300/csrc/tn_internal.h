@@ -70,6 +70,9 @@ struct StepDesc {
   int32_t kernel;                     // kernel variant chosen by the executor
   int32_t a_node, b_node, c_node;     // node ids (leaves 0..L-1, step i's result L+i)
   int32_t dep_flags;                  // result depends on the slice id (bit 0), on closed output bits (bit 1)
+  int32_t group;                      // steps with one group id >= 0 are consecutive, independent of each
+                                      // other, and no output of one overlaps an operand of another: they
+                                      // may run concurrently (small slice-dependent steps); -1 otherwise
   int8_t a_mpos[MAXR], a_kpos[MAXR], b_kpos[MAXR], b_npos[MAXR], c_mpos[MAXR], c_npos[MAXR];
   int8_t a_bpos[MAXB], b_bpos[MAXB], c_bpos[MAXB];
 };

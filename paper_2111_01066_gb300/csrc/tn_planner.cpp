@@ -828,8 +828,9 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
     const int v = L + mi;
     if ((nflag[v] & 1) == 0 && (parent[v] < 0 || nflag[parent[v]] != nflag[v])) pooled[v] = 1;
   }
+  std::vector<int> exec_group;   // group id of every step in execution order (-1: none)
   auto layout = [&](int b, std::vector<NodeInfo>& info, std::vector<StepDesc>& steps,
-                    int64_t& arena) -> bool {
+                    int64_t& arena, std::vector<int>& exec) -> bool {
     info.assign(L + nm, NodeInfo{});
     for (int i = 0; i < L; ++i) {
       for (int w : S.leaves[i].wires)
@@ -926,6 +927,81 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       }
       node_order.swap(lw);
       border_of.swap(lb);
+      // Execution order.  First the steps that depend on no slice (they run
+      // once per plan or per batch, before any chunk), in post-order.  Then the
+      // small slice-dependent steps (under 2^20 multiply-adds per chunk: the
+      // CUDA-core kernels) whose subtree holds only such steps, leaves and
+      // prologue results, one group per dependency level: a group's steps are
+      // independent and run as one launch.  Then the other slice-dependent
+      // steps in post-order, where the remaining small steps are deferred and
+      // emitted the same way, level by level, right before the first step
+      // that reads one of them.
+      exec.clear();
+      exec_group.clear();
+      std::vector<char> pend(nm, 0), hoist(nm, 0);
+      std::vector<int> pending, lev(nm, 0);
+      int next_group = 0;
+      auto small = [&](int mi) {
+        const int x = T.merges[mi].first, y = T.merges[mi].second;
+        std::vector<int> u;
+        std::set_union(wset[x].begin(), wset[x].end(), wset[y].begin(), wset[y].end(), std::back_inserter(u));
+        return (int)u.size() + __builtin_popcount(bm[x] | bm[y]) < 20;
+      };
+      // emit `set` (merge indices in post-order, closed under "child in set
+      // comes first") as one group per level among them
+      auto emit_levels = [&](const std::vector<int>& set, const std::vector<char>& in) {
+        int maxl = 0;
+        for (int mi : set) {
+          int l = 0;
+          for (int ch : {T.merges[mi].first, T.merges[mi].second})
+            if (ch >= L && in[ch - L]) l = std::max(l, lev[ch - L]);
+          lev[mi] = l + 1;
+          maxl = std::max(maxl, l + 1);
+        }
+        for (int l = 1; l <= maxl; ++l) {
+          for (int mi : set)
+            if (lev[mi] == l) {
+              exec.push_back(mi);
+              exec_group.push_back(next_group);
+            }
+          ++next_group;
+        }
+      };
+      for (int mi : order)
+        if (!(nflag[L + mi] & 1)) {
+          exec.push_back(mi);
+          exec_group.push_back(-1);
+        }
+      std::vector<int> hoisted;
+      for (int mi : order) {
+        if (!(nflag[L + mi] & 1) || !small(mi)) continue;
+        bool ok = true;
+        for (int ch : {T.merges[mi].first, T.merges[mi].second})
+          if (ch >= L && (nflag[ch] & 1) && !hoist[ch - L]) ok = false;
+        if (ok) {
+          hoist[mi] = 1;
+          hoisted.push_back(mi);
+        }
+      }
+      emit_levels(hoisted, hoist);
+      auto flush = [&]() {
+        emit_levels(pending, pend);
+        for (int mi : pending) pend[mi] = 0;
+        pending.clear();
+      };
+      for (int mi : order) {
+        if (!(nflag[L + mi] & 1) || hoist[mi]) continue;
+        if (small(mi)) {
+          pending.push_back(mi);
+          pend[mi] = 1;
+          continue;
+        }
+        const int x = T.merges[mi].first, y = T.merges[mi].second;
+        if ((x >= L && pend[x - L]) || (y >= L && pend[y - L])) flush();
+        exec.push_back(mi);
+        exec_group.push_back(-1);
+      }
+      flush();
     }
     // best-fit arena allocator
     std::vector<std::pair<int64_t, int64_t>> freel;  // (offset, size)
@@ -979,7 +1055,11 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
     }
     steps.clear();
     std::vector<int> step_of(nm, -1);
-    for (int mi : order) {
+    // a group's outputs are all allocated before any of its operands is
+    // released, so that no output overlaps an operand of another step of the group
+    std::vector<std::pair<int64_t, int64_t>> to_release;
+    for (size_t e = 0; e < exec.size(); ++e) {
+      const int mi = exec[e];
       const int x = T.merges[mi].first, y = T.merges[mi].second;
       const int64_t ex = elems_of(info[x]), ey = elems_of(info[y]);
       const bool x_is_a = ex > ey || (ex == ey && info[x].wires.size() >= info[y].wires.size());
@@ -1061,11 +1141,16 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       d.c_elems = elems_of(C);
       peak = std::max(peak, end);
       d.kernel = -1;
+      d.group = exec_group[e];
       const int a_id = x_is_a ? x : y, b_id = x_is_a ? y : x;
-      if (!pooled[a_id]) release(A.off, elems_of(A));
-      if (!pooled[b_id]) release(B.off, elems_of(B));
+      if (!pooled[a_id]) to_release.push_back({A.off, elems_of(A)});
+      if (!pooled[b_id]) to_release.push_back({B.off, elems_of(B)});
       info[L + mi] = C;
       steps.push_back(d);
+      if (exec_group[e] < 0 || e + 1 == exec.size() || exec_group[e + 1] != exec_group[e]) {
+        for (auto [off, sz] : to_release) release(off, sz);
+        to_release.clear();
+      }
     }
     arena = peak;
     return peak * 8 <= cap_bytes;
@@ -1073,11 +1158,12 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
 
   std::vector<NodeInfo> info;
   std::vector<StepDesc> steps;
+  std::vector<int> exec;   // merge index of every step, in execution order
   int64_t arena = 0;
   int b = o.log2_batch_slices > 0 ? std::min(o.log2_batch_slices, std::min(nS, 12)) : std::min(nS, 12);
   if (nF > 0) b = 0;   // caller-sliced plans contract one slice per chunk
   while (true) {
-    const bool ok = layout(b, info, steps, arena);
+    const bool ok = layout(b, info, steps, arena, exec);
     if (ok) break;
     if (b == 0) fail(TN_ERR_PLAN, "one slice does not fit the arena cap");
     --b;
@@ -1088,7 +1174,22 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
   // dependence of every step's result on the slice id (bit 0) and on the
   // closed output bits (bit 1): a step with neither computes the same tensor
   // in every chunk of every call
-  for (size_t j = 0; j < P->steps.size(); ++j) P->steps[j].dep_flags = nflag[L + order[j]];
+  for (size_t j = 0; j < P->steps.size(); ++j) P->steps[j].dep_flags = nflag[L + exec[j]];
+  // the executor runs a group's steps concurrently: check that none reads
+  // another's result and that no output overlaps another step's operands or output
+  for (size_t i = 0; i < P->steps.size(); ++i) {
+    const StepDesc& u = P->steps[i];
+    if (u.group < 0) continue;
+    for (size_t j = i + 1; j < P->steps.size() && P->steps[j].group == u.group; ++j) {
+      const StepDesc& v = P->steps[j];
+      auto overlap = [](int64_t o1, int64_t n1, int64_t o2, int64_t n2) { return o1 < o2 + n2 && o2 < o1 + n1; };
+      if (v.a_node == u.c_node || v.b_node == u.c_node || u.a_node == v.c_node || u.b_node == v.c_node ||
+          overlap(u.c_off, u.c_elems, v.a_off, v.a_elems) || overlap(u.c_off, u.c_elems, v.b_off, v.b_elems) ||
+          overlap(v.c_off, v.c_elems, u.a_off, u.a_elems) || overlap(v.c_off, v.c_elems, u.b_off, u.b_elems) ||
+          overlap(u.c_off, u.c_elems, v.c_off, v.c_elems) || (v.dep_flags & 1) == 0 || (u.dep_flags & 1) == 0)
+        fail(TN_ERR_PLAN, "internal: a step group is not independent");
+    }
+  }
 
   // leaves: source data ordered [kept planning wires, sliced wires by slice bit, closed outputs]
   P->leaves.resize(L);
@@ -1301,6 +1402,7 @@ extern "C" tn_status tn_plan_step_layout(const tn_plan_t* h, int32_t step, int32
   put(d.b_bpos, d.nb);
   put(d.c_bpos, d.nb);
   v.push_back(d.dep_flags);
+  v.push_back(d.group);
   *count = (int32_t)v.size();
   if ((int32_t)v.size() > cap) {
     set_error("tn_plan_step_layout: cap smaller than the layout");

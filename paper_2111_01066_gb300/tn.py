@@ -267,8 +267,9 @@ class Plan:
 
     def step_layout(self, i: int) -> dict:
         """Bit positions of step i's operands (A streamed, B small, C result):
-        keys a_m, a_k, b_k, b_n, c_m, c_n, a_b, b_b, c_b; and dep_flags (bit 0:
-        depends on the slice id, bit 1: on the closed output bits)."""
+        keys a_m, a_k, b_k, b_n, c_m, c_n, a_b, b_b, c_b; dep_flags (bit 0:
+        depends on the slice id, bit 1: on the closed output bits); group (steps
+        with one id >= 0 run concurrently; -1: alone)."""
         buf = (ctypes.c_int32 * 256)()
         cnt = ctypes.c_int32()
         _check(load().tn_plan_step_layout(self.handle, i, buf, 256, ctypes.byref(cnt)))
@@ -280,6 +281,7 @@ class Plan:
             out[key] = v[pos:pos + n]
             pos += n
         out["dep_flags"] = v[pos]
+        out["group"] = v[pos + 1]
         return out
 
     def tree(self, n_gates: int) -> Tuple[List[int], List[Tuple[int, int]]]:

@@ -9,7 +9,7 @@ line ("re im", 17 significant digits), in the batch order sum_j b(open_j) 2^j.
 With the amplitudes of c2 and c3 it also writes `<name>_xeb.txt`, their linear
 XEB computed by the oracle.  "c5block" writes the partial sums over the first
 slices of each candidate plan's timed block (the plan parameters are read as
-data from `c5_block_plans.json`, written by make_plan_data.py); "c3order"
+data from `c5_plans.json`, written by make_plan_data.py); "c3order"
 stores the oracle's own contraction order for the 42-qubit batch, so that the
 oracle can be timed without re-planning.
 """
@@ -80,13 +80,13 @@ def read_sliced(name: str):
 
 
 def write_block(name: str) -> None:
-    """For every candidate plan in <name>_block_plans.json: the FP64 sum over
+    """For every candidate plan in <name>_plans.json: the FP64 sum over
     slice ids block_first .. block_first + check_slices - 1 of the network with
     the candidate's sliced wires fixed (slice id s sets wire j to bit j of s),
     contracted by the oracle along an order it builds from the candidate's tree
     shape (tensornet.CircuitNetwork.tree_order), sub-sliced by the oracle
     itself under 2^27 entries."""
-    with open(os.path.join(HERE, f"{name}_block_plans.json")) as f:
+    with open(os.path.join(HERE, f"{name}_plans.json")) as f:
         data = json.load(f)
     circ, open_mask, closed = rqcgen.config_circuit(name)
     assert data["closed_bits"] == closed and data["open_mask"] == open_mask

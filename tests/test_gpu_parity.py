@@ -208,42 +208,86 @@ def test_c2_against_golden(env, prec, cm):
     _check_plan(got, want, circ.n_qubits, prec, f"c2 {prec} {cm}M")
 
 
-@pytest.mark.parametrize("cand", range(6))
-def test_c3_selection_candidates_against_golden(env, cand):
-    """Every plan that plan selection can hand the benchmark (candidate i: seed
-    1 + i, memory weight 32 x (1, 1/4, 4)[i % 3]) gives the oracle's C3
+def _pool_candidates(name):
+    from tests.golden.make_plan_data import read
+    return read(name)["candidates"]
+
+
+def _pool_plan(tn, name, c, precision="bf16x3"):
+    """The benchmark's plan for pool candidate c (options as recorded beside it)."""
+    from tests.golden.make_plan_data import RUNS
+    run = RUNS[name]
+    cfg = rqcgen.CONFIGS[name]
+    circ, om, _ = rqcgen.config_circuit(name)
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
+                   min_log2_slices=cfg["log2_slices"], log2_batch_slices=run["log2_batch"], trials=run["trials"],
+                   max_arena_bytes=run["arena_gib"] << 30, precision=precision, seed=c["seed"],
+                   mem_weight=c["mem_weight"])
+    # the planner is deterministic: the same options give the recorded slicing
+    assert plan.sliced_wires() == [tuple(w) for w in c["sliced_wires"]]
+    return plan
+
+
+@pytest.mark.parametrize("cand", range(8))
+def test_c3_pool_candidates_against_golden(env, cand):
+    """Every plan the benchmark may time (the 8 best-modeled of its 102-plan
+    pool, recorded in tests/golden/c3_plans.json) gives the oracle's C3
     amplitudes at full size (all 4096 slices, BF16x3)."""
     tn, torch = env
     from tests.golden.make_golden import read
     want = read("c3")
-    cfg = rqcgen.CONFIGS["c3"]
+    c = _pool_candidates("c3")[cand]
     circ, om, cb = rqcgen.config_circuit("c3")
-    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
-                   min_log2_slices=cfg["log2_slices"], precision="bf16x3", seed=1 + cand, trials=128,
-                   mem_weight=32.0 * (1.0, 0.25, 4.0)[cand % 3])
+    plan = _pool_plan(tn, "c3", c)
     out = torch.zeros(2 << 12, dtype=torch.float64, device="cuda")
     plan.contract_slices(0, 1 << plan.info()["log2_slices"], [cb], out)
     plan.sync()
     # plans with longer contracted dimensions accumulate more in the tensor
     # cores' FP32 (1.3e-4 seen); all stay well inside the 1e-3 target
-    _check_plan(out.cpu().numpy().view(np.complex128), want, circ.n_qubits, "bf16x3", f"c3 candidate {cand}",
-                5e-4)
+    _check_plan(out.cpu().numpy().view(np.complex128), want, circ.n_qubits, "bf16x3",
+                f"c3 pool candidate {cand} (seed {c['seed']}, weight {c['mem_weight']})", 5e-4)
+
+
+@pytest.mark.parametrize("cand", range(6))
+def test_c5_timed_block_against_golden(env, cand):
+    """53 qubits, 20 cycles, 2^20 slices: for every plan the benchmark may time
+    (the 6 best-modeled of its pool, tests/golden/c5_plans.json), the first 16
+    slice ids of the benchmark's timed 1024-slice block, contracted in the
+    benchmark's configuration (1024-slice chunks), match the oracle's FP64
+    partial sum over the same slices."""
+    tn, torch = env
+    from tests.golden.make_golden import read_block
+    c = _pool_candidates("c5")[cand]
+    gold = read_block("c5")[(c["seed"], c["mem_weight"])]
+    assert gold["first"] == c["block_first"] and gold["wires"] == [tuple(w) for w in c["sliced_wires"]]
+    circ, om, cb = rqcgen.config_circuit("c5")
+    plan = _pool_plan(tn, "c5", c)
+    assert rqcgen.timed_block_first(plan.info()["log2_slices"], 1024, rqcgen.CONFIGS["c5"]["seed"]) == gold["first"]
+    got = _run_plan(tn, torch, plan, gold["first"], gold["count"], [cb], 6)
+    _check_plan(got, gold["amps"], circ.n_qubits, "bf16x3",
+                f"c5 pool candidate {cand} (seed {c['seed']}, weight {c['mem_weight']}) slices "
+                f"{gold['first']}..{gold['first'] + gold['count'] - 1}", partial=True)
 
 
 @pytest.mark.parametrize("prec,cm", [("bf16x3", 4), ("bf16x3", 3), ("fp16x3", 4), ("fp16x3", 3), ("tf32", 4),
                                      ("fp32", 4)])
 def test_c3_all_slices_against_golden(env, prec, cm):
     """The benchmark workload at full size: 42 qubits, 16 cycles, 2^12 slices
-    contracted in the configuration bench.py times, summed, against the oracle's
-    plan-independent amplitudes of the whole batch; XEB of the batch too."""
+    contracted in the configuration bench.py times (the best-modeled plan of its
+    pool, in every precision and product the benchmark reports), summed, against
+    the oracle's plan-independent amplitudes of the whole batch; XEB of the
+    batch too."""
     tn, torch = env
     from tests.golden.make_golden import read
+    from tests.golden.make_plan_data import RUNS
     from oracle import xeb as oxeb
     want = read("c3")
     cfg = rqcgen.CONFIGS["c3"]
+    c = _pool_candidates("c3")[0]
     circ, om, cb = rqcgen.config_circuit("c3")
     plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
-                   min_log2_slices=cfg["log2_slices"], precision=prec, complex_mult=cm)
+                   min_log2_slices=cfg["log2_slices"], precision=prec, complex_mult=cm, seed=c["seed"],
+                   mem_weight=c["mem_weight"], trials=RUNS["c3"]["trials"])
     assert plan.info()["log2_slices"] == 12
     out = torch.zeros(2 << 12, dtype=torch.float64, device="cuda")
     plan.contract_slices(0, 1 << 12, [cb], out)
@@ -284,6 +328,15 @@ def test_plan_selection_by_measured_time(env):
     n_sl = 1 << plan.info()["log2_slices"]
     got = _run_plan(tn, torch, plan, 0, n_sl, [cb], 10)
     _check_plan(got, want, circ.n_qubits, "bf16x3", "c2 selected plan")
+    # the pool path: candidates ranked by model on the host, the best few timed
+    from paper_2111_01066_gb300 import pool
+    kw = dict(open_mask=om, max_log2_intermediate=24, trials=8)
+    ranked = pool.rank_pool(tn.Network(circ), 9, "bf16x3", 4, **kw)
+    assert len(ranked) == 9
+    plan, ch, est = pool.select_from(tn.Network(circ), ranked[:3], cb, "bf16x3", 4, **kw)
+    assert len(est) == 3 and all(e > 0 for e in est) and est[ch] == min(est)
+    got = _run_plan(tn, torch, plan, 0, 1 << plan.info()["log2_slices"], [cb], 10)
+    _check_plan(got, want, circ.n_qubits, "bf16x3", "c2 pool-selected plan")
 
 
 SHAPES = [  # (m bits, k bits, n bits): several tiles, ragged (smaller than a tile), degenerate
