@@ -525,20 +525,21 @@ def golden_amplitudes(name: str):
 
 
 def golden_block(name: str, cand):
-    """The oracle's stored partial sum over the first slices of candidate
-    cand = (seed, mem_weight)'s timed block, or None (tests/golden/<name>_block_amplitudes.txt)."""
+    """The oracle's stored partial sums for candidate cand = (seed, mem_weight)
+    (tests/golden/<name>_block_amplitudes.txt): {"block": the first slices of
+    its timed block, "sample": a seeded slice sample}, each {"slices", "wires",
+    "amps"}; None if absent."""
     import numpy as np
     path = os.path.join(ROOT, "tests", "golden", f"{name}_block_amplitudes.txt")
     if not os.path.exists(path):
         return None
     found, cur = {}, None
-    with open(path) as f:   # sections: "# candidate seed=.. mem_weight=.. slices=a..b", "# wires q,t ...", values
+    with open(path) as f:   # sections: "# candidate seed=.. mem_weight=.. kind=.. slices=a,b,..", "# wires", values
         for line in f:
             if line.startswith("# candidate"):
                 kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
-                lo, hi = (int(x) for x in kv["slices"].split(".."))
-                cur = {"first": lo, "count": hi - lo + 1, "amps": [], "wires": []}
-                found[(int(kv["seed"]), float(kv["mem_weight"]))] = cur
+                cur = {"slices": [int(x) for x in kv["slices"].split(",")], "amps": [], "wires": []}
+                found.setdefault((int(kv["seed"]), float(kv["mem_weight"])), {})[kv["kind"]] = cur
             elif line.startswith("# wires") and cur is not None:
                 cur["wires"] = [tuple(int(x) for x in w.split(",")) for w in line.split()[2:]]
             elif line.strip() and not line.startswith("#") and cur is not None:
@@ -546,7 +547,8 @@ def golden_block(name: str, cand):
                 cur["amps"].append(complex(float(re_), float(im_)))
     got = found.get((int(cand[0]), float(cand[1])))
     if got is not None:
-        got["amps"] = np.array(got["amps"])
+        for sec in got.values():
+            sec["amps"] = np.array(sec["amps"])
     return got
 
 
@@ -667,20 +669,40 @@ def run_workload(name: str, args, ctx: dict, prec: str, cm: int, pool_n: int, n_
             return {"rel_amp_err": float(np.linalg.norm(got - gold) / np.linalg.norm(gold)),
                     "elementwise_rel_err": elementwise_error(got, gold, circ.n_qubits),
                     "xeb_err": abs(f - gold_xeb), "against": "oracle amplitudes of the whole batch"}
-        if gblock is not None and gblock["first"] == first and [tuple(w) for w in p.sliced_wires()] == gblock["wires"]:
-            o.zero_()
-            p.contract_slices(gblock["first"], gblock["count"], [cb], o, stream)
-            p.sync(stream)
-            got = o.cpu().numpy().view(np.complex128)
-            want = gblock["amps"]
-            pw = np.abs(want) ** 2
-            sel = pw >= 0.01 * np.mean(pw)
-            r = np.abs(got[sel] - want[sel]) / np.abs(want[sel])
-            return {"rel_amp_err": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
-                    "elementwise_rel_err": {"max": float(r.max()), "median": float(np.median(r)),
-                                            "count": int(sel.sum()), "cut": "|a|^2 >= 0.01 mean |a|^2"},
-                    "against": f"oracle partial sum over slices {gblock['first']}..."
-                               f"{gblock['first'] + gblock['count'] - 1} of the timed block"}
+        if gblock is not None and gblock["block"]["slices"][0] == first and \
+                [tuple(w) for w in p.sliced_wires()] == gblock["block"]["wires"]:
+            def slice_sum(ids):
+                o.zero_()
+                ids = sorted(ids)
+                i = 0
+                while i < len(ids):
+                    j = i + 1
+                    while j < len(ids) and ids[j] == ids[j - 1] + 1:
+                        j += 1
+                    p.contract_slices(ids[i], j - i, [cb], o, stream)
+                    i = j
+                p.sync(stream)
+                return o.cpu().numpy().view(np.complex128).copy()
+
+            def rel(got, want, scale):
+                pw = np.abs(want) ** 2
+                sel = pw >= 0.01 * np.mean(pw)
+                r = np.abs(got[sel] - want[sel]) / np.abs(want[sel])
+                return {"rel_amp_err": float(np.linalg.norm(got - want) / scale),
+                        "elementwise_rel_err": {"max": float(r.max()), "median": float(np.median(r)),
+                                                "count": int(sel.sum()), "cut": "|a|^2 >= 0.01 mean |a|^2"}}
+            smp, blk = gblock["sample"], gblock["block"]
+            res = {"sample": dict(rel(slice_sum(smp["slices"]), smp["amps"], np.linalg.norm(smp["amps"])),
+                                  against=f"oracle partial sum over a seeded sample of {len(smp['slices'])} "
+                                          f"slice ids")}
+            scale = max(np.linalg.norm(blk["amps"]), np.linalg.norm(smp["amps"]))
+            b = rel(slice_sum(blk["slices"]), blk["amps"], scale)
+            b["near_zero_block"] = bool(np.linalg.norm(blk["amps"]) < 1e-6 * np.linalg.norm(smp["amps"]))
+            b["against"] = (f"oracle partial sum over slices {blk['slices'][0]}..{blk['slices'][-1]} of the timed "
+                            f"block; norm-wise error on the scale of a 16-slice sum")
+            res["timed_block"] = b
+            res["rel_amp_err"] = max(res["sample"]["rel_amp_err"], b["rel_amp_err"])
+            return res
         return None
 
     # untimed first call: device state + warm-up; then the per-step autotuner

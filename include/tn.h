@@ -267,9 +267,11 @@ tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int3
 
 /* Autotuner (after one tn_contract_slices call): times candidate kernels for
  * every step in place on `stream` -- tensor-core tiles of 32, 64 or 128
- * complex columns in the TF32 / BF16X3 modes, and the three CUDA-core tilings
- * for steps under 50 us or in the FP32 mode -- each `reps` times, and keeps the
- * fastest for later calls.  Synchronises `stream`; the arena contents are
+ * complex columns in the TF32 / BF16X3 / FP16X3 modes, each with either
+ * write-back order and with the default or a deeper ring of B' slots, and the
+ * three CUDA-core tilings for steps under 50 us, of low arithmetic intensity
+ * or in the FP32 mode -- each `reps` times, and keeps the fastest for later
+ * calls.  Synchronises `stream`; the arena contents are
  * overwritten (the next call recomputes them). */
 tn_status tn_plan_autotune(tn_plan_t* plan, int32_t reps, void* stream);
 

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(256) k_root_partial(const float2* __restrict__
   // (or -1 outside the call's range) are found once per block, then every
   // thread adds its amplitudes over them with four independent FP64
   // accumulators (slice i of a round goes to accumulator i % 4), combined in a
-  // fixed order, so the sum is deterministic
+  // fixed order, so the sum is deterministic.  256 threads, s_off has 256
+  // entries: cnt <= 256 and its padding to a multiple of 4 stays <= 256
   __shared__ int64_t s_off[256];
   const ChunkParam p = params[*counter];
   const int k = r.rank;
@@ -83,12 +84,13 @@ __global__ void __launch_bounds__(256) k_root_partial(const float2* __restrict__
     }
     for (uint32_t s0 = (uint32_t)g * per; s0 < (uint32_t)(g + 1) * per; s0 += 256) {
       const uint32_t cnt = min(256u, (uint32_t)(g + 1) * per - s0);
+      const uint32_t cnt4 = (cnt + 3u) & ~3u;   // padded with -1 (no slice) to whole quadruples
       __syncthreads();
-      if (threadIdx.x < cnt) {
+      if (threadIdx.x < cnt4) {
         const uint32_t sl = s0 + threadIdx.x;
         const uint64_t sid = p.slice_base + sl;
         int64_t o = -1;
-        if (sid >= p.valid_lo && sid < p.valid_hi) {
+        if (threadIdx.x < cnt && sid >= p.valid_lo && sid < p.valid_hi) {
           uint32_t inst = 0;
           for (int t = 0; t < nbat; ++t) inst |= ((sl >> r.bslice[t]) & 1u) << t;
           o = r.off + ((int64_t)inst << k);
@@ -96,15 +98,21 @@ __global__ void __launch_bounds__(256) k_root_partial(const float2* __restrict__
         s_off[threadIdx.x] = o;
       }
       __syncthreads();
-      for (uint32_t i = 0; i < cnt; ++i) {
-        const int64_t o = s_off[i];
-        if (o < 0) continue;
+      // four slices per pass, one per accumulator: four independent loads in flight
+      for (uint32_t i = 0; i < cnt4; i += 4) {
+        int64_t o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = s_off[i + u];
 #pragma unroll
         for (int t = 0; t < MAXJ; ++t)
           if (t < nj) {
-            const float2 v = arena[o + ri[t]];
-            ar[t][i & 3] += (double)v.x;
-            ai[t][i & 3] += (double)v.y;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (o[u] >= 0) {
+                const float2 v = arena[o[u] + ri[t]];
+                ar[t][u] += (double)v.x;
+                ai[t][u] += (double)v.y;
+              }
           }
       }
     }

@@ -230,9 +230,11 @@ static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
 
 // epi_mode: -1 chooses the write-back by the coalesced run lengths, 0 forces
 // direct per-column stores, 1 the staged order (where the tile allows it)
+// b_slots: B' ring slots (<= 0: 4 for slots up to 16 KB, else 3; the rest of
+// the shared-memory budget goes to A slots)
 static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_lin, int64_t c_total = 0,
                               bool allow_split = false, int epi_mode = -1,
-                              int64_t split_cap_bytes = (int64_t)256 << 20) {
+                              int64_t split_cap_bytes = (int64_t)256 << 20, int b_slots = 0) {
   StepLaunch L;
   L.kid = kid;
   L.g = g;
@@ -274,8 +276,9 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   // rings: B' slots first (3, or 4 when small), the rest of the budget to A slots
   const int b_slot = npl * b_plane;
   const int budget = 220 * 1024 - 4096 - TC_EPI_BYTES;
-  t.nbs = b_slot <= 16384 ? TC_MAX_B : 3;
+  t.nbs = b_slots > 0 ? std::min(b_slots, TC_MAX_B) : (b_slot <= 16384 ? TC_MAX_B : 3);
   t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
+  if (t.na < 2) fail(TN_ERR_UNSUPPORTED, "tensor-core rings do not fit shared memory");
   t.nbs = std::min(t.nbs, t.na);   // B' slots are released through the A slots' barriers
   // arrivals on an A slot: the TMA itself (TF32 4M), one converter group (TMA otherwise), all loaders
   t.fa_count = (t.a_tma && kid == K_TC_TF32) ? 1 : (t.a_tma ? TC_LOAD_THREADS / 2 : TC_LOAD_THREADS);
@@ -638,24 +641,32 @@ void destroy_device_state(Plan* p) {
   p->dev = nullptr;
 }
 
-static void run_chunk(Plan& p, cudaStream_t s) {
+// The steps whose dependence flags satisfy `in_class`, in plan order; a group
+// of independent small steps runs as its multi-step launches, then the rest of
+// the group alone.
+template <class Pred>
+static void launch_class(Plan& p, cudaStream_t s, Pred in_class) {
   DeviceState& ds = *p.dev;
-  const int nl = (int)p.leaves.size();
-  k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
-                                                                 ds.params, ds.counter);
-  for (size_t i = 0; i < p.steps.size(); ++i) {   // slice-dependent steps
-    if (!(p.steps[i].dep_flags & 1)) continue;
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    if (!in_class(p.steps[i].dep_flags)) continue;
     const int gi = ds.group_at.empty() ? -1 : ds.group_at[i];
     if (gi < 0) {
       launch_step(ds.launches[i], ds.ws, ds.err, s);
       continue;
     }
-    // a group of independent small steps: its multi-step launches, then the rest alone
     const DeviceState::GroupRun& gr = ds.groups[gi];
     for (const auto& m : gr.multi) launch_simt_multi(m, s);
     for (int t : gr.singles) launch_step(ds.launches[t], ds.ws, ds.err, s);
     i = (size_t)gr.end - 1;
   }
+}
+
+static void run_chunk(Plan& p, cudaStream_t s) {
+  DeviceState& ds = *p.dev;
+  const int nl = (int)p.leaves.size();
+  k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
+                                                                 ds.params, ds.counter);
+  launch_class(p, s, [](int f) { return (f & 1) != 0; });   // slice-dependent steps
   const int64_t nout = (int64_t)1 << p.root.rank;
   const int blocks = (int)std::min<int64_t>((nout + 255) / 256, 4096);
   k_root_partial<<<dim3(blocks, ds.root_groups), 256, 0, s>>>(ds.arena, p.root, p.log2_batch, ds.root_groups,
@@ -674,8 +685,7 @@ static void run_prologue(Plan& p, cudaStream_t s, int cls) {
   const int nl = (int)p.leaves.size();
   k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
                                                                  ds.params, ds.counter);
-  for (size_t i = 0; i < p.steps.size(); ++i)
-    if (p.steps[i].dep_flags == cls) launch_step(ds.launches[i], ds.ws, ds.err, s);
+  launch_class(p, s, [cls](int f) { return f == cls; });
 }
 
 // Capture run_chunk once into a graph (on a private stream, thread-local
@@ -835,7 +845,8 @@ extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_o
 }
 
 // Autotuner: for every step, time the candidate kernels in place (tensor-core
-// tiles of 32, 64 or 128 complex columns in the TF32 / BF16X3 modes, and the
+// tiles of 32, 64 or 128 complex columns in the TF32 / BF16X3 / FP16X3 modes,
+// each with either write-back order and with 3 or 4 B' ring slots, and the
 // three CUDA-core tilings where the step is small or the mode is FP32) and keep
 // the fastest.  The chunk graph is captured again on the next call.
 extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) {
@@ -875,32 +886,38 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   };
   for (size_t i = 0; i < p.steps.size(); ++i) {
     const StepDesc& d = p.steps[i];
-    auto build = [&](int kid, int tn_log, int epi) {
+    auto build = [&](int kid, int tn_log, int epi, int bslots = 0) {
       return make_launch(step_args(ds, d, kid, tn_log), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
-                         d.c_elems, true, epi);
+                         d.c_elems, true, epi, (int64_t)256 << 20, bslots);
     };
     double best = time_launch(ds.launches[i]);
-    std::vector<std::array<int, 3>> cands;   // kernel, tile width (log2 complex columns), write-back
+    std::vector<std::array<int, 4>> cands;   // kernel, tile width (log2 complex columns), write-back, B' slots
     const bool tc_mode = p.opts.precision != TN_PREC_FP32;
     const int tc_kid = tc_kernel(p.opts.precision, p.opts.complex_mult);
     if (tc_mode && d.nm >= 4)
       for (int tn_log : {7, 6, 5})
         if (tn_log <= std::max(3, d.nn))
-          for (int epi : {0, 1}) cands.push_back({tc_kid, tn_log, epi});
+          for (int epi : {0, 1})
+            for (int bs : {0, 4}) cands.push_back({tc_kid, tn_log, epi, bs});
     // CUDA-core tilings: FP32 mode, tiny steps, and low arithmetic intensity
     // (complex flops per byte moved), where a tile's fixed cost on the tensor
     // cores outweighs its few products
     const double flops = 8.0 * std::ldexp(1.0, d.nm + d.nk + d.nn + d.nb);
     const double bytes = 8.0 * (double)(d.a_elems + d.b_elems + d.c_elems);
     if (!tc_mode || best < 0.05 || flops / bytes < 48.0)
-      for (int k : {K_SIMT_64x64, K_SIMT_128x16, K_SIMT_256x4}) cands.push_back({k, -1, 0});
-    std::vector<std::array<int, 3>> seen;
+      for (int k : {K_SIMT_64x64, K_SIMT_128x16, K_SIMT_256x4}) cands.push_back({k, -1, 0, 0});
+    std::vector<std::array<int, 4>> seen;
     auto key = [](const StepLaunch& L) {
-      return std::array<int, 3>{L.kid, L.g.tn, is_tc(L.kid) ? L.tc.epi_ok : 0};
+      return std::array<int, 4>{L.kid, L.g.tn, is_tc(L.kid) ? L.tc.epi_ok : 0, is_tc(L.kid) ? L.tc.nbs : 0};
     };
     seen.push_back(key(ds.launches[i]));
-    for (auto [kid, tn_log, epi] : cands) {
-      StepLaunch L = build(kid, tn_log, epi);
+    for (auto [kid, tn_log, epi, bs] : cands) {
+      StepLaunch L;
+      try {
+        L = build(kid, tn_log, epi, bs);
+      } catch (const TnError&) {
+        continue;   // this configuration does not fit: not a candidate
+      }
       if (std::find(seen.begin(), seen.end(), key(L)) != seen.end()) continue;
       seen.push_back(key(L));
       const double t = time_launch(L);
@@ -1026,18 +1043,16 @@ extern "C" tn_status tn_plan_select_list(const tn_network_t* net, const tn_plan_
   API_END
 }
 
-extern "C" tn_status tn_plan_chunk_launches(const tn_plan_t* h, int32_t* launches) {
-  API_BEGIN
-  if (!h || !launches) fail(TN_ERR_ARG, "tn_plan_chunk_launches: NULL argument");
-  const Plan& p = h->plan;
-  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_chunk_launches: call after the first tn_contract_slices");
-  int n = 4;
+// Kernels launch_class launches for the steps of a class (memsets not counted).
+template <class Pred>
+static int class_launches(const Plan& p, Pred in_class) {
+  int n = 0;
   auto kernels_of = [&](int i) {
     const StepLaunch& L = p.dev->launches[i];
     return is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
   };
   for (size_t i = 0; i < p.steps.size(); ++i) {
-    if ((p.steps[i].dep_flags & 1) == 0) continue;
+    if (!in_class(p.steps[i].dep_flags)) continue;
     const int gi = p.dev->group_at.empty() ? -1 : p.dev->group_at[i];
     if (gi < 0) {
       n += kernels_of((int)i);
@@ -1048,7 +1063,15 @@ extern "C" tn_status tn_plan_chunk_launches(const tn_plan_t* h, int32_t* launche
     for (int t : gr.singles) n += kernels_of(t);
     i = (size_t)gr.end - 1;
   }
-  *launches = n;
+  return n;
+}
+
+extern "C" tn_status tn_plan_chunk_launches(const tn_plan_t* h, int32_t* launches) {
+  API_BEGIN
+  if (!h || !launches) fail(TN_ERR_ARG, "tn_plan_chunk_launches: NULL argument");
+  const Plan& p = h->plan;
+  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_chunk_launches: call after the first tn_contract_slices");
+  *launches = 4 + class_launches(p, [](int f) { return (f & 1) != 0; });
   API_END
 }
 
@@ -1057,12 +1080,7 @@ extern "C" tn_status tn_plan_batch_launches(const tn_plan_t* h, int32_t* launche
   if (!h || !launches) fail(TN_ERR_ARG, "tn_plan_batch_launches: NULL argument");
   const Plan& p = h->plan;
   if (!p.dev) fail(TN_ERR_ARG, "tn_plan_batch_launches: call after the first tn_contract_slices");
-  int n = 0;
-  for (size_t i = 0; i < p.steps.size(); ++i) {
-    if (p.steps[i].dep_flags != 2) continue;
-    const StepLaunch& L = p.dev->launches[i];
-    n += is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
-  }
+  const int n = class_launches(p, [](int f) { return f == 2; });
   *launches = n > 0 ? n + 1 : 0;   // + the leaf select ahead of them
   API_END
 }

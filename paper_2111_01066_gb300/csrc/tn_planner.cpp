@@ -927,15 +927,17 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       }
       node_order.swap(lw);
       border_of.swap(lb);
-      // Execution order.  First the steps that depend on no slice (they run
-      // once per plan or per batch, before any chunk), in post-order.  Then the
-      // small slice-dependent steps (under 2^20 multiply-adds per chunk: the
+      // Execution order.  First the steps that depend on neither the slice id
+      // nor the closed output bits (run once per plan), in post-order; then
+      // those that depend on the closed bits only (run once per batch); then
+      // the slice-dependent ones (run in every chunk).  Within the last two
+      // classes, the small steps (under 2^20 multiply-adds per chunk: the
       // CUDA-core kernels) whose subtree holds only such steps, leaves and
-      // prologue results, one group per dependency level: a group's steps are
-      // independent and run as one launch.  Then the other slice-dependent
-      // steps in post-order, where the remaining small steps are deferred and
-      // emitted the same way, level by level, right before the first step
-      // that reads one of them.
+      // results of earlier classes come first, one group per dependency level
+      // (a group's steps are independent and run as one launch); then the
+      // other steps of the class in post-order, where the remaining small
+      // steps are deferred and emitted the same way, level by level, right
+      // before the first step that reads one of them.
       exec.clear();
       exec_group.clear();
       std::vector<char> pend(nm, 0), hoist(nm, 0);
@@ -968,40 +970,43 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
         }
       };
       for (int mi : order)
-        if (!(nflag[L + mi] & 1)) {
+        if (nflag[L + mi] == 0) {
           exec.push_back(mi);
           exec_group.push_back(-1);
         }
-      std::vector<int> hoisted;
-      for (int mi : order) {
-        if (!(nflag[L + mi] & 1) || !small(mi)) continue;
-        bool ok = true;
-        for (int ch : {T.merges[mi].first, T.merges[mi].second})
-          if (ch >= L && (nflag[ch] & 1) && !hoist[ch - L]) ok = false;
-        if (ok) {
-          hoist[mi] = 1;
-          hoisted.push_back(mi);
+      for (int cls : {2, 1}) {   // per batch, then per chunk (flags 1 or 3)
+        auto in_cls = [&](int v) { return cls == 2 ? nflag[v] == 2 : (nflag[v] & 1) != 0; };
+        std::vector<int> hoisted;
+        for (int mi : order) {
+          if (!in_cls(L + mi) || !small(mi)) continue;
+          bool ok = true;
+          for (int ch : {T.merges[mi].first, T.merges[mi].second})
+            if (ch >= L && in_cls(ch) && !hoist[ch - L]) ok = false;
+          if (ok) {
+            hoist[mi] = 1;
+            hoisted.push_back(mi);
+          }
         }
-      }
-      emit_levels(hoisted, hoist);
-      auto flush = [&]() {
-        emit_levels(pending, pend);
-        for (int mi : pending) pend[mi] = 0;
-        pending.clear();
-      };
-      for (int mi : order) {
-        if (!(nflag[L + mi] & 1) || hoist[mi]) continue;
-        if (small(mi)) {
-          pending.push_back(mi);
-          pend[mi] = 1;
-          continue;
+        emit_levels(hoisted, hoist);
+        auto flush = [&]() {
+          emit_levels(pending, pend);
+          for (int mi : pending) pend[mi] = 0;
+          pending.clear();
+        };
+        for (int mi : order) {
+          if (!in_cls(L + mi) || hoist[mi]) continue;
+          if (small(mi)) {
+            pending.push_back(mi);
+            pend[mi] = 1;
+            continue;
+          }
+          const int x = T.merges[mi].first, y = T.merges[mi].second;
+          if ((x >= L && pend[x - L]) || (y >= L && pend[y - L])) flush();
+          exec.push_back(mi);
+          exec_group.push_back(-1);
         }
-        const int x = T.merges[mi].first, y = T.merges[mi].second;
-        if ((x >= L && pend[x - L]) || (y >= L && pend[y - L])) flush();
-        exec.push_back(mi);
-        exec_group.push_back(-1);
+        flush();
       }
-      flush();
     }
     // best-fit arena allocator
     std::vector<std::pair<int64_t, int64_t>> freel;  // (offset, size)
@@ -1186,7 +1191,8 @@ Plan* build_plan(const Network& net, const tn_plan_opts& o) {
       if (v.a_node == u.c_node || v.b_node == u.c_node || u.a_node == v.c_node || u.b_node == v.c_node ||
           overlap(u.c_off, u.c_elems, v.a_off, v.a_elems) || overlap(u.c_off, u.c_elems, v.b_off, v.b_elems) ||
           overlap(v.c_off, v.c_elems, u.a_off, u.a_elems) || overlap(v.c_off, v.c_elems, u.b_off, u.b_elems) ||
-          overlap(u.c_off, u.c_elems, v.c_off, v.c_elems) || (v.dep_flags & 1) == 0 || (u.dep_flags & 1) == 0)
+          overlap(u.c_off, u.c_elems, v.c_off, v.c_elems) || u.dep_flags == 0 || v.dep_flags == 0 ||
+          (u.dep_flags == 2) != (v.dep_flags == 2))   // one class: per batch (2) or per chunk (1, 3)
         fail(TN_ERR_PLAN, "internal: a step group is not independent");
     }
   }

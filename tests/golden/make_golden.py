@@ -80,12 +80,17 @@ def read_sliced(name: str):
 
 
 def write_block(name: str) -> None:
-    """For every candidate plan in <name>_plans.json: the FP64 sum over
-    slice ids block_first .. block_first + check_slices - 1 of the network with
-    the candidate's sliced wires fixed (slice id s sets wire j to bit j of s),
-    contracted by the oracle along an order it builds from the candidate's tree
-    shape (tensornet.CircuitNetwork.tree_order), sub-sliced by the oracle
-    itself under 2^27 entries."""
+    """For every candidate plan in <name>_plans.json, two FP64 partial sums of
+    the network with the candidate's sliced wires fixed (slice id s sets wire j
+    to bit j of s), contracted by the oracle along an order it builds from the
+    candidate's tree shape (tensornet.CircuitNetwork.tree_order), sub-sliced by
+    the oracle itself under 2^27 entries: over slice ids block_first ..
+    block_first + check_slices - 1 (the start of the benchmark's timed block),
+    and over a seeded sample of as many slice ids spread over all 2^S
+    (rqcgen.slice_sample, seed of the workload).  The second is the scale of a
+    typical partial sum: a block whose fixed slice bits route every path
+    through the fSim entries cos(pi/2) ~ 6e-17 sums to almost nothing, and is
+    then compared on that scale."""
     with open(os.path.join(HERE, f"{name}_plans.json")) as f:
         data = json.load(f)
     circ, open_mask, closed = rqcgen.config_circuit(name)
@@ -94,26 +99,29 @@ def write_block(name: str) -> None:
     path = os.path.join(HERE, f"{name}_block_amplitudes.txt")
     with open(path, "w") as f:
         f.write(f"# {name}: n={circ.n_qubits} open_mask={open_mask:#x} closed={closed:#x} oracle=tensornet complex128; "
-                f"per candidate plan: partial sum over its first timed slices\n")
+                f"per candidate plan: partial sums over its first timed slices and over a seeded slice sample\n")
         for c in data["candidates"]:
             wires = [tuple(w) for w in c["sliced_wires"]]
             t0 = time.time()
             merges, extra = net.plan_along_tree(wires, c["leaf_of_gate"], [tuple(p) for p in c["step_nodes"]],
                                                 max_log2=27)
             ids = range(c["block_first"], c["block_first"] + c["check_slices"])
-            amps = net.contract_in_order(merges, wires, ids, extra)
-            dt = time.time() - t0
-            f.write(f"# candidate seed={c['seed']} mem_weight={c['mem_weight']} slices={ids.start}..{ids.stop - 1} "
-                    f"count={amps.size} extra={len(extra)} ({dt:.1f} s)\n")
-            f.write("# wires " + " ".join(f"{q},{t}" for q, t in wires) + "\n")
-            for a in amps:
-                f.write(f"{a.real:.17e} {a.imag:.17e}\n")
-            print(f"seed {c['seed']} w {c['mem_weight']}: {dt:.1f} s", flush=True)
+            sample = [int(x) for x in rqcgen.slice_sample(c["log2_slices"], c["check_slices"],
+                                                         rqcgen.CONFIGS[name]["seed"])]
+            for kind, sl in (("block", list(ids)), ("sample", sample)):
+                amps = net.contract_in_order(merges, wires, sl, extra)
+                f.write(f"# candidate seed={c['seed']} mem_weight={c['mem_weight']} kind={kind} "
+                        f"slices={','.join(str(x) for x in sl)} count={amps.size} extra={len(extra)}\n")
+                f.write("# wires " + " ".join(f"{q},{t}" for q, t in wires) + "\n")
+                for a in amps:
+                    f.write(f"{a.real:.17e} {a.imag:.17e}\n")
+            print(f"seed {c['seed']} w {c['mem_weight']}: {time.time() - t0:.1f} s", flush=True)
     print(path)
 
 
 def read_block(name: str) -> dict:
-    """{(seed, mem_weight): (wires, first slice id, slice count, amplitudes)}."""
+    """{(seed, mem_weight): {"block": section, "sample": section}}, a section
+    being {"slices": [ids], "wires": [(q, t)], "amps": array}."""
     path = os.path.join(HERE, f"{name}_block_amplitudes.txt")
     out = {}
     cur = None
@@ -121,17 +129,16 @@ def read_block(name: str) -> dict:
         for line in f:
             if line.startswith("# candidate"):
                 kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
-                lo, hi = (int(x) for x in kv["slices"].split(".."))
-                cur = {"key": (int(kv["seed"]), float(kv["mem_weight"])), "first": lo, "count": hi - lo + 1,
-                       "amps": []}
-                out[cur["key"]] = cur
+                cur = {"slices": [int(x) for x in kv["slices"].split(",")], "amps": []}
+                out.setdefault((int(kv["seed"]), float(kv["mem_weight"])), {})[kv["kind"]] = cur
             elif line.startswith("# wires") and cur is not None:
                 cur["wires"] = [tuple(int(x) for x in w.split(",")) for w in line.split()[2:]]
             elif not line.startswith("#") and line.strip() and cur is not None:
                 re_, im_ = line.split()
                 cur["amps"].append(float(re_) + 1j * float(im_))
     for v in out.values():
-        v["amps"] = np.array(v["amps"])
+        for sec in v.values():
+            sec["amps"] = np.array(sec["amps"])
     return out
 
 

@@ -366,11 +366,10 @@ def test_select_list_and_device_sync_validate_before_device_work(tn):
 
 @pytest.mark.parametrize("name", ["c1", "c2", "c3"])
 def test_step_groups_are_consecutive_independent_and_small(tn, name):
-    """Small slice-dependent steps come in groups that the executor runs as one
-    launch: a group's steps are consecutive, depend on the slice id, read no
-    result of another step of the group, are under 2^20 multiply-adds, and all
-    steps that depend on no slice come first; the plan's per-chunk launch
-    count stays what the kernels need (checked on the GPU)."""
+    """Small steps come in groups that the executor runs as one launch: a
+    group's steps are consecutive, of one dependence class (per batch or per
+    chunk), read no result of another step of the group, and are under 2^20
+    multiply-adds; steps run once per plan, then once per batch, then per chunk."""
     cfg = rqcgen.CONFIGS[name]
     circ, om, _ = rqcgen.config_circuit(name)
     plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
@@ -380,12 +379,8 @@ def test_step_groups_are_consecutive_independent_and_small(tn, name):
     _, nodes = plan.tree(circ.n_gates)
     lay = [plan.step_layout(i) for i in range(n)]
     shapes = plan.step_shapes()
-    seen_chunk = False
-    for i, l in enumerate(lay):
-        if l["dep_flags"] & 1:
-            seen_chunk = True
-        else:
-            assert not seen_chunk, "steps without slice dependence run first"
+    cls = [0 if l["dep_flags"] == 0 else (1 if l["dep_flags"] == 2 else 2) for l in lay]
+    assert cls == sorted(cls), "once per plan, then once per batch, then per chunk"
     groups = {}
     for i, l in enumerate(lay):
         if l["group"] >= 0:
@@ -394,7 +389,7 @@ def test_step_groups_are_consecutive_independent_and_small(tn, name):
     for g, members in groups.items():
         assert members == list(range(members[0], members[-1] + 1))
         for i in members:
-            assert lay[i]["dep_flags"] & 1
+            assert (lay[i]["dep_flags"] == 2) == (lay[members[0]]["dep_flags"] == 2) and lay[i]["dep_flags"] > 0
             assert sum(shapes[i]) < 20
             for x in nodes[i]:
                 assert x - n_leaves not in members or x < n_leaves

@@ -248,25 +248,54 @@ def test_c3_pool_candidates_against_golden(env, cand):
                 f"c3 pool candidate {cand} (seed {c['seed']}, weight {c['mem_weight']})", 5e-4)
 
 
+def _slice_sum(tn, torch, plan, ids, bits, k_open):
+    """Sum over the given slice ids, contiguous runs contracted per call."""
+    out = torch.zeros(2 << k_open, dtype=torch.float64, device="cuda")
+    ids = sorted(ids)
+    i = 0
+    while i < len(ids):
+        j = i + 1
+        while j < len(ids) and ids[j] == ids[j - 1] + 1:
+            j += 1
+        plan.contract_slices(ids[i], j - i, [bits], out)
+        i = j
+    plan.sync()
+    return out.cpu().numpy().view(np.complex128)
+
+
 @pytest.mark.parametrize("cand", range(6))
 def test_c5_timed_block_against_golden(env, cand):
     """53 qubits, 20 cycles, 2^20 slices: for every plan the benchmark may time
-    (the 6 best-modeled of its pool, tests/golden/c5_plans.json), the first 16
-    slice ids of the benchmark's timed 1024-slice block, contracted in the
-    benchmark's configuration (1024-slice chunks), match the oracle's FP64
-    partial sum over the same slices."""
+    (the 6 best-modeled of its pool, tests/golden/c5_plans.json), contracted in
+    the benchmark's configuration (1024-slice chunks), against the oracle's FP64
+    partial sums (a) over 16 slice ids spread over all 2^20 (a seeded sample),
+    norm-wise and element-wise, and (b) over the first 16 slice ids of the
+    benchmark's timed 1024-slice block, norm-wise on the scale of a typical
+    16-slice sum: a block whose fixed slice bits route every path through the
+    fSim entries cos(pi/2) ~ 6e-17 sums to almost nothing (the first candidate's
+    does), and its relative error says nothing about the method."""
     tn, torch = env
     from tests.golden.make_golden import read_block
     c = _pool_candidates("c5")[cand]
     gold = read_block("c5")[(c["seed"], c["mem_weight"])]
-    assert gold["first"] == c["block_first"] and gold["wires"] == [tuple(w) for w in c["sliced_wires"]]
+    block, sample = gold["block"], gold["sample"]
+    assert block["slices"][0] == c["block_first"] and block["wires"] == [tuple(w) for w in c["sliced_wires"]]
     circ, om, cb = rqcgen.config_circuit("c5")
     plan = _pool_plan(tn, "c5", c)
-    assert rqcgen.timed_block_first(plan.info()["log2_slices"], 1024, rqcgen.CONFIGS["c5"]["seed"]) == gold["first"]
-    got = _run_plan(tn, torch, plan, gold["first"], gold["count"], [cb], 6)
-    _check_plan(got, gold["amps"], circ.n_qubits, "bf16x3",
-                f"c5 pool candidate {cand} (seed {c['seed']}, weight {c['mem_weight']}) slices "
-                f"{gold['first']}..{gold['first'] + gold['count'] - 1}", partial=True)
+    assert rqcgen.timed_block_first(plan.info()["log2_slices"], 1024, rqcgen.CONFIGS["c5"]["seed"]) == \
+        block["slices"][0]
+    tag = f"c5 pool candidate {cand} (seed {c['seed']}, weight {c['mem_weight']})"
+    got = _slice_sum(tn, torch, plan, sample["slices"], cb, 6)
+    _check_plan(got, sample["amps"], circ.n_qubits, "bf16x3", tag + " seeded 16-slice sample", partial=True)
+    got = _slice_sum(tn, torch, plan, block["slices"], cb, 6)
+    scale = max(np.linalg.norm(block["amps"]), np.linalg.norm(sample["amps"]))
+    err = float(np.linalg.norm(got - block["amps"]) / scale)
+    degenerate = np.linalg.norm(block["amps"]) < 1e-6 * np.linalg.norm(sample["amps"])
+    print(f"{tag} timed block {block['slices'][0]}..{block['slices'][-1]}: error {err:.3e} on the scale of a "
+          f"16-slice sum{' (near-zero block)' if degenerate else ''}")
+    assert err < PLAN_TOL["bf16x3"]
+    if not degenerate:
+        _check_plan(got, block["amps"], circ.n_qubits, "bf16x3", tag + " timed block", partial=True)
 
 
 @pytest.mark.parametrize("prec,cm", [("bf16x3", 4), ("bf16x3", 3), ("fp16x3", 4), ("fp16x3", 3), ("tf32", 4),
