@@ -8,17 +8,27 @@
 
 namespace tnx {
 
+// Shared memory of one tile of a tiling.
+template <int TM, int TN, int TK>
+struct SimtSmem {
+  float2 As[TK][TM];
+  float2 Bs[TK][TN];
+  int64_t offCm[TM];
+  int64_t offCn[TN];
+};
+
 // One (m tile bx, n tile by) of a GEMM for instances bz, bz + gz, ... (the
 // body of both kernels below; every thread of the block calls it).
 template <int TM, int TN, int TK, int RM, int RN>
-__device__ __forceinline__ void simt_tile(const GemmArgs& g, int bx, int by, int bz, int gz) {
+__device__ __forceinline__ void simt_tile(const GemmArgs& g, int bx, int by, int bz, int gz,
+                                          SimtSmem<TM, TN, TK>& sm) {
   constexpr int NTX = TM / RM, NTY = TN / RN, NT = NTX * NTY;
   constexpr int AE = (TM * TK + NT - 1) / NT;
   constexpr int BE = (TK * TN + NT - 1) / NT;
-  __shared__ float2 As[TK][TM];
-  __shared__ float2 Bs[TK][TN];
-  __shared__ int64_t offCm[TM];
-  __shared__ int64_t offCn[TN];
+  auto& As = sm.As;
+  auto& Bs = sm.Bs;
+  auto& offCm = sm.offCm;
+  auto& offCn = sm.offCn;
   const int tid = threadIdx.x;
   const int tx = tid % NTX, ty = tid / NTX;
   const int TMv = 1 << g.tm, TKv = 1 << g.tk, TNv = 1 << g.tn;
@@ -147,19 +157,26 @@ __device__ __forceinline__ void simt_tile(const GemmArgs& g, int bx, int by, int
 template <int TM, int TN, int TK, int RM, int RN>
 __global__ void __launch_bounds__((TM / RM) * (TN / RN))
 k_cgemm_simt(const GemmArgs g) {
-  simt_tile<TM, TN, TK, RM, RN>(g, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z);
+  __shared__ SimtSmem<TM, TN, TK> sm;
+  simt_tile<TM, TN, TK, RM, RN>(g, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm);
 }
 
 // Several independent GEMMs in one launch (a group of small steps that
 // neither read nor write what another of the group writes): block b runs
 // block b - start[i] of GEMM i, where start[i] <= b < start[i + 1] (start[n]
 // is the grid size), decoded as (m tile, n tile, instance) with the m tile
-// fastest, exactly as that GEMM's own grid would.
-template <int TM, int TN, int TK, int RM, int RN>
-__global__ void __launch_bounds__((TM / RM) * (TN / RN))
-k_cgemm_simt_multi(const GemmArgs* __restrict__ gs, const int32_t* __restrict__ start, int32_t n) {
+// fastest, exactly as that GEMM's own grid would, with that GEMM's tiling
+// tiling[i] (0: 64x64, 1: 128x16, 2: 256x4; all three use 256 threads).
+__global__ void __launch_bounds__(256)
+k_cgemm_simt_multi(const GemmArgs* __restrict__ gs, const int32_t* __restrict__ start,
+                   const int8_t* __restrict__ tiling, int32_t n) {
   __shared__ GemmArgs sg;
   __shared__ int s_i;
+  __shared__ union {   // one tiling per block: their tiles share the space
+    SimtSmem<64, 64, 8> t0;
+    SimtSmem<128, 16, 16> t1;
+    SimtSmem<256, 4, 16> t2;
+  } sm;
   const int b = blockIdx.x;
   if (threadIdx.x == 0) {
     int i = 0;
@@ -178,7 +195,18 @@ k_cgemm_simt_multi(const GemmArgs* __restrict__ gs, const int32_t* __restrict__ 
   const int gx = 1 << (sg.nm - sg.tm), gy = 1 << (sg.nn - sg.tn);
   const int gz = sg.n_inst < 65535 ? sg.n_inst : 65535;
   const int lb = b - start[i];
-  simt_tile<TM, TN, TK, RM, RN>(sg, lb % gx, (lb / gx) % gy, lb / (gx * gy), gz);
+  const int bx = lb % gx, by = (lb / gx) % gy, bz = lb / (gx * gy);
+  switch (tiling[i]) {   // block-uniform
+    case 0:
+      simt_tile<64, 64, 8, 4, 4>(sg, bx, by, bz, gz, sm.t0);
+      break;
+    case 1:
+      simt_tile<128, 16, 16, 4, 2>(sg, bx, by, bz, gz, sm.t1);
+      break;
+    default:
+      simt_tile<256, 4, 16, 4, 1>(sg, bx, by, bz, gz, sm.t2);
+      break;
+  }
 }
 
 }  // namespace tnx

@@ -66,6 +66,7 @@ constexpr int TC_A_SLOT = TC_M * TC_KP * 4;
 constexpr int TC_TMEM_COLS = 512;
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;           // 4 s per wait
 constexpr int TC_MIN_SMEM = 120 * 1024;                  // keeps one CTA per SM
+constexpr int TC_MAX_SMEM = 227 * 1024;                  // the dynamic shared-memory opt-in
 
 enum TcMode { TC_TF32 = 0, TC_BF16X3 = 1, TC_FP16X3 = 2 };
 

@@ -273,19 +273,6 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.ls_mt = g.nm - g.tm;
   t.ls_kc = g.nk - g.tk;
   setup_tma(L, a_bits, n_lin);
-  // rings: B' slots first (3, or 4 when small), the rest of the budget to A slots
-  const int b_slot = npl * b_plane;
-  const int budget = 220 * 1024 - 4096 - TC_EPI_BYTES;
-  t.nbs = b_slots > 0 ? std::min(b_slots, TC_MAX_B) : (b_slot <= 16384 ? TC_MAX_B : 3);
-  t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
-  if (t.na < 2) fail(TN_ERR_UNSUPPORTED, "tensor-core rings do not fit shared memory");
-  t.nbs = std::min(t.nbs, t.na);   // B' slots are released through the A slots' barriers
-  // arrivals on an A slot: the TMA itself (TF32 4M), one converter group (TMA otherwise), all loaders
-  t.fa_count = (t.a_tma && kid == K_TC_TF32) ? 1 : (t.a_tma ? TC_LOAD_THREADS / 2 : TC_LOAD_THREADS);
-  // as many accumulator sets as fit the 512 TMEM columns (at most 8): narrow
-  // tiles let the MMAs run several tiles ahead of the epilogue
-  t.n_acc = std::max(1, std::min(TC_MAX_ACC, TC_TMEM_COLS / ((tc_is_3m(kid) ? 3 : 2) * t.tn_c)));
-  L.smem = std::max(t.na * geo.a_slot + t.nbs * b_slot + 4096 + TC_EPI_BYTES + 1024, TC_MIN_SMEM);
   // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
   t.epi_ok = 0;
   if (g.tm >= 5 && g.tn >= 4) {
@@ -306,6 +293,22 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
     while (run_s < 5 && bits[run_s].first == run_s) ++run_s;
     t.epi_ok = epi_mode >= 0 ? epi_mode : (run_s > run_d && run_d < 2 ? 1 : 0);
   }
+  // rings: B' slots first (3, or 4 when small), the rest of the shared memory
+  // to A slots: up to the 227 KB opt-in, less the barriers, the alignment slack
+  // and the write-back staging (only when the staged order is used)
+  const int b_slot = npl * b_plane;
+  const int epi_bytes = t.epi_ok ? TC_EPI_BYTES : 0;
+  const int budget = TC_MAX_SMEM - 4096 - 1024 - epi_bytes;
+  t.nbs = b_slots > 0 ? std::min(b_slots, TC_MAX_B) : (b_slot <= 16384 ? TC_MAX_B : 3);
+  t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
+  if (t.na < 2) fail(TN_ERR_UNSUPPORTED, "tensor-core rings do not fit shared memory");
+  t.nbs = std::min(t.nbs, t.na);   // B' slots are released through the A slots' barriers
+  // arrivals on an A slot: the TMA itself (TF32 4M), one converter group (TMA otherwise), all loaders
+  t.fa_count = (t.a_tma && kid == K_TC_TF32) ? 1 : (t.a_tma ? TC_LOAD_THREADS / 2 : TC_LOAD_THREADS);
+  // as many accumulator sets as fit the 512 TMEM columns (at most 8): narrow
+  // tiles let the MMAs run several tiles ahead of the epilogue
+  t.n_acc = std::max(1, std::min(TC_MAX_ACC, TC_TMEM_COLS / ((tc_is_3m(kid) ? 3 : 2) * t.tn_c)));
+  L.smem = std::max(t.na * geo.a_slot + t.nbs * b_slot + 4096 + epi_bytes + 1024, TC_MIN_SMEM);
   return L;
 }
 
@@ -386,16 +389,18 @@ struct DeviceState {
   int root_groups = 1;
   std::vector<StepLaunch> launches;
   // groups of small independent steps (StepDesc::group): per group, the steps
-  // [first, end) and the launches that run them -- one multi-step launch per
-  // CUDA-core kernel variant used by two or more of its steps, single launches
-  // for the rest; rebuilt whenever the kernels are chosen again
+  // [first, end) and the launches that run them -- one multi-step launch for
+  // all its CUDA-core steps (each block with its step's tiling), single
+  // launches for its tensor-core steps; rebuilt whenever the kernels are
+  // chosen again
   struct GroupRun {
     int first = 0, end = 0;
     std::vector<int> singles;                  // steps launched alone
     struct Multi {
-      int kid = 0, blocks = 0, n = 0;
+      int blocks = 0, n = 0;
       GemmArgs* args = nullptr;                // device: n GemmArgs
       int32_t* start = nullptr;                // device: n + 1 block offsets
+      int8_t* tiling = nullptr;                // device: n CUDA-core tilings (kernel ids 0-2)
       std::vector<float*> amax;                // FP16X3: result maxima to clear first
     };
     std::vector<Multi> multi;
@@ -448,19 +453,7 @@ static GemmArgs step_args(const DeviceState& ds, const StepDesc& d, int kid, int
 
 static void launch_simt_multi(const DeviceState::GroupRun::Multi& m, cudaStream_t s) {
   for (float* am : m.amax) CK(cudaMemsetAsync(am, 0, sizeof(float), s));
-  switch (m.kid) {
-    case K_SIMT_64x64:
-      k_cgemm_simt_multi<64, 64, 8, 4, 4><<<m.blocks, 256, 0, s>>>(m.args, m.start, m.n);
-      break;
-    case K_SIMT_128x16:
-      k_cgemm_simt_multi<128, 16, 16, 4, 2><<<m.blocks, 256, 0, s>>>(m.args, m.start, m.n);
-      break;
-    case K_SIMT_256x4:
-      k_cgemm_simt_multi<256, 4, 16, 4, 1><<<m.blocks, 256, 0, s>>>(m.args, m.start, m.n);
-      break;
-    default:
-      fail(TN_ERR_UNSUPPORTED, "kernel variant not built");
-  }
+  k_cgemm_simt_multi<<<m.blocks, 256, 0, s>>>(m.args, m.start, m.tiling, m.n);
 }
 
 // Group runs from the plan's step groups and the kernels chosen so far.
@@ -484,20 +477,17 @@ static void build_groups(Plan& p, DeviceState& ds) {
     DeviceState::GroupRun gr;
     gr.first = (int)i;
     gr.end = (int)j;
-    std::vector<std::vector<int>> by_kid(K_COUNT);
+    std::vector<int> simt;
     for (size_t t = i; t < j; ++t) {
-      const int kid = ds.launches[t].kid;
-      if (is_tc(kid)) gr.singles.push_back((int)t);
-      else by_kid[kid].push_back((int)t);
+      if (is_tc(ds.launches[t].kid)) gr.singles.push_back((int)t);
+      else simt.push_back((int)t);
     }
-    for (int kid = 0; kid < K_COUNT; ++kid) {
-      if (by_kid[kid].size() == 1) gr.singles.push_back(by_kid[kid][0]);
-      if (by_kid[kid].size() < 2) continue;
+    if (simt.size() == 1) gr.singles.push_back(simt[0]);
+    if (simt.size() >= 2) {
       DeviceState::GroupRun::Multi m;
-      m.kid = kid;
-      m.n = (int)by_kid[kid].size();
+      m.n = (int)simt.size();
       gr.multi.push_back(m);
-      pending.push_back({ds.groups.size(), by_kid[kid]});
+      pending.push_back({ds.groups.size(), simt});
     }
     for (size_t t = i; t < j; ++t) ds.group_at[t] = (int)ds.groups.size();
     ds.groups.push_back(gr);
@@ -509,6 +499,7 @@ static void build_groups(Plan& p, DeviceState& ds) {
   for (auto& pm : pending) {
     bytes = (bytes + 255) / 256 * 256 + sizeof(GemmArgs) * pm.second.size();
     bytes = (bytes + 15) / 16 * 16 + sizeof(int32_t) * (pm.second.size() + 1);
+    bytes += pm.second.size();   // tilings
   }
   std::vector<uint8_t> host(bytes, 0);
   CK(cudaMalloc(&ds.group_buf, bytes));
@@ -522,10 +513,13 @@ static void build_groups(Plan& p, DeviceState& ds) {
     off = (off + 15) / 16 * 16;
     const size_t start_off = off;
     off += sizeof(int32_t) * (pm.second.size() + 1);
+    const size_t tiling_off = off;
+    off += pm.second.size();
     int32_t blocks = 0;
     for (size_t q = 0; q < pm.second.size(); ++q) {
       const GemmArgs& g = ds.launches[pm.second[q]].g;
       std::memcpy(host.data() + args_off + q * sizeof(GemmArgs), &g, sizeof(GemmArgs));
+      host[tiling_off + q] = (uint8_t)ds.launches[pm.second[q]].kid;   // K_SIMT_* are 0..2
       const int64_t nb = ((int64_t)1 << (g.nm - g.tm)) * ((int64_t)1 << (g.nn - g.tn)) *
                          std::min<int64_t>(g.n_inst, 65535);
       if (blocks + nb > 0x7fffffff) fail(TN_ERR_UNSUPPORTED, "step group grid too large");
@@ -537,6 +531,7 @@ static void build_groups(Plan& p, DeviceState& ds) {
     m.blocks = blocks;
     m.args = reinterpret_cast<GemmArgs*>(ds.group_buf + args_off);
     m.start = reinterpret_cast<int32_t*>(ds.group_buf + start_off);
+    m.tiling = reinterpret_cast<int8_t*>(ds.group_buf + tiling_off);
   }
   CK(cudaMemcpy(ds.group_buf, host.data(), bytes, cudaMemcpyHostToDevice));
 }
