@@ -135,10 +135,18 @@ typedef struct tn_plan_opts {
     const int32_t* forced_slice_t;      /* internal wires only: 1 <= t < gates on that qubit */
     double   mem_weight;             /* order-search cost = MACs + mem_weight * elements moved
                                         (<= 0: 32) */
+    int32_t  sm_pairs;               /* 1: tensor-core steps of 4M products with at least two
+                                        full 128-row m tiles may run on SM pairs (cta_group::2:
+                                        two SMs share each MMA of 256 rows, each holding its
+                                        128 rows of A and half of B'); 0: one SM per tile.
+                                        Results agree within the precision's rounding either
+                                        way (the FP32 summation order of an MMA may differ).
+                                        An implementation choice: the paper's processors have
+                                        no counterpart.  Other values: TN_ERR_ARG */
 } tn_plan_opts;
 
 /* Fill opts with defaults: no open qubits, bound 2^30, no forced slices, seed 1,
- * 64 trials, FP32, 4M, automatic batch, 96 GiB arena.  Index permutations are
+ * 64 trials, FP32, 4M, automatic batch, 96 GiB arena, SM pairs on.  Index permutations are
  * always folded into the contraction's operand loads and result stores (SI,
  * figure S7a): there is no separate permute pass on the plan path.
  * Forced slices: the given wires take slice bits 0..n_forced_slices-1 (in the
@@ -268,7 +276,8 @@ tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int3
 /* Autotuner (after one tn_contract_slices call): times candidate kernels for
  * every step in place on `stream` -- tensor-core tiles of 32, 64 or 128
  * complex columns in the TF32 / BF16X3 / FP16X3 modes, each with either
- * write-back order and with the default or a deeper ring of B' slots, and the
+ * write-back order, with the default or a deeper ring of B' slots and, where
+ * tn_plan_opts.sm_pairs allows, on one SM or on SM pairs, and the
  * three CUDA-core tilings for steps under 50 us, of low arithmetic intensity
  * or in the FP32 mode -- each `reps` times, and keeps the fastest for later
  * calls.  Synchronises `stream`; the arena contents are
@@ -384,9 +393,10 @@ tn_status tn_permute(const float* in, float* out, int32_t rank, const int32_t* p
  * arbitrary int32 ids, listed in storage order (position 0 fastest); a wire in
  * both A and B is contracted; c_wires must be the remaining wires in any order.
  * `batch` independent instances are stored back to back in each array.
- * precision and complex_mult as in tn_plan_opts.  Asynchronous on stream; a
- * device-side error (a bounded wait of the tensor-core kernel that ran out,
- * leaving C incomplete) is reported by the next tn_device_sync(). */
+ * precision and complex_mult as in tn_plan_opts; tensor-core products run on
+ * SM pairs wherever tn_plan_opts.sm_pairs = 1 would let them.  Asynchronous on
+ * stream; a device-side error (a bounded wait of the tensor-core kernel that
+ * ran out, leaving C incomplete) is reported by the next tn_device_sync(). */
 tn_status tn_contract_pair(const float* a, const int32_t* a_wires, int32_t a_rank,
                            const float* b, const int32_t* b_wires, int32_t b_rank,
                            float* c, const int32_t* c_wires, int32_t c_rank,

@@ -51,7 +51,7 @@ constexpr int TC_M = 128;
 constexpr int TC_TK = 16;            // complex k per pipeline stage
 constexpr int TC_KP = 2 * TC_TK;     // real K' per stage
 constexpr int TC_MAX_A = 8;           // A ring slots
-constexpr int TC_MAX_B = 4;           // B' ring slots
+constexpr int TC_MAX_B = 8;           // B' ring slots
 constexpr int TC_MAX_ACC = 8;         // TMEM accumulator sets
 constexpr int TC_EPI_WARPS = 4;
 constexpr int TC_MMA_WARP = 4;
@@ -153,6 +153,9 @@ struct TcArgs {
   float2* c_part;
   int64_t c_part_stride;
   int32_t ls_split, ls_nt, ls_mt, ls_kc;   // log2 of n_split, n_nt, n_mt, n_kc (powers of two)
+  // SM pairs: a work unit is a pair of m tiles (n_mt counts pairs); the CTA of
+  // cluster rank r takes m tile 2 mt + r and the B' rows [r N'/2, (r + 1) N'/2)
+  int32_t pair;
 };
 
 // Work unit `tile` -> split index, n tile, m tile, instance: shifts and masks
@@ -202,6 +205,9 @@ __device__ __forceinline__ uint64_t gtimer() {
   return t;
 }
 // Bounded wait: true when the phase completed, false on abort or deadline.
+// DRAIN: keep waiting after an abort (for work already in flight), still
+// within the limit.
+template <bool DRAIN = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag, int32_t* err,
                                           uint64_t limit_ns = TC_WAIT_NS) {
   if (mbar_try_wait(a, parity)) return true;
@@ -209,7 +215,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile 
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(a, parity)) return true;
     if ((i & 255) == 0) {
-      if (*abort_flag) return false;
+      if (!DRAIN && *abort_flag) return false;
       if (gtimer() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicExch(err, TN_ERR_TIMEOUT);
@@ -286,6 +292,47 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
 }
+// ---- SM pairs (cta_group::2): two CTAs of a 2-CTA cluster share each MMA
+// (M = 256: 128 A rows and half of B' in each CTA's shared memory, each CTA's
+// accumulator rows in its own TMEM); the even CTA issues the MMAs.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the object at CTA-local shared address `a` in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_cta(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// One arrival on a barrier of the peer CTA.  The default (CTA-scope) release:
+// the cluster-scope form waits for every outstanding memory operation first
+// (measured ~1,700 cycles per arrival under the epilogue's store stream), and
+// what it would order here -- operand writes to this CTA's own shared memory,
+// completed before the local barrier the caller waited on -- needs no more.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// commit of the pair's MMAs: one arrival on the barrier at this offset in both CTAs
+__device__ __forceinline__ void tc_commit_pair(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          mbar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+template <bool PAIR>
+__device__ __forceinline__ void tc_commit_g(uint32_t mbar) {
+  if constexpr (PAIR)
+    tc_commit_pair(mbar);
+  else
+    tc_commit(mbar);
+}
+// every thread of both CTAs of the cluster
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 // shared-memory matrix descriptor, K-major swizzled: start address, leading
 // byte offset (unused for swizzled K-major, encoded as 16 B), stride byte
 // offset between 8-row groups, descriptor version 1, layout type (2 = 128-byte
@@ -301,24 +348,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, uint3
 }
 // One MMA; the operand descriptors are given as their low words (start
 // address) and the high word they share (stride, version, layout).
-template <int MODE>
+template <int MODE, bool PAIR = false>
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint32_t adesc_lo, uint32_t bdesc_lo, uint32_t desc_hi,
                                        uint32_t idesc, uint32_t accumulate) {
+#define TC_MMA_ASM(GROUP, KIND)                                                                                   \
+  asm volatile("{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\tmov.b64 ad, {%1, %3};\n\tmov.b64 bd, {%2, %3};\n\t"    \
+               "setp.ne.b32 p, %5, 0;\n\t"                                                                         \
+               "tcgen05.mma.cta_group::" GROUP ".kind::" KIND " [%0], ad, bd, %4, p;\n\t}" ::"r"(d_tmem),           \
+               "r"(adesc_lo), "r"(bdesc_lo), "r"(desc_hi), "r"(idesc), "r"(accumulate)                            \
+               : "memory")
   if constexpr (MODE == TC_TF32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\tmov.b64 ad, {%1, %3};\n\tmov.b64 bd, {%2, %3};\n\t"
-        "setp.ne.b32 p, %5, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], ad, bd, %4, p;\n\t}" ::"r"(d_tmem),
-        "r"(adesc_lo), "r"(bdesc_lo), "r"(desc_hi), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if constexpr (PAIR)
+      TC_MMA_ASM("2", "tf32");
+    else
+      TC_MMA_ASM("1", "tf32");
   } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b64 ad, bd;\n\tmov.b64 ad, {%1, %3};\n\tmov.b64 bd, {%2, %3};\n\t"
-        "setp.ne.b32 p, %5, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], ad, bd, %4, p;\n\t}" ::"r"(d_tmem),
-        "r"(adesc_lo), "r"(bdesc_lo), "r"(desc_hi), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if constexpr (PAIR)
+      TC_MMA_ASM("2", "f16");
+    else
+      TC_MMA_ASM("1", "f16");
   }
+#undef TC_MMA_ASM
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -585,11 +635,12 @@ __global__ void k_split_reduce(const float2* __restrict__ part, int n_split, int
 }
 
 // ------------------------------------------------------------------ the GEMM
-template <int MODE, int CM>
+template <int MODE, int CM, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constant__ TcArgs a,
                                                               const __grid_constant__ CUtensorMap tma_a) {
   using T = TcT<MODE>;
   using P = TcPl<MODE, CM>;
+  static_assert(!PAIR || CM == 4, "SM pairs form 4M products");
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
   // swizzle atoms need 1024-byte aligned slots
   uint8_t* smem_raw = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
@@ -598,11 +649,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   const int ncp = 2 * a.tn_c;                                   // real columns of C per tile
   const int setw = P::ACC_PER_COL * a.tn_c;                     // TMEM columns per accumulator set
   const int a_plane = P::A_PLANE;
-  const int b_plane = tc_plane_bytes(P::ROWS_PER_COL * a.tn_c, T::ESZ);
+  // B' planes: the image's (all N' rows) and this CTA's (half of them for a pair)
+  const int b_plane_g = tc_plane_bytes(P::ROWS_PER_COL * a.tn_c, T::ESZ);
+  const int b_plane = PAIR ? b_plane_g / 2 : b_plane_g;
+  // the pair's rank, and the work units of this CTA (pairs take them together)
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const int64_t t_first = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+  const int64_t t_step = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
+  auto own_mt = [&](int mt) { return PAIR ? 2 * mt + (int)rank : mt; };
   // FP16X3: A and B enter scaled by 2^sa, 2^sb; the epilogue multiplies by 2^-sa 2^-sb (exact)
   const float sc_a = operand_scale<MODE>(g.amax_a);
   const float us_a = 1.f / sc_a, us_b = 1.f / operand_scale<MODE>(g.amax_b);
   const int b_slot = P::PLANES * b_plane;
+  const int64_t b_slot_g = (int64_t)P::PLANES * b_plane_g;
   const int na = a.na, nbs = a.nbs;
   uint8_t* aring = smem_raw;
   uint8_t* bring = aring + na * P::A_SLOT;
@@ -614,7 +673,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   uint64_t* tfull = fullB + TC_MAX_B;   // (B' slots are released through emptyA)
   uint64_t* tempty = tfull + TC_MAX_ACC;
   uint64_t* fin = tempty + TC_MAX_ACC;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  // SM pairs, in the even CTA: the odd CTA's operands of a chunk are in place
+  // (per A slot) and its epilogue has drained an accumulator set
+  uint64_t* pairA = fin + 1;
+  uint64_t* pairT = pairA + TC_MAX_A;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pairT + TC_MAX_ACC);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int64_t* offCm = reinterpret_cast<int64_t*>(tmem_slot + 4);
   float2* epi_stage = reinterpret_cast<float2*>(reinterpret_cast<uint8_t*>(bars) + 4096);
@@ -642,18 +705,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       mbar_init(smem_u32(&tempty[i]), TC_EPI_WARPS * 32);
     }
     mbar_init(smem_u32(fin), 1);
+    for (int i = 0; i < TC_MAX_A; ++i) mbar_init(smem_u32(&pairA[i]), 1);
+    for (int i = 0; i < TC_MAX_ACC; ++i) mbar_init(smem_u32(&pairT[i]), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == TC_MMA_WARP) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    // a pair allocates together: one warp in each of its two CTAs, unconditionally
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TC_TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(TC_TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
+  // a pair's barriers are initialised and its TMEM allocated in both CTAs
+  // before either CTA's arrivals or MMAs reach the other
+  if constexpr (PAIR) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int kc_n = a.n_kc;
@@ -666,10 +742,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int slot = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+      int64_t issued = 0;
+      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
         const TileIdx ti = tile_decode(tile, a);
         const int kc0 = ti.s * kc_per;
-        const int mt = ti.mt, inst = ti.inst;
+        const int mt = own_mt(ti.mt), inst = ti.inst;
         // tensor-map coordinates of the tile: rows from the m bits after the
         // first tm, dimension 2 from the remaining m bits and the instance bits
         const int c1 = (mt & ((1 << (a.nmw - g.tm)) - 1)) << g.tm;
@@ -684,11 +761,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           const uint32_t bar = (MODE == TC_TF32 && CM == 4) ? smem_u32(&fullA[slot]) : smem_u32(&rawA[slot]);
           mbar_arrive_expect_tx(bar, (uint32_t)a.a_box_bytes);
           tma_load_3d(smem_u32(aring + slot * P::A_SLOT), &tma_a, kc * TC_KP, c1, (int)c2, bar);
+          ++issued;
           if (++slot == na) {
             slot = 0;
             ph ^= 1;
           }
         }
+      }
+      if (!ok) {
+        // aborted: the loads still in flight (at most the last na) land before the CTA leaves
+        uint64_t* txb = (MODE == TC_TF32 && CM == 4) ? fullA : rawA;
+        for (int64_t j = issued - 1; j >= 0 && j >= issued - na; --j)
+          mbar_wait<true>(smem_u32(&txb[j % na]), (uint32_t)((j / na) & 1), abort_flag, a.err,
+                                 1000000000ull);
       }
     }
     __syncwarp();
@@ -703,11 +788,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t wph = 0;
       int64_t q = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
         const TileIdx ti = tile_decode(tile, a);
         const int kc0 = ti.s * kc_per;
         const int nt = ti.nt, inst = ti.inst;
-        const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * (int64_t)b_slot;
+        const uint8_t* bt = a.bimg + (((int64_t)inst * a.n_nt + nt) * kc_n) * b_slot_g;
         for (int kc = kc0; kc < kc0 + kc_per; ++kc, ++q) {
           if (q >= nbs) {
             if (!mbar_wait(smem_u32(&emptyA[ws]), wph, abort_flag, a.err)) { ok = false; break; }
@@ -718,9 +803,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
           const uint32_t fb = smem_u32(&fullB[slot]);
           mbar_arrive_expect_tx(fb, (uint32_t)b_slot);
-          bulk_g2s(smem_u32(bring + slot * b_slot), bt + (int64_t)kc * b_slot, (uint32_t)b_slot, fb);
+          if constexpr (PAIR) {
+            // this CTA's half of every plane: rows [rank N'/2, (rank + 1) N'/2)
+#pragma unroll
+            for (int pl = 0; pl < P::PLANES; ++pl)
+              bulk_g2s(smem_u32(bring + slot * b_slot + pl * b_plane),
+                       bt + (int64_t)kc * b_slot_g + pl * b_plane_g + (int)rank * b_plane, (uint32_t)b_plane, fb);
+          } else {
+            bulk_g2s(smem_u32(bring + slot * b_slot), bt + (int64_t)kc * b_slot, (uint32_t)b_slot, fb);
+          }
           if (++slot == nbs) slot = 0;
         }
+      }
+      if (!ok) {
+        // aborted: the copies still in flight (at most the last nbs) land before the CTA leaves
+        for (int64_t j = q - 1; j >= 0 && j >= q - nbs; --j)
+          mbar_wait<true>(smem_u32(&fullB[j % nbs]), (uint32_t)((j / nbs) & 1), abort_flag, a.err,
+                                 1000000000ull);
       }
     }
     __syncwarp();
@@ -760,7 +859,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       int64_t chunk = 0;
       bool stop = false;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && !stop; tile += gridDim.x) {
+      for (int64_t tile = t_first; tile < a.n_tiles && !stop; tile += t_step) {
         for (int kc = 0; kc < kc_per; ++kc, ++chunk) {
           if ((int)(chunk & 1) == grp) {
             const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
@@ -827,7 +926,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       }
       auto tile_base = [&](int64_t tile) -> const float2* {
         const TileIdx ti = tile_decode(tile, a);
-        const int mt = ti.mt, inst = ti.inst;
+        const int mt = own_mt(ti.mt), inst = ti.inst;
         return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) +
                deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
       };
@@ -848,7 +947,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       };
       int slot = 0;
       uint32_t ph = 0;
-      int64_t tile = blockIdx.x;
+      int64_t tile = t_first;
       int kc = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
       const float2* An = tile < a.n_tiles ? tile_base(tile) : g.A;
       float2 v0[8], v1[8];
@@ -856,7 +955,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         int64_t ntile = tile;
         int nkc = kc + 1;
         if (nkc == (int)(tile & (int64_t)(a.n_split - 1)) * kc_per + kc_per) {
-          ntile += gridDim.x;
+          ntile += t_step;
           nkc = (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per;
           if (ntile < a.n_tiles) An = tile_base(ntile);
         }
@@ -913,14 +1012,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       }
       auto tile_base = [&](int64_t tile) -> const float2* {
         const TileIdx ti = tile_decode(tile, a);
-        const int mt = ti.mt, inst = ti.inst;
+        const int mt = own_mt(ti.mt), inst = ti.inst;
         return g.A + inst_offset(inst, g.a_istride, g.a_bpos, g.nb) + deposit_hi((uint64_t)mt, g.a_mpos, g.tm, g.nm);
       };
       int slot = 0;
       uint32_t ph = 0;
       if constexpr (MODE == TC_TF32) {
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+        for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
           const float2* At = tile_base(tile);
           const int kc0 = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
           for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
@@ -969,7 +1068,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
               }
             }
         };
-        int64_t tile = blockIdx.x;
+        int64_t tile = t_first;
         int kc = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
         const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
         const float2* An = At;     // base of the tile of the prefetched slot
@@ -977,7 +1076,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           int64_t ntile = tile;
           int nkc = kc + 1;
           if (nkc == (int)(tile & (int64_t)(a.n_split - 1)) * kc_per + kc_per) {
-            ntile += gridDim.x;
+            ntile += t_step;
             nkc = (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per;
             if (ntile < a.n_tiles) An = tile_base(ntile);
           }
@@ -1019,11 +1118,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     }
   } else if (warp == TC_MMA_WARP) {
     // ---------------------------------------------------------------- MMA issue
-    if (lane == 0) {
-      // N of one MMA: all N' = 2 tn_c real columns (4M), or tn_c per product (3M)
+    if (lane == 0 && rank == 0) {
+      // N of one MMA: all N' = 2 tn_c real columns (4M), or tn_c per product (3M);
+      // M: 128 rows, or 256 for a pair (128 in each CTA)
       const int mma_n = CM == 4 ? ncp : a.tn_c;
       const uint32_t idesc = (1u << 4) | ((uint32_t)T::FMT << 7) | ((uint32_t)T::FMT << 10) |
-                             ((uint32_t)(mma_n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+                             ((uint32_t)(mma_n >> 3) << 17) | ((uint32_t)((PAIR ? 2 : 1) * TC_M >> 4) << 24);
       // operand descriptors of the ring bases: a slot, plane or K-step offset
       // is added to the 14-bit start-address field in 16-byte units (shared
       // addresses stay below 256 KB, so the field never carries)
@@ -1040,20 +1140,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int sa_i = 0, sb_i = 0, acc = 0;
       uint32_t pha = 0, phb = 0, aph = 0;
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-        if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) { ok = false; break; }
+      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
+        // the accumulator set is drained (in both CTAs of a pair)
+        if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err) ||
+            (PAIR && !mbar_wait(smem_u32(&pairT[acc]), aph ^ 1, abort_flag, a.err))) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * setw);
         for (int kc = 0; kc < kc_per; ++kc) {
+          // the chunk's operands are in place (in both CTAs of a pair)
           if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err) ||
-              !mbar_wait(smem_u32(&fullB[sb_i]), phb, abort_flag, a.err)) {
+              !mbar_wait(smem_u32(&fullB[sb_i]), phb, abort_flag, a.err) ||
+              (PAIR && !mbar_wait(smem_u32(&pairA[sa_i]), pha, abort_flag, a.err))) {
             ok = false;
             break;
           }
           if (fence_a) fence_proxy_async();
           tc_fence_after();
           auto mma = [&](uint32_t d, uint32_t adesc, uint32_t bdesc, uint32_t accumulate) {
-            tc_mma<MODE>(d, adesc, bdesc, dhi, idesc, accumulate);
+            tc_mma<MODE, PAIR>(d, adesc, bdesc, dhi, idesc, accumulate);
           };
           // one MMA K step = 32 bytes of every plane row (2 descriptor units):
           // the step advances inside the swizzle atom
@@ -1097,7 +1204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
               mma(d3, S + 2u, BS, 1u);
             }
           }
-          tc_commit(smem_u32(&emptyA[sa_i]));
+          tc_commit_g<PAIR>(smem_u32(&emptyA[sa_i]));
           da += a_step;
           if (++sa_i == na) {
             sa_i = 0;
@@ -1112,15 +1219,56 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
         }
         if (!ok) break;
-        tc_commit(smem_u32(&tfull[acc]));
+        tc_commit_g<PAIR>(smem_u32(&tfull[acc]));
         if (++acc == a.n_acc) {
           acc = 0;
           aph ^= 1;
         }
       }
-      // drain: every MMA issued so far completes before the CTA frees TMEM
-      tc_commit(smem_u32(fin));
-      mbar_wait(smem_u32(fin), 0, abort_flag, a.err);
+      // drain: every MMA issued so far completes before the CTA (or pair) frees
+      // TMEM, also after an abort (within the limit)
+      tc_commit_g<PAIR>(smem_u32(fin));
+      mbar_wait<true>(smem_u32(fin), 0, abort_flag, a.err, 1000000000ull);
+    } else if (PAIR && lane == 0) {
+      // ---------------------------------------------------------------- pair relay (odd CTA)
+      // Follows the MMA thread's order: per chunk, once this CTA's A and B'
+      // slots are filled, one arrival on the even CTA's pairA of that A slot;
+      // per tile after the first n_acc, once this CTA's epilogue has drained
+      // the accumulator set, one arrival on the even CTA's pairT.  The slots
+      // themselves are released by the MMAs' commits, which reach both CTAs.
+      const bool fence_a = MODE == TC_TF32 && CM == 4 && !a.a_tma;
+      const uint32_t rA = mapa_cta(smem_u32(pairA), 0), rT = mapa_cta(smem_u32(pairT), 0);
+      int sa_i = 0, sb_i = 0, acc = 0;
+      uint32_t pha = 0, phb = 0, aph = 0;
+      int64_t j = 0;
+      bool ok = true;
+      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step, ++j) {
+        if (j >= a.n_acc) {
+          if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) break;
+          mbar_arrive_remote(rT + 8u * (uint32_t)acc);
+        }
+        for (int kc = 0; kc < kc_per; ++kc) {
+          if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err) ||
+              !mbar_wait(smem_u32(&fullB[sb_i]), phb, abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          if (fence_a) fence_proxy_async();
+          mbar_arrive_remote(rA + 8u * (uint32_t)sa_i);
+          if (++sa_i == na) {
+            sa_i = 0;
+            pha ^= 1;
+          }
+          if (++sb_i == nbs) {
+            sb_i = 0;
+            phb ^= 1;
+          }
+        }
+        if (++acc == a.n_acc) {
+          acc = 0;
+          aph ^= 1;
+        }
+      }
     }
     __syncwarp();
   } else {
@@ -1155,14 +1303,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     const bool track = g.amax_c != nullptr && a.n_split == 1;
     int acc = -1;
     uint32_t aph = 1;
-    for (int64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    for (int64_t tile = t_first; tile < a.n_tiles; tile += t_step) {
       if (++acc == a.n_acc) acc = 0;
       if (acc == 0) aph ^= 1;
       // warp-uniform decision: the TMEM loads and shuffles below need all 32 lanes
       if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, a.err))) break;
       tc_fence_after();
       const TileIdx ti = tile_decode(tile, a);
-      const int nt = ti.nt, mt = ti.mt, inst = ti.inst;
+      const int nt = ti.nt, mt = own_mt(ti.mt), inst = ti.inst;
       float2* Cb = a.n_split > 1 ? a.c_part + ti.s * a.c_part_stride : g.C;
       // the tile's base in C: its instance, m-tile and n-tile bits deposited at
       // their positions in C, one bit per lane, summed over the warp
@@ -1252,10 +1400,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   }
   tc_fence_before();
   __syncthreads();
+  // neither CTA of a pair leaves (or frees TMEM) while the other may still
+  // reach its shared memory: the even CTA arrives here after its MMAs drained
+  if constexpr (PAIR) cluster_sync_all();
   if (warp == TC_MMA_WARP) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
-                 : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+                   : "memory");
   }
 }
 

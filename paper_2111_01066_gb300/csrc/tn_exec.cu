@@ -230,11 +230,15 @@ static void setup_tma(StepLaunch& L, int a_bits, int64_t n_lin) {
 
 // epi_mode: -1 chooses the write-back by the coalesced run lengths, 0 forces
 // direct per-column stores, 1 the staged order (where the tile allows it)
-// b_slots: B' ring slots (<= 0: 4 for slots up to 16 KB, else 3; the rest of
-// the shared-memory budget goes to A slots)
+// b_slots: B' ring slots (<= 0: 4 for slots up to 16 KB, else 3; at most
+// TC_MAX_B; the rest of the shared-memory budget goes to A slots)
+// pair_mode: SM pairs (cta_group::2, two m tiles per work unit, half of B' per
+// CTA) where the step allows them -- 4M products and at least two full 128-row
+// m tiles: -1 or 1 uses them there, 0 never
+static bool pair_ok(const GemmArgs& g, int kid) { return !tc_is_3m(kid) && g.tm == 7 && g.nm - g.tm >= 1; }
 static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_lin, int64_t c_total = 0,
                               bool allow_split = false, int epi_mode = -1,
-                              int64_t split_cap_bytes = (int64_t)256 << 20, int b_slots = 0) {
+                              int64_t split_cap_bytes = (int64_t)256 << 20, int b_slots = 0, int pair_mode = -1) {
   StepLaunch L;
   L.kid = kid;
   L.g = g;
@@ -246,7 +250,8 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.tnb = g.tn;
   const TcGeom geo = tc_geom(kid);
   t.tn_c = std::max(geo.min_tn_c, 1 << g.tn);
-  t.n_mt = 1 << (g.nm - g.tm);
+  t.pair = (pair_mode != 0 && pair_ok(g, kid)) ? 1 : 0;
+  t.n_mt = 1 << (g.nm - g.tm - t.pair);
   t.n_nt = 1 << (g.nn - g.tn);
   t.n_kc = 1 << (g.nk - g.tk);
   t.n_tiles = (int64_t)g.n_inst * t.n_mt * t.n_nt;
@@ -254,11 +259,13 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   const int npl = geo.planes;
   L.ws_bytes = (int64_t)g.n_inst * t.n_nt * t.n_kc * npl * b_plane;
   // split-K when the output tiles cannot fill the SMs and the k loop is long
+  // (a pair's work unit occupies two SMs)
+  const int64_t unit_sms = 1 + t.pair;
   t.n_split = 1;
-  if (allow_split && c_total > 0 && t.n_tiles < sm_count() && t.n_kc >= 8) {
+  if (allow_split && c_total > 0 && t.n_tiles * unit_sms < sm_count() && t.n_kc >= 8) {
     int sp = 1;
     // enough tiles for several waves (tail below ~15%), each split >= 4 k chunks
-    while (sp < 32 && t.n_tiles * sp * 2 <= 8 * (int64_t)sm_count() && t.n_kc / (sp * 2) >= 4) sp *= 2;
+    while (sp < 32 && t.n_tiles * unit_sms * sp * 2 <= 8 * (int64_t)sm_count() && t.n_kc / (sp * 2) >= 4) sp *= 2;
     if (sp > 1 && (int64_t)sp * c_total * 8 <= split_cap_bytes) {
       t.n_split = sp;
       t.c_part_stride = c_total;
@@ -270,7 +277,7 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.n_tiles *= t.n_split;
   t.ls_split = __builtin_ctz((unsigned)t.n_split);
   t.ls_nt = g.nn - g.tn;
-  t.ls_mt = g.nm - g.tm;
+  t.ls_mt = g.nm - g.tm - t.pair;
   t.ls_kc = g.nk - g.tk;
   setup_tma(L, a_bits, n_lin);
   // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
@@ -295,11 +302,12 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   }
   // rings: B' slots first (3, or 4 when small), the rest of the shared memory
   // to A slots: up to the 227 KB opt-in, less the barriers, the alignment slack
-  // and the write-back staging (only when the staged order is used)
-  const int b_slot = npl * b_plane;
+  // and the write-back staging (only when the staged order is used); a pair's
+  // CTA holds half of every B' plane
+  const int b_slot = npl * (t.pair ? b_plane / 2 : b_plane);
   const int epi_bytes = t.epi_ok ? TC_EPI_BYTES : 0;
   const int budget = TC_MAX_SMEM - 4096 - 1024 - epi_bytes;
-  t.nbs = b_slots > 0 ? std::min(b_slots, TC_MAX_B) : (b_slot <= 16384 ? TC_MAX_B : 3);
+  t.nbs = b_slots > 0 ? std::min(b_slots, TC_MAX_B) : (b_slot <= 16384 ? 4 : 3);
   t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
   if (t.na < 2) fail(TN_ERR_UNSUPPORTED, "tensor-core rings do not fit shared memory");
   t.nbs = std::min(t.nbs, t.na);   // B' slots are released through the A slots' barriers
@@ -312,7 +320,38 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   return L;
 }
 
-template <int MODE, int CM>
+// SM pairs of a tensor-core kernel that can be resident at once (one pair per
+// two SMs when the device fits them all), queried once per kernel and device
+template <int MODE, bool PAIR>
+static int pair_clusters() {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const int slot = dev < 64 ? dev : 63;
+  int n = cached[slot].load(std::memory_order_acquire);
+  if (n > 0) return n;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * (sm_count() / 2));
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = TC_MAX_SMEM;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int q = 0;
+  if (cudaOccupancyMaxActiveClusters(&q, k_cgemm_tc<MODE, 4, PAIR>, &cfg) != cudaSuccess || q <= 0) {
+    cudaGetLastError();
+    q = sm_count() / 2;
+  }
+  n = std::min(q, sm_count() / 2);
+  cached[slot].store(n, std::memory_order_release);
+  return n;
+}
+
+template <int MODE, int CM, bool PAIR>
 static void launch_tc(const TcArgs& t, const StepLaunch& L, int grid, cudaStream_t s) {
   // one CTA per B' image block at a time
   const int64_t n_blocks = (int64_t)t.g.n_inst * t.n_nt * t.n_kc;
@@ -329,10 +368,28 @@ static void launch_tc(const TcArgs& t, const StepLaunch& L, int grid, cudaStream
   CK(cudaGetDevice(&dev));
   const uint64_t bit = dev < 64 ? (1ULL << dev) : 0;
   if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
-    CK(cudaFuncSetAttribute(k_cgemm_tc<MODE, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    CK(cudaFuncSetAttribute(k_cgemm_tc<MODE, CM, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_MAX_SMEM));
     attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
-  k_cgemm_tc<MODE, CM><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
+  if constexpr (PAIR) {
+    // clusters of two CTAs, each pair persistent over the work units
+    const int clusters = (int)std::min<int64_t>(t.n_tiles, pair_clusters<MODE, PAIR>());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = L.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_cgemm_tc<MODE, CM, PAIR>, t, L.tma));
+  } else {
+    k_cgemm_tc<MODE, CM, PAIR><<<grid, TC_THREADS, L.smem, s>>>(t, L.tma);
+  }
 }
 
 static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s) {
@@ -349,22 +406,31 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
   const int grid = (int)std::min<int64_t>(t.n_tiles, sm_count());
   switch (L.kid) {
     case K_TC_TF32:
-      launch_tc<TC_TF32, 4>(t, L, grid, s);
+      if (t.pair)
+        launch_tc<TC_TF32, 4, true>(t, L, grid, s);
+      else
+        launch_tc<TC_TF32, 4, false>(t, L, grid, s);
       break;
     case K_TC_BF16X3:
-      launch_tc<TC_BF16X3, 4>(t, L, grid, s);
+      if (t.pair)
+        launch_tc<TC_BF16X3, 4, true>(t, L, grid, s);
+      else
+        launch_tc<TC_BF16X3, 4, false>(t, L, grid, s);
       break;
     case K_TC_TF32_3M:
-      launch_tc<TC_TF32, 3>(t, L, grid, s);
+      launch_tc<TC_TF32, 3, false>(t, L, grid, s);
       break;
     case K_TC_BF16X3_3M:
-      launch_tc<TC_BF16X3, 3>(t, L, grid, s);
+      launch_tc<TC_BF16X3, 3, false>(t, L, grid, s);
       break;
     case K_TC_FP16X3:
-      launch_tc<TC_FP16X3, 4>(t, L, grid, s);
+      if (t.pair)
+        launch_tc<TC_FP16X3, 4, true>(t, L, grid, s);
+      else
+        launch_tc<TC_FP16X3, 4, false>(t, L, grid, s);
       break;
     default:
-      launch_tc<TC_FP16X3, 3>(t, L, grid, s);
+      launch_tc<TC_FP16X3, 3, false>(t, L, grid, s);
       break;
   }
   if (t.n_split > 1) {
@@ -596,8 +662,8 @@ static void ensure_device(Plan& p) {
                     ((int64_t)1 << (d.nm + d.nn + d.nb)) == d.c_elems;
     if (!ok) fail(TN_ERR_PLAN, "internal: step operand outside its extent");
     const int kid = pick_kernel(p.opts.precision, p.opts.complex_mult, d);
-    ds->launches.push_back(
-        make_launch(step_args(*ds, d, kid), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1, d.c_elems, true));
+    ds->launches.push_back(make_launch(step_args(*ds, d, kid), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
+                                       d.c_elems, true, -1, (int64_t)256 << 20, 0, p.opts.sm_pairs ? -1 : 0));
   }
   int64_t ws = 16;
   for (const StepLaunch& L : ds->launches) ws = std::max(ws, L.ws_bytes);
@@ -841,9 +907,10 @@ extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_o
 
 // Autotuner: for every step, time the candidate kernels in place (tensor-core
 // tiles of 32, 64 or 128 complex columns in the TF32 / BF16X3 / FP16X3 modes,
-// each with either write-back order and with 3 or 4 B' ring slots, and the
-// three CUDA-core tilings where the step is small or the mode is FP32) and keep
-// the fastest.  The chunk graph is captured again on the next call.
+// each with either write-back order, with the default or a deeper B' ring (4,
+// 6 or 8 slots) and on one SM or an SM pair, and the three CUDA-core tilings
+// where the step is small or the mode is FP32) and keep the fastest.  The
+// chunk graph is captured again on the next call.
 extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) {
   API_BEGIN
   if (!h) fail(TN_ERR_ARG, "tn_plan_autotune: NULL plan");
@@ -881,35 +948,39 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   };
   for (size_t i = 0; i < p.steps.size(); ++i) {
     const StepDesc& d = p.steps[i];
-    auto build = [&](int kid, int tn_log, int epi, int bslots = 0) {
+    auto build = [&](int kid, int tn_log, int epi, int bslots, int pair) {
       return make_launch(step_args(ds, d, kid, tn_log), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
-                         d.c_elems, true, epi, (int64_t)256 << 20, bslots);
+                         d.c_elems, true, epi, (int64_t)256 << 20, bslots, pair);
     };
     double best = time_launch(ds.launches[i]);
-    std::vector<std::array<int, 4>> cands;   // kernel, tile width (log2 complex columns), write-back, B' slots
+    // kernel, tile width (log2 complex columns), write-back, B' slots, SM pairs
+    std::vector<std::array<int, 5>> cands;
     const bool tc_mode = p.opts.precision != TN_PREC_FP32;
     const int tc_kid = tc_kernel(p.opts.precision, p.opts.complex_mult);
     if (tc_mode && d.nm >= 4)
       for (int tn_log : {7, 6, 5})
         if (tn_log <= std::max(3, d.nn))
           for (int epi : {0, 1})
-            for (int bs : {0, 4}) cands.push_back({tc_kid, tn_log, epi, bs});
+            for (int bs : {0, 4, 6, 8})
+              for (int pair : {1, 0})
+                if (pair == 0 || p.opts.sm_pairs) cands.push_back({tc_kid, tn_log, epi, bs, pair});
     // CUDA-core tilings: FP32 mode, tiny steps, and low arithmetic intensity
     // (complex flops per byte moved), where a tile's fixed cost on the tensor
     // cores outweighs its few products
     const double flops = 8.0 * std::ldexp(1.0, d.nm + d.nk + d.nn + d.nb);
     const double bytes = 8.0 * (double)(d.a_elems + d.b_elems + d.c_elems);
     if (!tc_mode || best < 0.05 || flops / bytes < 48.0)
-      for (int k : {K_SIMT_64x64, K_SIMT_128x16, K_SIMT_256x4}) cands.push_back({k, -1, 0, 0});
-    std::vector<std::array<int, 4>> seen;
+      for (int k : {K_SIMT_64x64, K_SIMT_128x16, K_SIMT_256x4}) cands.push_back({k, -1, 0, 0, 0});
+    std::vector<std::array<int, 5>> seen;
     auto key = [](const StepLaunch& L) {
-      return std::array<int, 4>{L.kid, L.g.tn, is_tc(L.kid) ? L.tc.epi_ok : 0, is_tc(L.kid) ? L.tc.nbs : 0};
+      return std::array<int, 5>{L.kid, L.g.tn, is_tc(L.kid) ? L.tc.epi_ok : 0, is_tc(L.kid) ? L.tc.nbs : 0,
+                                is_tc(L.kid) ? L.tc.pair : 0};
     };
     seen.push_back(key(ds.launches[i]));
-    for (auto [kid, tn_log, epi, bs] : cands) {
+    for (auto [kid, tn_log, epi, bs, pair] : cands) {
       StepLaunch L;
       try {
-        L = build(kid, tn_log, epi, bs);
+        L = build(kid, tn_log, epi, bs, pair);
       } catch (const TnError&) {
         continue;   // this configuration does not fit: not a candidate
       }

@@ -1296,6 +1296,7 @@ extern "C" tn_status tn_plan_default_opts(tn_plan_opts* o) {
   o->log2_batch_slices = 0;
   o->max_arena_bytes = (int64_t)96 << 30;
   o->mem_weight = 0.0;
+  o->sm_pairs = 1;
   return TN_OK;
 }
 
@@ -1306,6 +1307,7 @@ extern "C" tn_status tn_plan(const tn_network_t* net, const tn_plan_opts* opts, 
     *out = nullptr;
     if (!(opts->mem_weight <= 0.0 || (opts->mem_weight >= 1e-6 && opts->mem_weight <= 1e9)))
       fail(TN_ERR_ARG, "mem_weight must be <= 0 (default) or in [1e-6, 1e9]");
+    if (opts->sm_pairs != 0 && opts->sm_pairs != 1) fail(TN_ERR_ARG, "sm_pairs must be 0 or 1");
     g_alpha = opts->mem_weight > 0.0 ? opts->mem_weight : 32.0;
     Plan* p = nullptr;
     try {

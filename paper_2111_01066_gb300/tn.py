@@ -51,7 +51,7 @@ class tn_plan_opts(ctypes.Structure):
                 ("max_arena_bytes", ctypes.c_int64), ("n_forced_slices", ctypes.c_int32),
                 ("forced_slice_qubit", ctypes.POINTER(ctypes.c_int32)),
                 ("forced_slice_t", ctypes.POINTER(ctypes.c_int32)),
-                ("mem_weight", ctypes.c_double)]
+                ("mem_weight", ctypes.c_double), ("sm_pairs", ctypes.c_int32)]
 
 
 class tn_plan_stats(ctypes.Structure):
@@ -200,7 +200,7 @@ def default_opts() -> tn_plan_opts:
 
 
 def _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed, trials,
-               log2_batch_slices, max_arena_bytes, forced_slices, mem_weight):
+               log2_batch_slices, max_arena_bytes, forced_slices, mem_weight, sm_pairs=1):
     o = default_opts()
     o.open_mask = open_mask
     o.max_log2_intermediate = max_log2_intermediate
@@ -218,6 +218,7 @@ def _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, com
     o.forced_slice_qubit = ctypes.cast(fq, ctypes.POINTER(ctypes.c_int32))
     o.forced_slice_t = ctypes.cast(ft, ctypes.POINTER(ctypes.c_int32))
     o.mem_weight = float(mem_weight)
+    o.sm_pairs = int(sm_pairs)
     return o, (fq, ft)
 
 
@@ -229,14 +230,14 @@ class Plan:
                  seed: int = 1, trials: int = 64, log2_batch_slices: int = 0,
                  max_arena_bytes: int = 0,
                  forced_slices: Sequence[Tuple[int, int]] = (), mem_weight: float = 0.0,
-                 _handle=None):
+                 sm_pairs: int = 1, _handle=None):
         self.network = network
         self.open_mask = open_mask
         if _handle is not None:
             self.handle = _handle
             return
         o, keep = _make_opts(open_mask, max_log2_intermediate, min_log2_slices, precision, complex_mult, seed,
-                             trials, log2_batch_slices, max_arena_bytes, forced_slices, mem_weight)
+                             trials, log2_batch_slices, max_arena_bytes, forced_slices, mem_weight, sm_pairs)
         h = ctypes.c_void_p()
         _check(load().tn_plan(network.handle, ctypes.byref(o), ctypes.byref(h)))
         self.handle = h

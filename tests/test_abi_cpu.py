@@ -144,6 +144,21 @@ def test_mem_weight_option(tn):
     assert e.value.status == tn.TN_ERR_ARG
 
 
+def test_sm_pairs_option(tn):
+    """SM pairs are on by default, can be switched off, and nothing else is
+    accepted; the order and slices do not depend on it (a kernel choice only)."""
+    assert tn.default_opts().sm_pairs == 1
+    circ, om, _ = rqcgen.config_circuit("c2")
+    net = tn.Network(circ)
+    a = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3, precision="bf16x3")
+    b = tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, seed=3, precision="bf16x3", sm_pairs=0)
+    assert a.step_shapes() == b.step_shapes() and a.sliced_wires() == b.sliced_wires()
+    for bad in (2, -1):
+        with pytest.raises(tn.TnError) as e:
+            tn.Plan(net, open_mask=om, max_log2_intermediate=22, trials=8, sm_pairs=bad)
+        assert e.value.status == tn.TN_ERR_ARG
+
+
 @pytest.mark.parametrize("name", ["c2", "c3"])
 def test_layout_pass_guarantees(tn, name):
     """The planner stores every streamed operand A as [its contracted wires,

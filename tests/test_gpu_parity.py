@@ -329,6 +329,28 @@ def test_c3_all_slices_against_golden(env, prec, cm):
     assert xerr < (1e-3 if prec != "tf32" else 5e-2)
 
 
+@pytest.mark.parametrize("sm_pairs", [0, 1])
+def test_c3_one_sm_and_sm_pair_tiles_against_golden(env, sm_pairs):
+    """The benchmark's C3 plan with its tensor-core steps on one SM per tile or
+    on SM pairs (two SMs share each 256-row MMA): both give the oracle's
+    amplitudes, after autotuning too (which then chooses per step)."""
+    tn, torch = env
+    from tests.golden.make_golden import read
+    from tests.golden.make_plan_data import RUNS
+    want = read("c3")
+    cfg = rqcgen.CONFIGS["c3"]
+    c = _pool_candidates("c3")[0]
+    circ, om, cb = rqcgen.config_circuit("c3")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, max_log2_intermediate=cfg["log2_bound"],
+                   min_log2_slices=cfg["log2_slices"], precision="bf16x3", seed=c["seed"],
+                   mem_weight=c["mem_weight"], trials=RUNS["c3"]["trials"], sm_pairs=sm_pairs)
+    got = _run_plan(tn, torch, plan, 0, 1 << 12, [cb], 12)
+    _check_plan(got, want, circ.n_qubits, "bf16x3", f"c3 sm_pairs={sm_pairs}")
+    plan.autotune(reps=1)
+    got = _run_plan(tn, torch, plan, 0, 1 << 12, [cb], 12)
+    _check_plan(got, want, circ.n_qubits, "bf16x3", f"c3 sm_pairs={sm_pairs} autotuned")
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_c2_autotuned_plan_still_matches_golden(env, prec):
     """The autotuner swaps kernels and tile widths per step; results keep their accuracy."""
@@ -471,6 +493,33 @@ def test_contract_pair_fp16x3_scaling(env, shape, mag, cm):
     assert np.linalg.norm(base - want) <= 2e-5 * np.linalg.norm(want)
     scaled = run((a * np.float32(mag)).astype(np.complex64), (b * np.float32(mag_b)).astype(np.complex64))
     assert np.array_equal(scaled, (base * np.float32(mag * mag_b)).astype(np.complex64))
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("shape", [(8, 4, 3, 1), (10, 4, 6, 3), (12, 5, 7, 1), (8, 8, 8, 2), (9, 13, 3, 1),
+                                   (8, 14, 5, 3), (11, 6, 2, 1)])
+def test_contract_pair_sm_pairs_a_by_tma(env, shape, prec):
+    """4M products with two or more full 128-row m tiles run on SM pairs; here
+    with A stored [k, m] (fetched by tensor-map loads, then split in shared
+    memory) and C in a random order: one pair, several pairs, batched
+    instances, 8- to 128-column tiles, split-K over a long k."""
+    tn, torch = env
+    nm, nk, nn, batch = shape
+    rng = np.random.default_rng(sum(shape) + 7)
+    wires = list(range(500, 500 + nm + nk + nn))
+    m_w, k_w, n_w = wires[:nm], wires[nm:nm + nk], wires[nm + nk:]
+    a_w, b_w, c_w = k_w + m_w, list(rng.permutation(k_w + n_w)), list(rng.permutation(m_w + n_w))
+    a = (rng.normal(size=(batch, 2 ** len(a_w))) + 1j * rng.normal(size=(batch, 2 ** len(a_w)))) / 2
+    b = (rng.normal(size=(batch, 2 ** len(b_w))) + 1j * rng.normal(size=(batch, 2 ** len(b_w)))) / 2
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    tc = torch.empty((batch, 2 ** len(c_w)), dtype=torch.complex64, device="cuda")
+    tn.contract_pair(dev(a), a_w, dev(b), b_w, tc, c_w, batch=batch, precision=prec)
+    tn.device_sync()
+    got = tc.cpu().numpy()
+    for i in range(batch):
+        want = pairwise.contract_pair(a[i], a_w, b[i], b_w, c_w)
+        scale = math.sqrt(2 ** nk) * np.sqrt(np.mean(np.abs(a[i]) ** 2) * np.mean(np.abs(b[i]) ** 2))
+        assert np.max(np.abs(got[i] - want)) <= PAIR_TOL[prec] * max(scale, 1e-30) * 8
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3", "fp16x3"])
