@@ -156,6 +156,9 @@ struct TcArgs {
   // SM pairs: a work unit is a pair of m tiles (n_mt counts pairs); the CTA of
   // cluster rank r takes m tile 2 mt + r and the B' rows [r N'/2, (r + 1) N'/2)
   int32_t pair;
+  // 1: each CTA (pair) runs all n tiles of one A block back to back (the block's
+  // later reads come from L2 right after the first); 0: work units in index order
+  int32_t nt_inner;
 };
 
 // Work unit `tile` -> split index, n tile, m tile, instance: shifts and masks
@@ -657,6 +660,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   const int64_t t_first = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
   const int64_t t_step = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
   auto own_mt = [&](int mt) { return PAIR ? 2 * mt + (int)rank : mt; };
+  // the j-th work unit of this CTA (pair), -1 past the last: units t_first,
+  // t_first + t_step, ... in index order, or -- nt_inner -- groups (split index,
+  // m tile, instance) taken that way with all their n tiles in turn
+  const int64_t n_groups = a.n_tiles >> a.ls_nt;
+  auto seq_tile = [&](int64_t j) -> int64_t {
+    if (!a.nt_inner) {
+      const int64_t t = t_first + j * t_step;
+      return t < a.n_tiles ? t : -1;
+    }
+    const int64_t gi = t_first + (j >> a.ls_nt) * t_step;
+    if (gi >= n_groups) return -1;
+    const int64_t sp = gi & (int64_t)(a.n_split - 1), rest = gi >> a.ls_split;
+    return sp | ((j & (int64_t)(a.n_nt - 1)) << a.ls_split) | (rest << (a.ls_split + a.ls_nt));
+  };
   // FP16X3: A and B enter scaled by 2^sa, 2^sb; the epilogue multiplies by 2^-sa 2^-sb (exact)
   const float sc_a = operand_scale<MODE>(g.amax_a);
   const float us_a = 1.f / sc_a, us_b = 1.f / operand_scale<MODE>(g.amax_b);
@@ -743,7 +760,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       bool ok = true;
       int64_t issued = 0;
-      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
+      int64_t jt = 0;
+      for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++jt)) {
         const TileIdx ti = tile_decode(tile, a);
         const int kc0 = ti.s * kc_per;
         const int mt = own_mt(ti.mt), inst = ti.inst;
@@ -788,7 +806,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t wph = 0;
       int64_t q = 0;
       bool ok = true;
-      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
+      int64_t jt = 0;
+      for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++jt)) {
         const TileIdx ti = tile_decode(tile, a);
         const int kc0 = ti.s * kc_per;
         const int nt = ti.nt, inst = ti.inst;
@@ -830,7 +849,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     // the operand planes: 4M BF16X3/FP16X3 hi and lo (128 rows x 64 bytes
     // each); 3M the planes of TcPl<MODE, 3> by items (row, 8 complex k).  The 8
     // warps form two groups of 4 that take alternate k chunks, so two chunks
-    // are converted at once; rows past the tile's 2^tm are left alone.
+    // are converted at once (the A ring has an even number of slots, so every
+    // slot belongs to one group); rows past the tile's 2^tm are left alone.
     if constexpr (CM == 3 || MODE != TC_TF32) {
       const int lt = threadIdx.x - (TC_MMA_WARP + 1) * 32;
       constexpr int GT = TC_LOAD_THREADS / 2;                     // threads per group
@@ -859,7 +879,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       int64_t chunk = 0;
       bool stop = false;
-      for (int64_t tile = t_first; tile < a.n_tiles && !stop; tile += t_step) {
+      int64_t jt = 0;
+      for (int64_t tile = seq_tile(0); tile >= 0 && !stop; tile = seq_tile(++jt)) {
         for (int kc = 0; kc < kc_per; ++kc, ++chunk) {
           if ((int)(chunk & 1) == grp) {
             const bool got = mbar_wait(smem_u32(&rawA[slot]), ph, abort_flag, a.err);
@@ -947,19 +968,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       };
       int slot = 0;
       uint32_t ph = 0;
-      int64_t tile = t_first;
-      int kc = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
-      const float2* An = tile < a.n_tiles ? tile_base(tile) : g.A;
+      int64_t jt = 0;
+      int64_t tile = seq_tile(0);
+      int kc = tile >= 0 ? (int)(tile & (int64_t)(a.n_split - 1)) * kc_per : 0;
+      const float2* An = tile >= 0 ? tile_base(tile) : g.A;
       float2 v0[8], v1[8];
       auto body = [&](float2(&vc)[8], float2(&vn)[8]) -> bool {
-        int64_t ntile = tile;
+        int64_t ntile = tile, njt = jt;
         int nkc = kc + 1;
         if (nkc == (int)(tile & (int64_t)(a.n_split - 1)) * kc_per + kc_per) {
-          ntile += t_step;
-          nkc = (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per;
-          if (ntile < a.n_tiles) An = tile_base(ntile);
+          ntile = seq_tile(++njt);
+          nkc = ntile >= 0 ? (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per : 0;
+          if (ntile >= 0) An = tile_base(ntile);
         }
-        if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
+        if (ntile >= 0) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
         uint8_t* sa = aring + slot * P::A_SLOT;
         if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) return false;
         if (rok) put3m<MODE>(sa, row, h, vc, sc_a);
@@ -970,12 +992,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           ph ^= 1;
         }
         tile = ntile;
+        jt = njt;
         kc = nkc;
         return true;
       };
-      if (tile < a.n_tiles) issue(v0, An + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
-      while (tile < a.n_tiles) {
-        if (!body(v0, v1) || tile >= a.n_tiles) break;
+      if (tile >= 0) issue(v0, An + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
+      while (tile >= 0) {
+        if (!body(v0, v1) || tile < 0) break;
         if (!body(v1, v0)) break;
       }
     } else {
@@ -1019,7 +1042,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t ph = 0;
       if constexpr (MODE == TC_TF32) {
         bool ok = true;
-        for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
+        int64_t jt = 0;
+        for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++jt)) {
           const float2* At = tile_base(tile);
           const int kc0 = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
           for (int kc = kc0; kc < kc0 + kc_per; ++kc) {
@@ -1068,19 +1092,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
               }
             }
         };
-        int64_t tile = t_first;
-        int kc = (int)(tile & (int64_t)(a.n_split - 1)) * kc_per;
-        const float2* At = tile < a.n_tiles ? tile_base(tile) : g.A;
+        int64_t jt = 0;
+        int64_t tile = seq_tile(0);
+        int kc = tile >= 0 ? (int)(tile & (int64_t)(a.n_split - 1)) * kc_per : 0;
+        const float2* At = tile >= 0 ? tile_base(tile) : g.A;
         const float2* An = At;     // base of the tile of the prefetched slot
         auto body = [&](float4(&vc)[NCH][KPC / 2], float4(&vn)[NCH][KPC / 2]) -> bool {
-          int64_t ntile = tile;
+          int64_t ntile = tile, njt = jt;
           int nkc = kc + 1;
           if (nkc == (int)(tile & (int64_t)(a.n_split - 1)) * kc_per + kc_per) {
-            ntile += t_step;
-            nkc = (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per;
-            if (ntile < a.n_tiles) An = tile_base(ntile);
+            ntile = seq_tile(++njt);
+            nkc = ntile >= 0 ? (int)(ntile & (int64_t)(a.n_split - 1)) * kc_per : 0;
+            if (ntile >= 0) An = tile_base(ntile);
           }
-          if (ntile < a.n_tiles) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
+          if (ntile >= 0) issue(vn, An + deposit_hi((uint64_t)nkc, g.a_kpos, g.tk, g.nk));
           uint8_t* sa = aring + slot * P::A_SLOT;
           if (!mbar_wait(smem_u32(&emptyA[slot]), ph ^ 1, abort_flag, a.err)) return false;
           {
@@ -1106,12 +1131,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           }
           if (ntile != tile) At = An;
           tile = ntile;
+          jt = njt;
           kc = nkc;
           return true;
         };
-        if (tile < a.n_tiles) issue(v0, At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
-        while (tile < a.n_tiles) {
-          if (!body(v0, v1) || tile >= a.n_tiles) break;
+        if (tile >= 0) issue(v0, At + deposit_hi((uint64_t)kc, g.a_kpos, g.tk, g.nk));
+        while (tile >= 0) {
+          if (!body(v0, v1) || tile < 0) break;
           if (!body(v1, v0)) break;
         }
       }
@@ -1140,7 +1166,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int sa_i = 0, sb_i = 0, acc = 0;
       uint32_t pha = 0, phb = 0, aph = 0;
       bool ok = true;
-      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step) {
+      int64_t jt = 0;
+      for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++jt)) {
         // the accumulator set is drained (in both CTAs of a pair)
         if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err) ||
             (PAIR && !mbar_wait(smem_u32(&pairT[acc]), aph ^ 1, abort_flag, a.err))) {
@@ -1242,7 +1269,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       uint32_t pha = 0, phb = 0, aph = 0;
       int64_t j = 0;
       bool ok = true;
-      for (int64_t tile = t_first; tile < a.n_tiles && ok; tile += t_step, ++j) {
+      for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++j)) {
         if (j >= a.n_acc) {
           if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) break;
           mbar_arrive_remote(rT + 8u * (uint32_t)acc);
@@ -1303,7 +1330,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     const bool track = g.amax_c != nullptr && a.n_split == 1;
     int acc = -1;
     uint32_t aph = 1;
-    for (int64_t tile = t_first; tile < a.n_tiles; tile += t_step) {
+    int64_t jt = 0;
+    for (int64_t tile = seq_tile(0); tile >= 0; tile = seq_tile(++jt)) {
       if (++acc == a.n_acc) acc = 0;
       if (acc == 0) aph ^= 1;
       // warp-uniform decision: the TMEM loads and shuffles below need all 32 lanes

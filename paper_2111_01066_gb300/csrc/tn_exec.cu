@@ -278,6 +278,11 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.ls_split = __builtin_ctz((unsigned)t.n_split);
   t.ls_nt = g.nn - g.tn;
   t.ls_mt = g.nm - g.tm - t.pair;
+  // the n tiles of one A block back to back on the same SM (pair), so that the
+  // block's later reads hit L2, when there are enough A blocks to keep every SM
+  // (pair) busy
+  const int64_t units = t.pair ? sm_count() / 2 : sm_count();
+  t.nt_inner = (t.n_nt > 1 && (t.n_tiles >> t.ls_nt) >= 2 * units) ? 1 : 0;
   t.ls_kc = g.nk - g.tk;
   setup_tma(L, a_bits, n_lin);
   // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
@@ -309,6 +314,14 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   const int budget = TC_MAX_SMEM - 4096 - 1024 - epi_bytes;
   t.nbs = b_slots > 0 ? std::min(b_slots, TC_MAX_B) : (b_slot <= 16384 ? 4 : 3);
   t.na = std::min(TC_MAX_A, (budget - t.nbs * b_slot) / geo.a_slot);
+  // A by tensor-map loads converted in place: the two converter groups take
+  // alternate k chunks, and chunk q sits in A slot q % na.  An even na keeps
+  // every slot with one group, which then waits for the slot's phases strictly
+  // in order; with an odd na a group could wait for phase u of a slot before the
+  // other group's phase u - 1 had landed, and a parity wait cannot tell the two
+  // apart (it would pass on the stale phase and convert the wrong data).
+  const bool converters = t.a_tma && (tc_is_3m(kid) || kid != K_TC_TF32);
+  if (converters) t.na &= ~1;
   if (t.na < 2) fail(TN_ERR_UNSUPPORTED, "tensor-core rings do not fit shared memory");
   t.nbs = std::min(t.nbs, t.na);   // B' slots are released through the A slots' barriers
   // arrivals on an A slot: the TMA itself (TF32 4M), one converter group (TMA otherwise), all loaders
