@@ -279,10 +279,16 @@ static StepLaunch make_launch(const GemmArgs& g, int kid, int a_bits, int64_t n_
   t.ls_nt = g.nn - g.tn;
   t.ls_mt = g.nm - g.tm - t.pair;
   // the n tiles of one A block back to back on the same SM (pair), so that the
-  // block's later reads hit L2, when there are enough A blocks to keep every SM
-  // (pair) busy
+  // block's later reads hit L2: when the A blocks in flight on all SMs fit half
+  // of L2 (else they evict each other between reads, while in index order the
+  // n tiles of a block run at the same time on neighbouring SMs) and there are
+  // at least 8 blocks per SM (pair), so that the coarser units leave no long tail
   const int64_t units = t.pair ? sm_count() / 2 : sm_count();
-  t.nt_inner = (t.n_nt > 1 && (t.n_tiles >> t.ls_nt) >= 2 * units) ? 1 : 0;
+  const double a_block_bytes = 8.0 * TC_M * (1 + t.pair) * std::ldexp(1.0, g.nk);
+  t.nt_inner = (t.n_nt > 1 && (t.n_tiles >> t.ls_nt) >= 8 * units &&
+                units * a_block_bytes <= 64.0 * (1 << 20))
+                   ? 1
+                   : 0;
   t.ls_kc = g.nk - g.tk;
   setup_tma(L, a_bits, n_lin);
   // epilogue write order: a warp's rows are m bits 0-4, a chunk's 16 columns n bits 0-3
