@@ -230,41 +230,38 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 flops x G
 
 # DRAM bytes (read + write) per launch of the tensor-core GEMM at full size,
 # keyed by (kernel, log2 m,k,n,batch): one ncu launch list (time and DRAM bytes,
-# a single pass per launch) of one timed step of each benchmark plan, matched
-# to the steps in launch order (profiles/c3_bf16x3_launch_list.md,
+# a single pass per launch) of one timed step of each benchmark plan with the
+# kernels the autotuner chose (one SM or SM pairs), matched to the steps in
+# launch order (profiles/c3_bf16x3_launch_list.md,
 # profiles/c5_bf16x3_launch_list.md)
 MEASURED_TRAFFIC = {
-    ("tc_bf16x3", (21, 8, 8, 0)): 8.5398e+09,   # c3
-    ("tc_bf16x3", (21, 7, 8, 0)): 6.6049e+09,   # c3
-    ("tc_bf16x3", (12, 10, 7, 7)): 5.1236e+09,   # c3
-    ("tc_bf16x3", (22, 4, 6, 0)): 2.6210e+09,   # c3
-    ("tc_bf16x3", (19, 8, 5, 0)): 1.1942e+09,   # c3
-    ("tc_bf16x3", (11, 10, 9, 5)): 1.0778e+09,   # c3
-    ("tc_bf16x3", (15, 7, 12, 0)): 1.0514e+09,   # c3
-    ("tc_bf16x3", (16, 6, 10, 0)): 5.0632e+08,   # c3
-    ("tc_bf16x3", (20, 5, 4, 0)): 3.6384e+08,   # c3
-    ("tc_bf16x3", (18, 6, 4, 0)): 1.4462e+08,   # c3
-    ("tc_bf16x3", (13, 9, 11, 0)): 1.2783e+08,   # c3
-    ("tc_bf16x3", (13, 8, 11, 0)): 9.5281e+07,   # c3
-    ("tc_bf16x3", (11, 6, 11, 0)): 3.2333e+06,   # c3
-    ("tc_bf16x3", (20, 8, 8, 0)): 4.2455e+09,   # c5
-    ("tc_bf16x3", (21, 7, 7, 0)): 4.2374e+09,   # c5
-    ("tc_bf16x3", (14, 9, 8, 5)): 3.2512e+09,   # c5
-    ("tc_bf16x3", (18, 8, 9, 1)): 3.1653e+09,   # c5
-    ("tc_bf16x3", (19, 8, 8, 0)): 2.0930e+09,   # c5
-    ("tc_bf16x3", (18, 6, 9, 0)): 1.1434e+09,   # c5
+    ("tc_bf16x3", (21, 8, 8, 0)): 8.7436e+09,   # c3
+    ("tc_bf16x3", (21, 7, 8, 0)): 6.4079e+09,   # c3
+    ("tc_bf16x3", (12, 10, 7, 7)): 5.1233e+09,   # c3
+    ("tc_bf16x3", (11, 10, 9, 5)): 1.1156e+09,   # c3
+    ("tc_bf16x3", (22, 4, 6, 0)): 2.6200e+09,   # c3
+    ("tc_bf16x3", (15, 7, 12, 0)): 1.0586e+09,   # c3
+    ("tc_bf16x3", (19, 8, 5, 0)): 1.1940e+09,   # c3
+    ("tc_bf16x3", (13, 9, 11, 0)): 1.3054e+08,   # c3
+    ("tc_bf16x3", (16, 6, 10, 0)): 5.0608e+08,   # c3
+    ("tc_bf16x3", (20, 5, 4, 0)): 3.6432e+08,   # c3
+    ("tc_bf16x3", (13, 8, 11, 0)): 9.5436e+07,   # c3
+    ("tc_bf16x3", (18, 6, 4, 0)): 1.4484e+08,   # c3
+    ("tc_bf16x3", (20, 8, 8, 0)): 4.3271e+09,   # c5
+    ("tc_bf16x3", (18, 8, 9, 1)): 3.3313e+09,   # c5
+    ("tc_bf16x3", (14, 9, 8, 5)): 3.9273e+09,   # c5
+    ("tc_bf16x3", (21, 7, 7, 0)): 4.2373e+09,   # c5
+    ("tc_bf16x3", (19, 8, 8, 0)): 2.1238e+09,   # c5
+    ("tc_bf16x3", (13, 10, 11, 0)): 2.4044e+08,   # c5
+    ("tc_bf16x3", (18, 6, 9, 0)): 1.1464e+09,   # c5
     ("tc_bf16x3", (13, 14, 3, 0)): 1.0959e+09,   # c5
-    ("tc_bf16x3", (19, 7, 5, 0)): 6.4680e+08,   # c5
-    ("tc_bf16x3", (18, 6, 8, 0)): 6.0606e+08,   # c5
-    ("tc_bf16x3", (12, 9, 9, 3)): 2.5661e+08,   # c5
-    ("tc_bf16x3", (13, 10, 11, 0)): 2.2483e+08,   # c5
-    ("tc_bf16x3", (12, 11, 9, 1)): 1.9241e+08,   # c5
-    ("tc_bf16x3", (11, 11, 8, 0)): 1.1131e+08,   # c5
-    ("tc_bf16x3", (12, 5, 12, 0)): 7.2255e+07,   # c5
-    ("tc_bf16x3", (14, 7, 7, 0)): 1.7126e+07,   # c5
-    ("tc_bf16x3", (11, 8, 10, 0)): 8.4764e+06,   # c5
-    ("tc_bf16x3", (11, 8, 8, 0)): 5.3302e+06,   # c5
-    ("tc_bf16x3", (11, 7, 10, 0)): 4.2836e+06,   # c5
+    ("tc_bf16x3", (12, 11, 9, 1)): 2.0227e+08,   # c5
+    ("tc_bf16x3", (12, 9, 9, 3)): 2.6093e+08,   # c5
+    ("tc_bf16x3", (18, 6, 8, 0)): 6.0653e+08,   # c5
+    ("tc_bf16x3", (19, 7, 5, 0)): 6.4699e+08,   # c5
+    ("tc_bf16x3", (11, 8, 10, 0)): 8.4869e+06,   # c5
+    ("tc_bf16x3", (11, 11, 8, 0)): 1.1226e+08,   # c5
+    ("tc_bf16x3", (12, 5, 12, 0)): 7.2395e+07,   # c5
 }
 
 

@@ -686,8 +686,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   uint64_t* fullA = bars;
   uint64_t* emptyA = bars + TC_MAX_A;
   uint64_t* rawA = bars + 2 * TC_MAX_A;
-  uint64_t* fullB = bars + 3 * TC_MAX_A;
-  uint64_t* tfull = fullB + TC_MAX_B;   // (B' slots are released through emptyA)
+  // (a chunk's B' copy also completes on fullA of the chunk's A slot, and B'
+  // slots are released through emptyA: the B' ring has no barriers of its own)
+  uint64_t* tfull = bars + 3 * TC_MAX_A;
   uint64_t* tempty = tfull + TC_MAX_ACC;
   uint64_t* fin = tempty + TC_MAX_ACC;
   // SM pairs, in the even CTA: the odd CTA's operands of a chunk are in place
@@ -710,12 +711,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     offCn[c] = c < tnv ? deposit_hi((uint64_t)c, g.c_npos, 0, a.tnb) : 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < na; ++s) {
-      mbar_init(smem_u32(&fullA[s]), a.fa_count);
+      mbar_init(smem_u32(&fullA[s]), a.fa_count + 1);   // + the B' producer's arrival
       mbar_init(smem_u32(&emptyA[s]), 1);
       mbar_init(smem_u32(&rawA[s]), 1);
-    }
-    for (int s = 0; s < nbs; ++s) {
-      mbar_init(smem_u32(&fullB[s]), 1);
     }
     for (int i = 0; i < TC_MAX_ACC; ++i) {
       mbar_init(smem_u32(&tfull[i]), 1);
@@ -801,8 +799,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       // B' slot q % nbs is free again once the MMAs of chunk q - nbs are done:
       // the MMA thread's single commit per chunk arrives on emptyA of that
       // chunk's A slot, whose completion for chunk j has parity (j / na) & 1
-      // (na >= nbs, so that barrier cannot have moved on by a further phase)
-      int slot = 0, ws = 0;
+      // (na >= nbs, so that barrier cannot have moved on by a further phase).
+      // The copy of chunk q completes on fullA of A slot q % na, whose previous
+      // phase (chunk q - na <= q - nbs) the MMA thread has already passed, so
+      // the MMA thread waits for A and B' of a chunk on one barrier.
+      int slot = 0, ws = 0, sa = 0;
       uint32_t wph = 0;
       int64_t q = 0;
       bool ok = true;
@@ -820,7 +821,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
               wph ^= 1;
             }
           }
-          const uint32_t fb = smem_u32(&fullB[slot]);
+          const uint32_t fb = smem_u32(&fullA[sa]);
           mbar_arrive_expect_tx(fb, (uint32_t)b_slot);
           if constexpr (PAIR) {
             // this CTA's half of every plane: rows [rank N'/2, (rank + 1) N'/2)
@@ -832,13 +833,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
             bulk_g2s(smem_u32(bring + slot * b_slot), bt + (int64_t)kc * b_slot, (uint32_t)b_slot, fb);
           }
           if (++slot == nbs) slot = 0;
+          if (++sa == na) sa = 0;
         }
       }
       if (!ok) {
-        // aborted: the copies still in flight (at most the last nbs) land before the CTA leaves
+        // aborted: the copies still in flight (at most the last nbs) land before
+        // the CTA leaves; their barriers also wait for A arrivals that an abort
+        // may have cut off, so each wait is short (a copy lands in microseconds)
         for (int64_t j = q - 1; j >= 0 && j >= q - nbs; --j)
-          mbar_wait<true>(smem_u32(&fullB[j % nbs]), (uint32_t)((j / nbs) & 1), abort_flag, a.err,
-                                 1000000000ull);
+          mbar_wait<true>(smem_u32(&fullA[j % na]), (uint32_t)((j / na) & 1), abort_flag, a.err,
+                          20000000ull);
       }
     }
     __syncwarp();
@@ -1164,7 +1168,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       const bool fence_a = MODE == TC_TF32 && CM == 4 && !a.a_tma;
       uint32_t da = da0, db = db0;
       int sa_i = 0, sb_i = 0, acc = 0;
-      uint32_t pha = 0, phb = 0, aph = 0;
+      uint32_t pha = 0, aph = 0;
       bool ok = true;
       int64_t jt = 0;
       for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++jt)) {
@@ -1179,7 +1183,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         for (int kc = 0; kc < kc_per; ++kc) {
           // the chunk's operands are in place (in both CTAs of a pair)
           if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err) ||
-              !mbar_wait(smem_u32(&fullB[sb_i]), phb, abort_flag, a.err) ||
               (PAIR && !mbar_wait(smem_u32(&pairA[sa_i]), pha, abort_flag, a.err))) {
             ok = false;
             break;
@@ -1241,7 +1244,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           db += b_step;
           if (++sb_i == nbs) {
             sb_i = 0;
-            phb ^= 1;
             db = db0;
           }
         }
@@ -1259,14 +1261,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     } else if (PAIR && lane == 0) {
       // ---------------------------------------------------------------- pair relay (odd CTA)
       // Follows the MMA thread's order: per chunk, once this CTA's A and B'
-      // slots are filled, one arrival on the even CTA's pairA of that A slot;
+      // slots are filled (one barrier: fullA), one arrival on the even CTA's
+      // pairA of that A slot;
       // per tile after the first n_acc, once this CTA's epilogue has drained
       // the accumulator set, one arrival on the even CTA's pairT.  The slots
       // themselves are released by the MMAs' commits, which reach both CTAs.
       const bool fence_a = MODE == TC_TF32 && CM == 4 && !a.a_tma;
       const uint32_t rA = mapa_cta(smem_u32(pairA), 0), rT = mapa_cta(smem_u32(pairT), 0);
-      int sa_i = 0, sb_i = 0, acc = 0;
-      uint32_t pha = 0, phb = 0, aph = 0;
+      int sa_i = 0, acc = 0;
+      uint32_t pha = 0, aph = 0;
       int64_t j = 0;
       bool ok = true;
       for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++j)) {
@@ -1275,8 +1278,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           mbar_arrive_remote(rT + 8u * (uint32_t)acc);
         }
         for (int kc = 0; kc < kc_per; ++kc) {
-          if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err) ||
-              !mbar_wait(smem_u32(&fullB[sb_i]), phb, abort_flag, a.err)) {
+          if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err)) {
             ok = false;
             break;
           }
@@ -1285,10 +1287,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
           if (++sa_i == na) {
             sa_i = 0;
             pha ^= 1;
-          }
-          if (++sb_i == nbs) {
-            sb_i = 0;
-            phb ^= 1;
           }
         }
         if (++acc == a.n_acc) {
