@@ -235,33 +235,33 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 flops x G
 # launch order (profiles/c3_bf16x3_launch_list.md,
 # profiles/c5_bf16x3_launch_list.md)
 MEASURED_TRAFFIC = {
-    ("tc_bf16x3", (21, 8, 8, 0)): 8.7436e+09,   # c3
-    ("tc_bf16x3", (21, 7, 8, 0)): 6.4079e+09,   # c3
+    ("tc_bf16x3", (21, 8, 8, 0)): 8.7815e+09,   # c3
+    ("tc_bf16x3", (21, 7, 8, 0)): 6.3947e+09,   # c3
     ("tc_bf16x3", (12, 10, 7, 7)): 5.1233e+09,   # c3
-    ("tc_bf16x3", (11, 10, 9, 5)): 1.1156e+09,   # c3
-    ("tc_bf16x3", (22, 4, 6, 0)): 2.6200e+09,   # c3
-    ("tc_bf16x3", (15, 7, 12, 0)): 1.0586e+09,   # c3
-    ("tc_bf16x3", (19, 8, 5, 0)): 1.1940e+09,   # c3
-    ("tc_bf16x3", (13, 9, 11, 0)): 1.3054e+08,   # c3
-    ("tc_bf16x3", (16, 6, 10, 0)): 5.0608e+08,   # c3
-    ("tc_bf16x3", (20, 5, 4, 0)): 3.6432e+08,   # c3
-    ("tc_bf16x3", (13, 8, 11, 0)): 9.5436e+07,   # c3
-    ("tc_bf16x3", (18, 6, 4, 0)): 1.4484e+08,   # c3
-    ("tc_bf16x3", (20, 8, 8, 0)): 4.3271e+09,   # c5
-    ("tc_bf16x3", (18, 8, 9, 1)): 3.3313e+09,   # c5
-    ("tc_bf16x3", (14, 9, 8, 5)): 3.9273e+09,   # c5
-    ("tc_bf16x3", (21, 7, 7, 0)): 4.2373e+09,   # c5
-    ("tc_bf16x3", (19, 8, 8, 0)): 2.1238e+09,   # c5
-    ("tc_bf16x3", (13, 10, 11, 0)): 2.4044e+08,   # c5
-    ("tc_bf16x3", (18, 6, 9, 0)): 1.1464e+09,   # c5
+    ("tc_bf16x3", (22, 4, 6, 0)): 2.6202e+09,   # c3
+    ("tc_bf16x3", (11, 10, 9, 5)): 1.1262e+09,   # c3
+    ("tc_bf16x3", (15, 7, 12, 0)): 1.0577e+09,   # c3
+    ("tc_bf16x3", (19, 8, 5, 0)): 1.1941e+09,   # c3
+    ("tc_bf16x3", (16, 6, 10, 0)): 5.0651e+08,   # c3
+    ("tc_bf16x3", (13, 9, 11, 0)): 1.3026e+08,   # c3
+    ("tc_bf16x3", (20, 5, 4, 0)): 3.6406e+08,   # c3
+    ("tc_bf16x3", (13, 8, 11, 0)): 9.5338e+07,   # c3
+    ("tc_bf16x3", (18, 6, 4, 0)): 1.4485e+08,   # c3
+    ("tc_bf16x3", (20, 8, 8, 0)): 4.3087e+09,   # c5
+    ("tc_bf16x3", (18, 8, 9, 1)): 3.3264e+09,   # c5
+    ("tc_bf16x3", (14, 9, 8, 5)): 3.2887e+09,   # c5
+    ("tc_bf16x3", (21, 7, 7, 0)): 4.2365e+09,   # c5
+    ("tc_bf16x3", (19, 8, 8, 0)): 2.1285e+09,   # c5
+    ("tc_bf16x3", (13, 10, 11, 0)): 2.4036e+08,   # c5
+    ("tc_bf16x3", (18, 6, 9, 0)): 1.1467e+09,   # c5
     ("tc_bf16x3", (13, 14, 3, 0)): 1.0959e+09,   # c5
-    ("tc_bf16x3", (12, 11, 9, 1)): 2.0227e+08,   # c5
-    ("tc_bf16x3", (12, 9, 9, 3)): 2.6093e+08,   # c5
-    ("tc_bf16x3", (18, 6, 8, 0)): 6.0653e+08,   # c5
-    ("tc_bf16x3", (19, 7, 5, 0)): 6.4699e+08,   # c5
-    ("tc_bf16x3", (11, 8, 10, 0)): 8.4869e+06,   # c5
-    ("tc_bf16x3", (11, 11, 8, 0)): 1.1226e+08,   # c5
-    ("tc_bf16x3", (12, 5, 12, 0)): 7.2395e+07,   # c5
+    ("tc_bf16x3", (12, 11, 9, 1)): 2.0077e+08,   # c5
+    ("tc_bf16x3", (18, 6, 8, 0)): 6.0652e+08,   # c5
+    ("tc_bf16x3", (12, 9, 9, 3)): 2.6183e+08,   # c5
+    ("tc_bf16x3", (19, 7, 5, 0)): 6.4671e+08,   # c5
+    ("tc_bf16x3", (11, 11, 8, 0)): 4.2098e+07,   # c5
+    ("tc_bf16x3", (12, 5, 12, 0)): 7.2059e+07,   # c5
+    ("tc_bf16x3", (11, 8, 10, 0)): 8.4800e+06,   # c5
 }
 
 
