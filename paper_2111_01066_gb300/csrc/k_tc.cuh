@@ -691,11 +691,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   uint64_t* tfull = bars + 3 * TC_MAX_A;
   uint64_t* tempty = tfull + TC_MAX_ACC;
   uint64_t* fin = tempty + TC_MAX_ACC;
-  // SM pairs, in the even CTA: the odd CTA's operands of a chunk are in place
-  // (per A slot) and its epilogue has drained an accumulator set
-  uint64_t* pairA = fin + 1;
-  uint64_t* pairT = pairA + TC_MAX_A;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(pairT + TC_MAX_ACC);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int64_t* offCm = reinterpret_cast<int64_t*>(tmem_slot + 4);
   float2* epi_stage = reinterpret_cast<float2*>(reinterpret_cast<uint8_t*>(bars) + 4096);
@@ -710,18 +706,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
   for (int c = threadIdx.x; c < 128; c += blockDim.x)
     offCn[c] = c < tnv ? deposit_hi((uint64_t)c, g.c_npos, 0, a.tnb) : 0;
   if (threadIdx.x == 0) {
+    // SM pairs: the even CTA's fullA and tempty also take one arrival from the
+    // odd CTA per phase (its chunk in place, its accumulator set drained)
+    const uint32_t peer = (PAIR && rank == 0) ? 1u : 0u;
     for (int s = 0; s < na; ++s) {
-      mbar_init(smem_u32(&fullA[s]), a.fa_count + 1);   // + the B' producer's arrival
+      mbar_init(smem_u32(&fullA[s]), a.fa_count + 1 + peer);   // + the B' producer's arrival
       mbar_init(smem_u32(&emptyA[s]), 1);
       mbar_init(smem_u32(&rawA[s]), 1);
     }
     for (int i = 0; i < TC_MAX_ACC; ++i) {
       mbar_init(smem_u32(&tfull[i]), 1);
-      mbar_init(smem_u32(&tempty[i]), TC_EPI_WARPS * 32);
+      mbar_init(smem_u32(&tempty[i]), TC_EPI_WARPS * 32 + peer);
     }
     mbar_init(smem_u32(fin), 1);
-    for (int i = 0; i < TC_MAX_A; ++i) mbar_init(smem_u32(&pairA[i]), 1);
-    for (int i = 0; i < TC_MAX_ACC; ++i) mbar_init(smem_u32(&pairT[i]), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -1173,8 +1170,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
       int64_t jt = 0;
       for (int64_t tile = seq_tile(0); tile >= 0 && ok; tile = seq_tile(++jt)) {
         // the accumulator set is drained (in both CTAs of a pair)
-        if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err) ||
-            (PAIR && !mbar_wait(smem_u32(&pairT[acc]), aph ^ 1, abort_flag, a.err))) {
+        if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, a.err)) {
           ok = false;
           break;
         }
@@ -1182,8 +1178,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * setw);
         for (int kc = 0; kc < kc_per; ++kc) {
           // the chunk's operands are in place (in both CTAs of a pair)
-          if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err) ||
-              (PAIR && !mbar_wait(smem_u32(&pairA[sa_i]), pha, abort_flag, a.err))) {
+          if (!mbar_wait(smem_u32(&fullA[sa_i]), pha, abort_flag, a.err)) {
             ok = false;
             break;
           }
@@ -1261,13 +1256,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_cgemm_tc(const __grid_constan
     } else if (PAIR && lane == 0) {
       // ---------------------------------------------------------------- pair relay (odd CTA)
       // Follows the MMA thread's order: per chunk, once this CTA's A and B'
-      // slots are filled (one barrier: fullA), one arrival on the even CTA's
-      // pairA of that A slot;
-      // per tile after the first n_acc, once this CTA's epilogue has drained
-      // the accumulator set, one arrival on the even CTA's pairT.  The slots
-      // themselves are released by the MMAs' commits, which reach both CTAs.
+      // slots are filled (its fullA), one arrival on the even CTA's fullA of
+      // that slot; per tile after the first n_acc, once this CTA's epilogue has
+      // drained the accumulator set, one arrival on the even CTA's tempty.  Each
+      // arrival lands in the phase it completes: the even CTA's previous phase
+      // of that barrier is over before this CTA's own one can complete (the
+      // slot is refilled, the set drained, only after the even CTA's MMAs of
+      // that previous phase).  The slots themselves are released by the MMAs'
+      // commits, which reach both CTAs.
       const bool fence_a = MODE == TC_TF32 && CM == 4 && !a.a_tma;
-      const uint32_t rA = mapa_cta(smem_u32(pairA), 0), rT = mapa_cta(smem_u32(pairT), 0);
+      const uint32_t rA = mapa_cta(smem_u32(fullA), 0), rT = mapa_cta(smem_u32(tempty), 0);
       int sa_i = 0, acc = 0;
       uint32_t pha = 0, aph = 0;
       int64_t j = 0;
