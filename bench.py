@@ -235,33 +235,35 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 flops x G
 # launch order (profiles/c3_bf16x3_launch_list.md,
 # profiles/c5_bf16x3_launch_list.md)
 MEASURED_TRAFFIC = {
-    ("tc_bf16x3", (21, 8, 8, 0)): 8.7815e+09,   # c3
-    ("tc_bf16x3", (21, 7, 8, 0)): 6.3947e+09,   # c3
+    ("tc_bf16x3", (21, 8, 8, 0)): 8.7832e+09,   # c3
+    ("tc_bf16x3", (21, 7, 8, 0)): 6.3952e+09,   # c3
     ("tc_bf16x3", (12, 10, 7, 7)): 5.1233e+09,   # c3
-    ("tc_bf16x3", (22, 4, 6, 0)): 2.6202e+09,   # c3
-    ("tc_bf16x3", (11, 10, 9, 5)): 1.1262e+09,   # c3
-    ("tc_bf16x3", (15, 7, 12, 0)): 1.0577e+09,   # c3
-    ("tc_bf16x3", (19, 8, 5, 0)): 1.1941e+09,   # c3
-    ("tc_bf16x3", (16, 6, 10, 0)): 5.0651e+08,   # c3
-    ("tc_bf16x3", (13, 9, 11, 0)): 1.3026e+08,   # c3
-    ("tc_bf16x3", (20, 5, 4, 0)): 3.6406e+08,   # c3
-    ("tc_bf16x3", (13, 8, 11, 0)): 9.5338e+07,   # c3
-    ("tc_bf16x3", (18, 6, 4, 0)): 1.4485e+08,   # c3
-    ("tc_bf16x3", (20, 8, 8, 0)): 4.3087e+09,   # c5
-    ("tc_bf16x3", (18, 8, 9, 1)): 3.3264e+09,   # c5
-    ("tc_bf16x3", (14, 9, 8, 5)): 3.2887e+09,   # c5
-    ("tc_bf16x3", (21, 7, 7, 0)): 4.2365e+09,   # c5
-    ("tc_bf16x3", (19, 8, 8, 0)): 2.1285e+09,   # c5
-    ("tc_bf16x3", (13, 10, 11, 0)): 2.4036e+08,   # c5
-    ("tc_bf16x3", (18, 6, 9, 0)): 1.1467e+09,   # c5
-    ("tc_bf16x3", (13, 14, 3, 0)): 1.0959e+09,   # c5
-    ("tc_bf16x3", (12, 11, 9, 1)): 2.0077e+08,   # c5
-    ("tc_bf16x3", (18, 6, 8, 0)): 6.0652e+08,   # c5
-    ("tc_bf16x3", (12, 9, 9, 3)): 2.6183e+08,   # c5
-    ("tc_bf16x3", (19, 7, 5, 0)): 6.4671e+08,   # c5
-    ("tc_bf16x3", (11, 11, 8, 0)): 4.2098e+07,   # c5
-    ("tc_bf16x3", (12, 5, 12, 0)): 7.2059e+07,   # c5
-    ("tc_bf16x3", (11, 8, 10, 0)): 8.4800e+06,   # c5
+    ("tc_bf16x3", (22, 4, 6, 0)): 2.6201e+09,   # c3
+    ("tc_bf16x3", (11, 10, 9, 5)): 1.1167e+09,   # c3
+    ("tc_bf16x3", (15, 7, 12, 0)): 1.0527e+09,   # c3
+    ("tc_bf16x3", (19, 8, 5, 0)): 1.1935e+09,   # c3
+    ("tc_bf16x3", (16, 6, 10, 0)): 5.0633e+08,   # c3
+    ("tc_bf16x3", (13, 9, 11, 0)): 1.3020e+08,   # c3
+    ("tc_bf16x3", (20, 5, 4, 0)): 3.6353e+08,   # c3
+    ("tc_bf16x3", (13, 8, 11, 0)): 9.5432e+07,   # c3
+    ("tc_bf16x3", (18, 6, 4, 0)): 1.4212e+08,   # c3
+    ("tc_bf16x3", (10, 7, 7, 0)): 1.4021e+06,   # c3
+    ("tc_bf16x3", (20, 8, 8, 0)): 4.3223e+09,   # c5
+    ("tc_bf16x3", (18, 8, 9, 1)): 3.3285e+09,   # c5
+    ("tc_bf16x3", (14, 9, 8, 5)): 3.3978e+09,   # c5
+    ("tc_bf16x3", (21, 7, 7, 0)): 4.2359e+09,   # c5
+    ("tc_bf16x3", (19, 8, 8, 0)): 2.1308e+09,   # c5
+    ("tc_bf16x3", (13, 10, 11, 0)): 2.4344e+08,   # c5
+    ("tc_bf16x3", (18, 6, 9, 0)): 1.1462e+09,   # c5
+    ("tc_bf16x3", (13, 14, 3, 0)): 1.0958e+09,   # c5
+    ("tc_bf16x3", (12, 11, 9, 1)): 2.0201e+08,   # c5
+    ("tc_bf16x3", (12, 9, 9, 3)): 2.6118e+08,   # c5
+    ("tc_bf16x3", (18, 6, 8, 0)): 6.0651e+08,   # c5
+    ("tc_bf16x3", (11, 11, 8, 0)): 1.2073e+08,   # c5
+    ("tc_bf16x3", (19, 7, 5, 0)): 6.4670e+08,   # c5
+    ("tc_bf16x3", (12, 5, 12, 0)): 7.2219e+07,   # c5
+    ("tc_bf16x3", (11, 8, 10, 0)): 8.4833e+06,   # c5
+    ("tc_bf16x3", (14, 7, 7, 0)): 1.7131e+07,   # c5
 }
 
 
