@@ -736,14 +736,25 @@ def run_workload(name: str, args, ctx: dict, prec: str, cm: int, pool_n: int, n_
             return res
         return None
 
-    # untimed first call: device state + warm-up; then the per-step autotuner
+    # untimed first call: device state + warm-up; then the per-step autotuner,
+    # or the per-step kernel choices of an earlier run (a profiled run replays
+    # those of its unprofiled twin: under a profiler the autotuner's own timing
+    # is distorted and would pick other kernels)
     step(plan, out)
     torch.cuda.synchronize()
     t_tune = time.time()
-    if args.autotune:
+    if ctx.get("tuning_in"):
+        with open(ctx["tuning_in"]) as f:
+            plan.set_tuning(json.load(f))
+        step(plan, out)
+        torch.cuda.synchronize()
+    elif args.autotune:
         plan.autotune(reps=2, stream=stream)
         step(plan, out)
         torch.cuda.synchronize()
+    if ctx.get("tuning_out") and rank == 0:
+        with open(ctx["tuning_out"], "w") as f:
+            json.dump(plan.get_tuning(), f)
     t_tune = time.time() - t_tune
     barrier(world)
     clocks = ClockSampler(ctx["local"])
@@ -951,6 +962,10 @@ def main() -> int:
                     help="with the default workload on one GPU, also time the 53-qubit block (c5 sub-object)")
     ap.add_argument("--c5-steps", type=int, default=5)
     ap.add_argument("--autotune", type=int, default=1, help="tune kernels per step before timing")
+    ap.add_argument("--tuning-out", default=None, help="write the per-step kernel choices (JSON) after tuning")
+    ap.add_argument("--tuning-in", default=None,
+                    help="use the per-step kernel choices of an earlier run (JSON from --tuning-out) instead of "
+                         "tuning: the same plan then runs the same kernels, e.g. under a profiler")
     ap.add_argument("--shard", default="batches", choices=["batches", "slices"],
                     help="N > 1: every rank its own batch (weak scaling), or one batch whose slices are split "
                          "across the ranks and summed by one FP64 all-reduce (strong scaling)")
@@ -993,6 +1008,7 @@ def main() -> int:
         plan_choice = (int(sd), float(wt))
     ctx = {"tn": tn, "rank": rank, "world": world, "local": local, "dev": dev, "shard": args.shard,
            "plan_choice": plan_choice, "step_report": args.step_report,
+           "tuning_in": args.tuning_in, "tuning_out": args.tuning_out,
            "stream": torch.cuda.current_stream(),
            "flush": torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)}
     n_select = args.select if args.select is not None else WORKLOAD_RUN[name].get("select", 6)
@@ -1006,7 +1022,7 @@ def main() -> int:
     if args.c5 and name == "c3" and world == 1:
         del r["plan"]
         torch.cuda.empty_cache()
-        r5 = run_workload("c5", args, dict(ctx, plan_choice=None, step_report=None), prec, args.complex_mult, args.pool, WORKLOAD_RUN["c5"]["select"], False,
+        r5 = run_workload("c5", args, dict(ctx, plan_choice=None, step_report=None, tuning_in=None, tuning_out=None), prec, args.complex_mult, args.pool, WORKLOAD_RUN["c5"]["select"], False,
                           min(args.cpu_budget, 10.0), args.c5_steps, args.warmup)
         c5 = {"workload": workload_string("c5", r5["circ"], r5["cfg"], r5["info"]["log2_slices"], r5["k_open"]),
               "metric": "slices/s", "value": r5["value"], "ms_per_block": r5["ms"], "steps": args.c5_steps,

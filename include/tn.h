@@ -284,6 +284,30 @@ tn_status tn_plan_step_times(tn_plan_t* plan, int32_t reps, double* ms_out, int3
  * overwritten (the next call recomputes them). */
 tn_status tn_plan_autotune(tn_plan_t* plan, int32_t reps, void* stream);
 
+/* The kernel chosen for every step (after one tn_contract_slices call; the
+ * autotuner's choices once tn_plan_autotune ran), TN_TUNING_INTS int32 per step
+ * in plan order: kernel id (as in tn_plan_step_times), tile width as log2
+ * complex columns (-1: the CUDA-core default), write-back order (0 direct, 1
+ * staged in C's memory order), B' ring slots (0 for CUDA-core kernels), SM
+ * pair (0 or 1).  `out` is a host array of `cap` int32; *n_out receives the
+ * count written (n_steps * TN_TUNING_INTS); TN_ERR_ARG if cap is too small.
+ * With tn_plan_set_tuning it carries a tuning from one process to another (a
+ * profiled run, whose own timing the profiler distorts, then runs the kernels
+ * an unprofiled autotuner chose).  Host only; no device work.  The paper has no
+ * counterpart (an implementation's kernel choice). */
+#define TN_TUNING_INTS 5
+tn_status tn_plan_get_tuning(const tn_plan_t* plan, int32_t* out, int32_t cap, int32_t* n_out);
+
+/* Apply a tuning from tn_plan_get_tuning of a plan with the same steps (the
+ * same network and tn_plan_opts), after one tn_contract_slices call on this
+ * plan: every step gets the given kernel as the autotuner would have built it.
+ * n must be n_steps * TN_TUNING_INTS; an unknown kernel id, or a choice the
+ * step cannot take (a tensor-core kernel for the FP32 mode, rings that do not
+ * fit), gives TN_ERR_ARG and leaves the plan's kernels unchanged.  Host only;
+ * the next contract call captures the chunk graph again and reruns the
+ * prologues. */
+tn_status tn_plan_set_tuning(tn_plan_t* plan, const int32_t* in, int32_t n);
+
 /* Plan selection by measured time (SI, TN section: the order whose measured
  * slice time is smallest is kept, not the one with the fewest flops).  Builds
  * n_candidates plans from *opts with seeds seed, seed+1, ... and memory weights

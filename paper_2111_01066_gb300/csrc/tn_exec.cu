@@ -469,6 +469,7 @@ struct DeviceState {
   unsigned* counter = nullptr;
   int32_t* err = nullptr;
   uint8_t* ws = nullptr;
+  int64_t ws_bytes = 0;           // capacity of ws
   double2* root_part = nullptr;   // [groups][2^k] partial slice sums
   float* amax = nullptr;          // FP16X3: largest component of every node (leaves, then steps)
   int root_groups = 1;
@@ -690,6 +691,7 @@ static void ensure_device(Plan& p) {
     cudaGetLastError();
     fail(TN_ERR_OOM, "workspace allocation of " + std::to_string(ws) + " bytes failed");
   }
+  ds->ws_bytes = ws;
   ds->root_groups = std::min(1 << p.log2_batch, 64);
   CK(cudaMalloc(&ds->root_part, sizeof(double2) * (size_t)ds->root_groups << p.root.rank));
   if (!in_arena(p.root.off, (int64_t)1 << p.root.rank, 1 << __builtin_popcount(p.root.bmask)))
@@ -924,6 +926,26 @@ extern "C" tn_status tn_plan_step_times(tn_plan_t* h, int32_t reps, double* ms_o
   API_END
 }
 
+// Step d's launch with one kernel choice (as the autotuner builds its candidates).
+static StepLaunch build_choice(const DeviceState& ds, const StepDesc& d, int kid, int tn_log, int epi, int bslots,
+                               int pair) {
+  return make_launch(step_args(ds, d, kid, tn_log), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
+                     d.c_elems, true, epi, (int64_t)256 << 20, bslots, pair);
+}
+
+// After the kernels of a plan changed: group runs, chunk graph and prologues anew.
+static void kernels_changed(Plan& p, DeviceState& ds) {
+  build_groups(p, ds);
+  if (ds.graph) {
+    cudaGraphExecDestroy(ds.graph);
+    ds.graph = nullptr;
+  }
+  ds.graph_failed = false;
+  ds.eager_done = false;
+  ds.pro0_done = false;   // the arena may have been overwritten: prologues run again
+  ds.pro2_valid = false;
+}
+
 // Autotuner: for every step, time the candidate kernels in place (tensor-core
 // tiles of 32, 64 or 128 complex columns in the TF32 / BF16X3 / FP16X3 modes,
 // each with either write-back order, with the default or a deeper B' ring (4,
@@ -943,18 +965,17 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  int64_t ws_cap = 0;
-  for (const StepLaunch& L : ds.launches) ws_cap = std::max(ws_cap, L.ws_bytes);
   auto time_launch = [&](StepLaunch& L) -> double {
-    if (L.ws_bytes > ws_cap) {
+    if (L.ws_bytes > ds.ws_bytes) {
       CK(cudaStreamSynchronize(s));
       CK(cudaFree(ds.ws));
       ds.ws = nullptr;
+      ds.ws_bytes = 0;
       if (cudaMalloc(&ds.ws, (size_t)L.ws_bytes) != cudaSuccess) {
         cudaGetLastError();
         fail(TN_ERR_OOM, "autotune workspace allocation failed");
       }
-      ws_cap = L.ws_bytes;
+      ds.ws_bytes = L.ws_bytes;
     }
     launch_step(L, ds.ws, ds.err, s);  // warm-up
     CK(cudaEventRecord(e0, s));
@@ -968,8 +989,7 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   for (size_t i = 0; i < p.steps.size(); ++i) {
     const StepDesc& d = p.steps[i];
     auto build = [&](int kid, int tn_log, int epi, int bslots, int pair) {
-      return make_launch(step_args(ds, d, kid, tn_log), kid, 64 - __builtin_clzll((uint64_t)d.a_elems) - 1, 1,
-                         d.c_elems, true, epi, (int64_t)256 << 20, bslots, pair);
+      return build_choice(ds, d, kid, tn_log, epi, bslots, pair);
     };
     double best = time_launch(ds.launches[i]);
     // kernel, tile width (log2 complex columns), write-back, B' slots, SM pairs
@@ -1015,15 +1035,70 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
   CK(cudaGetLastError());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  build_groups(p, ds);   // kernels may have changed
-  if (ds.graph) {
-    cudaGraphExecDestroy(ds.graph);
-    ds.graph = nullptr;
+  kernels_changed(p, ds);
+  API_END
+}
+
+extern "C" tn_status tn_plan_get_tuning(const tn_plan_t* h, int32_t* out, int32_t cap, int32_t* n_out) {
+  API_BEGIN
+  if (!h || !out || !n_out) fail(TN_ERR_ARG, "tn_plan_get_tuning: NULL argument");
+  const Plan& p = h->plan;
+  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_get_tuning: run tn_contract_slices first");
+  const int64_t need = (int64_t)p.steps.size() * TN_TUNING_INTS;
+  if (cap < need) fail(TN_ERR_ARG, "tn_plan_get_tuning: cap below n_steps * TN_TUNING_INTS");
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    const StepLaunch& L = p.dev->launches[i];
+    int32_t* o = out + i * TN_TUNING_INTS;
+    const bool tc = is_tc(L.kid);
+    o[0] = L.kid;
+    o[1] = tc ? L.g.tn : -1;
+    o[2] = tc ? L.tc.epi_ok : 0;
+    o[3] = tc ? L.tc.nbs : 0;
+    o[4] = tc ? L.tc.pair : 0;
   }
-  ds.graph_failed = false;
-  ds.eager_done = false;
-  ds.pro0_done = false;   // the arena was overwritten: prologues run again
-  ds.pro2_valid = false;
+  *n_out = (int32_t)need;
+  API_END
+}
+
+extern "C" tn_status tn_plan_set_tuning(tn_plan_t* h, const int32_t* in, int32_t n) {
+  API_BEGIN
+  if (!h || !in) fail(TN_ERR_ARG, "tn_plan_set_tuning: NULL argument");
+  Plan& p = h->plan;
+  if (!p.dev) fail(TN_ERR_ARG, "tn_plan_set_tuning: run tn_contract_slices first");
+  if ((int64_t)n != (int64_t)p.steps.size() * TN_TUNING_INTS)
+    fail(TN_ERR_ARG, "tn_plan_set_tuning: n is not n_steps * TN_TUNING_INTS");
+  DeviceState& ds = *p.dev;
+  std::vector<StepLaunch> next(p.steps.size());
+  int64_t ws = ds.ws_bytes;
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    const int32_t* c = in + i * TN_TUNING_INTS;
+    const int kid = c[0];
+    const bool simt = kid == K_SIMT_64x64 || kid == K_SIMT_128x16 || kid == K_SIMT_256x4;
+    if (!simt && !is_tc(kid)) fail(TN_ERR_ARG, "tn_plan_set_tuning: unknown kernel id");
+    if (is_tc(kid) && (p.opts.precision == TN_PREC_FP32 || kid != tc_kernel(p.opts.precision, p.opts.complex_mult)))
+      fail(TN_ERR_ARG, "tn_plan_set_tuning: tensor-core kernel of another precision or product");
+    if (c[2] < 0 || c[2] > 1 || c[3] < 0 || c[3] > TC_MAX_B || c[4] < 0 || c[4] > 1 || c[1] < -1 || c[1] > 7)
+      fail(TN_ERR_ARG, "tn_plan_set_tuning: choice out of range");
+    try {
+      next[i] = simt ? build_choice(ds, p.steps[i], kid, -1, 0, 0, 0)
+                     : build_choice(ds, p.steps[i], kid, c[1], c[2], c[3], c[4] && p.opts.sm_pairs ? 1 : 0);
+    } catch (const TnError& e) {
+      fail(TN_ERR_ARG, std::string("tn_plan_set_tuning: step ") + std::to_string(i) + ": " + e.msg);
+    }
+    ws = std::max(ws, next[i].ws_bytes);
+  }
+  if (ws > ds.ws_bytes) {   // a larger workspace (synchronises the device through cudaFree)
+    CK(cudaFree(ds.ws));
+    ds.ws = nullptr;
+    ds.ws_bytes = 0;
+    if (cudaMalloc(&ds.ws, (size_t)ws) != cudaSuccess) {
+      cudaGetLastError();
+      fail(TN_ERR_OOM, "tn_plan_set_tuning: workspace allocation failed");
+    }
+    ds.ws_bytes = ws;
+  }
+  ds.launches.swap(next);
+  kernels_changed(p, ds);
   API_END
 }
 

@@ -26,6 +26,8 @@ TN_ERR_TIMEOUT = -5
 TN_ERR_UNSUPPORTED = -6
 TN_ERR_DEVICE = -7
 
+TN_TUNING_INTS = 5   # int32 per step in tn_plan_get_tuning / tn_plan_set_tuning
+
 PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2, "fp16x3": 3}
 PREC_NAME = {v: k for k, v in PREC.items()}
 
@@ -105,6 +107,9 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p]),
     "tn_plan_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "tn_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "tn_plan_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "tn_plan_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
     "tn_plan_step_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "tn_plan_destroy": (None, [ctypes.c_void_p]),
@@ -336,6 +341,21 @@ class Plan:
     def autotune(self, reps: int = 2, stream=None) -> None:
         """Pick the fastest kernel / tile for every step by timing (tn_plan_autotune)."""
         _check(load().tn_plan_autotune(self.handle, reps, _stream_handle(stream)))
+
+    def get_tuning(self) -> List[List[int]]:
+        """tn_plan_get_tuning: per step [kernel id, log2 tile width, write-back,
+        B' slots, SM pair] of the kernels in use (after one contract call)."""
+        n = self.info()["n_steps"]
+        buf = (ctypes.c_int32 * max(1, n * TN_TUNING_INTS))()
+        cnt = ctypes.c_int32()
+        _check(load().tn_plan_get_tuning(self.handle, buf, n * TN_TUNING_INTS, ctypes.byref(cnt)))
+        v = list(buf[:cnt.value])
+        return [v[i:i + TN_TUNING_INTS] for i in range(0, len(v), TN_TUNING_INTS)]
+
+    def set_tuning(self, tuning: Sequence[Sequence[int]]) -> None:
+        """tn_plan_set_tuning: use the given per-step kernel choices (after one contract call)."""
+        flat = [int(x) for row in tuning for x in row]
+        _check(load().tn_plan_set_tuning(self.handle, _i32(flat), len(flat)))
 
     def sync(self, stream=None) -> None:
         _check(load().tn_plan_sync(self.handle, _stream_handle(stream)))

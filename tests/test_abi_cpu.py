@@ -379,6 +379,27 @@ def test_select_list_and_device_sync_validate_before_device_work(tn):
     assert e.value.status == tn.TN_ERR_ARG
 
 
+def test_tuning_calls_validate_before_device_work(tn):
+    """tn_plan_get_tuning / tn_plan_set_tuning need the plan's device state (one
+    contract call) and reject NULL arguments, short buffers and wrong lengths
+    before touching anything."""
+    import ctypes
+    lib = tn.load()
+    circ, om, _ = rqcgen.config_circuit("c1")
+    plan = tn.Plan(tn.Network(circ), open_mask=om, trials=2)
+    n = plan.info()["n_steps"]
+    buf = (ctypes.c_int32 * (n * tn.TN_TUNING_INTS))()
+    cnt = ctypes.c_int32()
+    for args in ((plan.handle, None, len(buf), ctypes.byref(cnt)), (plan.handle, buf, len(buf), None),
+                 (None, buf, len(buf), ctypes.byref(cnt)), (plan.handle, buf, len(buf), ctypes.byref(cnt))):
+        assert lib.tn_plan_get_tuning(*args) == tn.TN_ERR_ARG   # the last: no device state yet
+    for args in ((plan.handle, None, len(buf)), (None, buf, len(buf)), (plan.handle, buf, len(buf))):
+        assert lib.tn_plan_set_tuning(*args) == tn.TN_ERR_ARG
+    with pytest.raises(tn.TnError) as e:
+        plan.get_tuning()
+    assert e.value.status == tn.TN_ERR_ARG
+
+
 @pytest.mark.parametrize("name", ["c1", "c2", "c3"])
 def test_step_groups_are_consecutive_independent_and_small(tn, name):
     """Small steps come in groups that the executor runs as one launch: a

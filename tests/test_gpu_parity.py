@@ -367,6 +367,38 @@ def test_c2_autotuned_plan_still_matches_golden(env, prec):
         _check_plan(got, want, circ.n_qubits, prec, f"c2 autotuned {prec}")
 
 
+def test_tuning_carries_to_another_plan(env):
+    """The autotuner's per-step kernel choices read from one plan and applied
+    to a second plan of the same network and options: the second plan then
+    runs exactly those kernels (read back equal) and still gives the oracle's
+    amplitudes; choices of the wrong length or precision are refused."""
+    tn, torch = env
+    from tests.golden.make_golden import read
+    want = read("c2")
+    circ, om, cb = rqcgen.config_circuit("c2")
+    net = tn.Network(circ)
+    kw = dict(open_mask=om, max_log2_intermediate=26, precision="bf16x3")
+    a = tn.Plan(net, **kw)
+    _run_plan(tn, torch, a, 0, 1, [cb], 10)
+    a.autotune(reps=1)
+    tuning = a.get_tuning()
+    assert len(tuning) == a.info()["n_steps"] and all(len(t) == tn.TN_TUNING_INTS for t in tuning)
+    b = tn.Plan(net, **kw)
+    _run_plan(tn, torch, b, 0, 1, [cb], 10)
+    b.set_tuning(tuning)
+    assert b.get_tuning() == tuning
+    for _ in range(2):   # eager chunk, then the re-captured graph
+        got = _run_plan(tn, torch, b, 0, 1, [cb], 10)
+        _check_plan(got, want, circ.n_qubits, "bf16x3", "c2 with a carried tuning")
+    with pytest.raises(tn.TnError):
+        b.set_tuning(tuning[:-1])
+    fp32 = tn.Plan(net, **dict(kw, precision="fp32"))
+    _run_plan(tn, torch, fp32, 0, 1, [cb], 10)
+    if any(tn.Plan.KERNELS.get(t[0], "").startswith("tc") for t in tuning):
+        with pytest.raises(tn.TnError):
+            fp32.set_tuning(tuning)
+
+
 def test_plan_selection_by_measured_time(env):
     """tn_plan_select times one chunk of each candidate plan and keeps the
     fastest; the chosen plan still gives the oracle's amplitudes."""
