@@ -231,39 +231,40 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 flops x G
 # DRAM bytes (read + write) per launch of the tensor-core GEMM at full size,
 # keyed by (kernel, log2 m,k,n,batch): one ncu launch list (time and DRAM bytes,
 # a single pass per launch) of one timed step of each benchmark plan with the
-# kernels the autotuner chose (one SM or SM pairs), matched to the steps in
-# launch order (profiles/c3_bf16x3_launch_list.md,
+# kernels an unprofiled run's autotuner chose (one SM or SM pairs; replayed in
+# the profiled run), matched to the steps in launch order (profiles/c3_bf16x3_launch_list.md,
 # profiles/c5_bf16x3_launch_list.md)
 MEASURED_TRAFFIC = {
-    ("tc_bf16x3", (21, 8, 8, 0)): 8.7832e+09,   # c3
-    ("tc_bf16x3", (21, 7, 8, 0)): 6.3952e+09,   # c3
-    ("tc_bf16x3", (12, 10, 7, 7)): 5.1233e+09,   # c3
-    ("tc_bf16x3", (22, 4, 6, 0)): 2.6201e+09,   # c3
-    ("tc_bf16x3", (11, 10, 9, 5)): 1.1167e+09,   # c3
-    ("tc_bf16x3", (15, 7, 12, 0)): 1.0527e+09,   # c3
+    ("tc_bf16x3", (21, 8, 8, 0)): 8.7764e+09,   # c3
+    ("tc_bf16x3", (21, 7, 8, 0)): 6.3972e+09,   # c3
+    ("tc_bf16x3", (12, 10, 7, 7)): 5.2334e+09,   # c3
+    ("tc_bf16x3", (22, 4, 6, 0)): 2.6207e+09,   # c3
+    ("tc_bf16x3", (11, 10, 9, 5)): 1.1135e+09,   # c3
+    ("tc_bf16x3", (15, 7, 12, 0)): 1.0525e+09,   # c3
     ("tc_bf16x3", (19, 8, 5, 0)): 1.1935e+09,   # c3
-    ("tc_bf16x3", (16, 6, 10, 0)): 5.0633e+08,   # c3
-    ("tc_bf16x3", (13, 9, 11, 0)): 1.3020e+08,   # c3
-    ("tc_bf16x3", (20, 5, 4, 0)): 3.6353e+08,   # c3
-    ("tc_bf16x3", (13, 8, 11, 0)): 9.5432e+07,   # c3
-    ("tc_bf16x3", (18, 6, 4, 0)): 1.4212e+08,   # c3
-    ("tc_bf16x3", (10, 7, 7, 0)): 1.4021e+06,   # c3
-    ("tc_bf16x3", (20, 8, 8, 0)): 4.3223e+09,   # c5
-    ("tc_bf16x3", (18, 8, 9, 1)): 3.3285e+09,   # c5
-    ("tc_bf16x3", (14, 9, 8, 5)): 3.3978e+09,   # c5
-    ("tc_bf16x3", (21, 7, 7, 0)): 4.2359e+09,   # c5
-    ("tc_bf16x3", (19, 8, 8, 0)): 2.1308e+09,   # c5
-    ("tc_bf16x3", (13, 10, 11, 0)): 2.4344e+08,   # c5
-    ("tc_bf16x3", (18, 6, 9, 0)): 1.1462e+09,   # c5
-    ("tc_bf16x3", (13, 14, 3, 0)): 1.0958e+09,   # c5
-    ("tc_bf16x3", (12, 11, 9, 1)): 2.0201e+08,   # c5
-    ("tc_bf16x3", (12, 9, 9, 3)): 2.6118e+08,   # c5
-    ("tc_bf16x3", (18, 6, 8, 0)): 6.0651e+08,   # c5
-    ("tc_bf16x3", (11, 11, 8, 0)): 1.2073e+08,   # c5
-    ("tc_bf16x3", (19, 7, 5, 0)): 6.4670e+08,   # c5
-    ("tc_bf16x3", (12, 5, 12, 0)): 7.2219e+07,   # c5
-    ("tc_bf16x3", (11, 8, 10, 0)): 8.4833e+06,   # c5
-    ("tc_bf16x3", (14, 7, 7, 0)): 1.7131e+07,   # c5
+    ("tc_bf16x3", (16, 6, 10, 0)): 5.0616e+08,   # c3
+    ("tc_bf16x3", (13, 9, 11, 0)): 1.3011e+08,   # c3
+    ("tc_bf16x3", (20, 5, 4, 0)): 3.6260e+08,   # c3
+    ("tc_bf16x3", (13, 8, 11, 0)): 9.5300e+07,   # c3
+    ("tc_bf16x3", (18, 6, 4, 0)): 1.4390e+08,   # c3
+    ("tc_bf16x3", (20, 8, 8, 0)): 4.3428e+09,   # c5
+    ("tc_bf16x3", (18, 8, 9, 1)): 3.3585e+09,   # c5
+    ("tc_bf16x3", (14, 9, 8, 5)): 3.5387e+09,   # c5
+    ("tc_bf16x3", (21, 7, 7, 0)): 4.2378e+09,   # c5
+    ("tc_bf16x3", (19, 8, 8, 0)): 2.1324e+09,   # c5
+    ("tc_bf16x3", (13, 10, 11, 0)): 2.4117e+08,   # c5
+    ("tc_bf16x3", (18, 6, 9, 0)): 1.1468e+09,   # c5
+    ("tc_bf16x3", (13, 14, 3, 0)): 1.0962e+09,   # c5
+    ("tc_bf16x3", (12, 9, 9, 3)): 2.6126e+08,   # c5
+    ("tc_bf16x3", (12, 11, 9, 1)): 2.0128e+08,   # c5
+    ("tc_bf16x3", (18, 6, 8, 0)): 6.0639e+08,   # c5
+    ("tc_bf16x3", (19, 7, 5, 0)): 6.4657e+08,   # c5
+    ("tc_bf16x3", (11, 11, 8, 0)): 5.2865e+07,   # c5
+    ("tc_bf16x3", (12, 5, 12, 0)): 7.2299e+07,   # c5
+    ("tc_bf16x3", (13, 3, 10, 0)): 4.6098e+06,   # c5
+    ("tc_bf16x3", (11, 8, 10, 0)): 8.4805e+06,   # c5
+    ("tc_bf16x3", (17, 5, 5, 0)): 3.3671e+07,   # c5
+    ("tc_bf16x3", (16, 6, 6, 0)): 3.3717e+07,   # c5
 }
 
 
