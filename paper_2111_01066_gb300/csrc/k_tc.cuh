@@ -26,15 +26,21 @@
 // Roles (480 threads, one CTA per SM, persistent over tiles):
 //   warps 0-3  epilogue: TMEM -> registers -> C (lane = tile row)
 //   warp  4    TMEM allocation; lane 0 issues tcgen05.mma and commits
+//              (on an SM pair: lane 0 of the even CTA; the odd CTA's lane 0
+//              forwards its readiness to the even CTA's barriers)
 //   warps 5-12 loaders: A gathers into the A ring, or, when A is fetched by
 //              TMA (and is not the TF32 4M operand itself), the fp32 ->
 //              operand-plane converters (in place)
 //   warp  13   A producer: when A is stored as [contracted..., free...] its
 //              tiles are fetched by one tensor-map load per k chunk
-//   warp  14   B' producer: one bulk copy of the (n tile, k chunk) image per k chunk
+//   warp  14   B' producer: one bulk copy of the (n tile, k chunk) image per k
+//              chunk (two, of half planes, on an SM pair)
 // Two rings decouple the operands: a deep ring of 16-32 KB A slots (more of
-// the streamed operand in flight for the memory-bound steps) and a shallow
-// ring of B' slots (B' comes from L2).
+// the streamed operand in flight for the memory-bound steps) and a shallower
+// ring of B' slots (B' comes from L2); a chunk's A and B' complete on the A
+// slot's barrier, so the MMA thread waits once per chunk.
+// SM pairs (PAIR): 2-CTA clusters, the even CTA issuing cta_group::2 MMAs of
+// 256 rows over both CTAs' shared memory and TMEM.
 // Every mbarrier wait is bounded by a globaltimer deadline; on expiry the
 // kernel records TN_ERR_TIMEOUT in *err, every role leaves its loop, and the
 // CTA frees its TMEM and returns.
