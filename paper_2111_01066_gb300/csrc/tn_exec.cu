@@ -146,6 +146,11 @@ struct StepLaunch {
   int64_t split_off = 0;   // split-K partials inside the workspace
   int64_t c_total = 0;     // elements of C (all instances)
   int smem = 0;
+  // B' images built ahead of the chunks (the step's B depends on no slice):
+  // built by the prologue of class bimg_cls (0 once per plan, 2 once per
+  // batch) into bimg_own; null: built with every launch in the workspace
+  uint8_t* bimg_own = nullptr;
+  int bimg_cls = -1;
 };
 
 static bool is_tc(int kid) { return kid >= K_TC_TF32 && kid <= K_TC_FP16X3_3M; }
@@ -370,15 +375,42 @@ static int pair_clusters() {
   return n;
 }
 
-template <int MODE, int CM, bool PAIR>
-static void launch_tc(const TcArgs& t, const StepLaunch& L, int grid, cudaStream_t s) {
-  // one CTA per B' image block at a time
+// The B' images of a tensor-core step into t.bimg: one CTA per image block at a time.
+template <int MODE, int CM>
+static void launch_prep(const TcArgs& t, cudaStream_t s) {
   const int64_t n_blocks = (int64_t)t.g.n_inst * t.n_nt * t.n_kc;
   const int pgrid = (int)std::max<int64_t>(1, std::min<int64_t>(n_blocks, (int64_t)sm_count() * 16));
   if constexpr (CM == 4)
     k_tc_prep_b<MODE><<<pgrid, 256, 0, s>>>(t);
   else
     k_tc_prep_b3<MODE><<<pgrid, 256, 0, s>>>(t);
+}
+static void launch_prep_kid(const TcArgs& t, int kid, cudaStream_t s) {
+  switch (kid) {
+    case K_TC_TF32:
+      launch_prep<TC_TF32, 4>(t, s);
+      break;
+    case K_TC_BF16X3:
+      launch_prep<TC_BF16X3, 4>(t, s);
+      break;
+    case K_TC_TF32_3M:
+      launch_prep<TC_TF32, 3>(t, s);
+      break;
+    case K_TC_BF16X3_3M:
+      launch_prep<TC_BF16X3, 3>(t, s);
+      break;
+    case K_TC_FP16X3:
+      launch_prep<TC_FP16X3, 4>(t, s);
+      break;
+    default:
+      launch_prep<TC_FP16X3, 3>(t, s);
+      break;
+  }
+}
+
+template <int MODE, int CM, bool PAIR>
+static void launch_tc(const TcArgs& t, const StepLaunch& L, int grid, cudaStream_t s) {
+  if (!L.bimg_own) launch_prep<MODE, CM>(t, s);   // else built ahead by a prologue
   // the shared-memory opt-in is a per-device function attribute: one bit per
   // device (ids < 64) records that it was set there; two threads racing on the
   // same bit both set the same value, which is harmless
@@ -418,7 +450,7 @@ static void launch_step(StepLaunch& L, uint8_t* ws, int32_t* err, cudaStream_t s
     return;
   }
   TcArgs t = L.tc;
-  t.bimg = ws;
+  t.bimg = L.bimg_own ? L.bimg_own : ws;
   t.err = err;
   if (t.n_split > 1) t.c_part = reinterpret_cast<float2*>(ws + L.split_off);
   if (t.n_tiles <= 0) return;
@@ -494,6 +526,7 @@ struct DeviceState {
   std::vector<GroupRun> groups;
   std::vector<int> group_at;                   // per step: its group run's index, or -1
   uint8_t* group_buf = nullptr;                // device memory of every Multi's arrays
+  std::vector<uint8_t*> own_imgs;              // B' images built ahead of the chunks (StepLaunch::bimg_own)
   cudaEvent_t done = nullptr;
   bool have_done = false;
   // the chunk's launch sequence as one CUDA graph, captured after the first
@@ -540,6 +573,45 @@ static GemmArgs step_args(const DeviceState& ds, const StepDesc& d, int kid, int
 static void launch_simt_multi(const DeviceState::GroupRun::Multi& m, cudaStream_t s) {
   for (float* am : m.amax) CK(cudaMemsetAsync(am, 0, sizeof(float), s));
   k_cgemm_simt_multi<<<m.blocks, 256, 0, s>>>(m.args, m.start, m.tiling, m.n);
+}
+
+// Dependence flags of a node (bit 0: on the slice id, bit 1: on the closed
+// output bits): a step's own flags; a leaf's from the wires its select fixes
+// and the slice bits it carries as batch bits.
+static int node_flags(const Plan& p, int node) {
+  const int nl = (int)p.leaves.size();
+  if (node >= nl) return p.steps[node - nl].dep_flags;
+  const LeafDesc& lf = p.leaves[node];
+  int f = lf.bmask ? 1 : 0;
+  for (int t = 0; t < lf.nfixed; ++t) f |= lf.fixed_kind[t] == 0 ? 1 : 2;
+  return f;
+}
+
+// B' images of per-chunk tensor-core steps whose B depends on no slice: one
+// buffer each, built by the prologue of B's class (once per plan, or once per
+// batch bitstring) instead of with every chunk.  Where a buffer cannot be had
+// the step keeps building its images per launch.
+static void setup_hoisted(Plan& p, DeviceState& ds) {
+  for (uint8_t* b : ds.own_imgs) cudaFree(b);
+  ds.own_imgs.clear();
+  for (size_t i = 0; i < p.steps.size(); ++i) {
+    StepLaunch& L = ds.launches[i];
+    L.bimg_own = nullptr;
+    L.bimg_cls = -1;
+    const StepDesc& d = p.steps[i];
+    if (!is_tc(L.kid) || !(d.dep_flags & 1)) continue;
+    const int bf = node_flags(p, d.b_node);
+    if (bf & 1) continue;
+    const int64_t img = L.tc.n_split > 1 ? L.split_off : L.ws_bytes;
+    uint8_t* buf = nullptr;
+    if (img <= 0 || cudaMalloc(&buf, (size_t)img) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    ds.own_imgs.push_back(buf);
+    L.bimg_own = buf;
+    L.bimg_cls = bf;
+  }
 }
 
 // Group runs from the plan's step groups and the kernels chosen so far.
@@ -697,6 +769,7 @@ static void ensure_device(Plan& p) {
   if (!in_arena(p.root.off, (int64_t)1 << p.root.rank, 1 << __builtin_popcount(p.root.bmask)))
     fail(TN_ERR_PLAN, "internal: root outside the arena");
   build_groups(p, *ds);
+  setup_hoisted(p, *ds);
 }
 
 void destroy_device_state(Plan* p) {
@@ -716,6 +789,7 @@ void destroy_device_state(Plan* p) {
   cudaFree(ds->root_part);
   cudaFree(ds->amax);
   cudaFree(ds->group_buf);
+  for (uint8_t* b : ds->own_imgs) cudaFree(b);
   if (ds->graph) cudaGraphExecDestroy(ds->graph);
   if (ds->done) cudaEventDestroy(ds->done);
   cudaSetDevice(cur);
@@ -763,11 +837,20 @@ static void run_prologue(Plan& p, cudaStream_t s, int cls) {
   DeviceState& ds = *p.dev;
   bool any = false;
   for (const StepDesc& d : p.steps) any = any || d.dep_flags == cls;
+  for (const StepLaunch& L : ds.launches) any = any || (L.bimg_own && L.bimg_cls == cls);
   if (!any) return;
   const int nl = (int)p.leaves.size();
   k_leaf_select<<<std::max(1, std::min(nl, 4096)), 128, 0, s>>>(ds.leaf_data, ds.leaf_desc, nl, ds.arena,
                                                                  ds.params, ds.counter);
   launch_class(p, s, [cls](int f) { return f == cls; });
+  // the B' images of later steps whose B this class completes
+  for (const StepLaunch& L : ds.launches) {
+    if (!L.bimg_own || L.bimg_cls != cls) continue;
+    TcArgs t = L.tc;
+    t.bimg = L.bimg_own;
+    t.err = ds.err;
+    launch_prep_kid(t, L.kid, s);
+  }
 }
 
 // Capture run_chunk once into a graph (on a private stream, thread-local
@@ -936,6 +1019,7 @@ static StepLaunch build_choice(const DeviceState& ds, const StepDesc& d, int kid
 // After the kernels of a plan changed: group runs, chunk graph and prologues anew.
 static void kernels_changed(Plan& p, DeviceState& ds) {
   build_groups(p, ds);
+  setup_hoisted(p, ds);
   if (ds.graph) {
     cudaGraphExecDestroy(ds.graph);
     ds.graph = nullptr;
@@ -991,7 +1075,9 @@ extern "C" tn_status tn_plan_autotune(tn_plan_t* h, int32_t reps, void* stream) 
     auto build = [&](int kid, int tn_log, int epi, int bslots, int pair) {
       return build_choice(ds, d, kid, tn_log, epi, bslots, pair);
     };
-    double best = time_launch(ds.launches[i]);
+    StepLaunch cur = ds.launches[i];
+    cur.bimg_own = nullptr;   // timed like the candidates: B' images built with the launch
+    double best = time_launch(cur);
     // kernel, tile width (log2 complex columns), write-back, B' slots, SM pairs
     std::vector<std::array<int, 5>> cands;
     const bool tc_mode = p.opts.precision != TN_PREC_FP32;
@@ -1209,7 +1295,7 @@ static int class_launches(const Plan& p, Pred in_class) {
   int n = 0;
   auto kernels_of = [&](int i) {
     const StepLaunch& L = p.dev->launches[i];
-    return is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) : 1;
+    return is_tc(L.kid) ? (L.tc.n_split > 1 ? 3 : 2) - (L.bimg_own ? 1 : 0) : 1;
   };
   for (size_t i = 0; i < p.steps.size(); ++i) {
     if (!in_class(p.steps[i].dep_flags)) continue;
@@ -1240,7 +1326,8 @@ extern "C" tn_status tn_plan_batch_launches(const tn_plan_t* h, int32_t* launche
   if (!h || !launches) fail(TN_ERR_ARG, "tn_plan_batch_launches: NULL argument");
   const Plan& p = h->plan;
   if (!p.dev) fail(TN_ERR_ARG, "tn_plan_batch_launches: call after the first tn_contract_slices");
-  const int n = class_launches(p, [](int f) { return f == 2; });
+  int n = class_launches(p, [](int f) { return f == 2; });
+  for (const StepLaunch& L : p.dev->launches) n += (L.bimg_own && L.bimg_cls == 2) ? 1 : 0;   // B' images
   *launches = n > 0 ? n + 1 : 0;   // + the leaf select ahead of them
   API_END
 }
