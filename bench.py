@@ -235,36 +235,35 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 1.92 / 1e3   # SMs x FP32 lanes x 2 flops x G
 # the profiled run), matched to the steps in launch order (profiles/c3_bf16x3_launch_list.md,
 # profiles/c5_bf16x3_launch_list.md)
 MEASURED_TRAFFIC = {
-    ("tc_bf16x3", (21, 8, 8, 0)): 8.7764e+09,   # c3
-    ("tc_bf16x3", (21, 7, 8, 0)): 6.3972e+09,   # c3
-    ("tc_bf16x3", (12, 10, 7, 7)): 5.2334e+09,   # c3
-    ("tc_bf16x3", (22, 4, 6, 0)): 2.6207e+09,   # c3
-    ("tc_bf16x3", (11, 10, 9, 5)): 1.1135e+09,   # c3
-    ("tc_bf16x3", (15, 7, 12, 0)): 1.0525e+09,   # c3
+    ("tc_bf16x3", (21, 8, 8, 0)): 8.7789e+09,   # c3
+    ("tc_bf16x3", (21, 7, 8, 0)): 6.4022e+09,   # c3
+    ("tc_bf16x3", (12, 10, 7, 7)): 5.1233e+09,   # c3
+    ("tc_bf16x3", (11, 10, 9, 5)): 1.1190e+09,   # c3
+    ("tc_bf16x3", (22, 4, 6, 0)): 2.6199e+09,   # c3
+    ("tc_bf16x3", (15, 7, 12, 0)): 1.0543e+09,   # c3
     ("tc_bf16x3", (19, 8, 5, 0)): 1.1935e+09,   # c3
-    ("tc_bf16x3", (16, 6, 10, 0)): 5.0616e+08,   # c3
-    ("tc_bf16x3", (13, 9, 11, 0)): 1.3011e+08,   # c3
-    ("tc_bf16x3", (20, 5, 4, 0)): 3.6260e+08,   # c3
-    ("tc_bf16x3", (13, 8, 11, 0)): 9.5300e+07,   # c3
-    ("tc_bf16x3", (18, 6, 4, 0)): 1.4390e+08,   # c3
-    ("tc_bf16x3", (20, 8, 8, 0)): 4.3428e+09,   # c5
-    ("tc_bf16x3", (18, 8, 9, 1)): 3.3585e+09,   # c5
-    ("tc_bf16x3", (14, 9, 8, 5)): 3.5387e+09,   # c5
-    ("tc_bf16x3", (21, 7, 7, 0)): 4.2378e+09,   # c5
-    ("tc_bf16x3", (19, 8, 8, 0)): 2.1324e+09,   # c5
-    ("tc_bf16x3", (13, 10, 11, 0)): 2.4117e+08,   # c5
-    ("tc_bf16x3", (18, 6, 9, 0)): 1.1468e+09,   # c5
-    ("tc_bf16x3", (13, 14, 3, 0)): 1.0962e+09,   # c5
-    ("tc_bf16x3", (12, 9, 9, 3)): 2.6126e+08,   # c5
-    ("tc_bf16x3", (12, 11, 9, 1)): 2.0128e+08,   # c5
-    ("tc_bf16x3", (18, 6, 8, 0)): 6.0639e+08,   # c5
-    ("tc_bf16x3", (19, 7, 5, 0)): 6.4657e+08,   # c5
-    ("tc_bf16x3", (11, 11, 8, 0)): 5.2865e+07,   # c5
-    ("tc_bf16x3", (12, 5, 12, 0)): 7.2299e+07,   # c5
-    ("tc_bf16x3", (13, 3, 10, 0)): 4.6098e+06,   # c5
-    ("tc_bf16x3", (11, 8, 10, 0)): 8.4805e+06,   # c5
-    ("tc_bf16x3", (17, 5, 5, 0)): 3.3671e+07,   # c5
-    ("tc_bf16x3", (16, 6, 6, 0)): 3.3717e+07,   # c5
+    ("tc_bf16x3", (16, 6, 10, 0)): 5.0618e+08,   # c3
+    ("tc_bf16x3", (13, 9, 11, 0)): 1.3029e+08,   # c3
+    ("tc_bf16x3", (20, 5, 4, 0)): 3.6322e+08,   # c3
+    ("tc_bf16x3", (13, 8, 11, 0)): 9.5713e+07,   # c3
+    ("tc_bf16x3", (18, 6, 4, 0)): 1.4450e+08,   # c3
+    ("tc_bf16x3", (20, 8, 8, 0)): 4.3654e+09,   # c5
+    ("tc_bf16x3", (18, 8, 9, 1)): 3.3820e+09,   # c5
+    ("tc_bf16x3", (14, 9, 8, 5)): 3.8655e+09,   # c5
+    ("tc_bf16x3", (21, 7, 7, 0)): 4.2418e+09,   # c5
+    ("tc_bf16x3", (19, 8, 8, 0)): 2.1476e+09,   # c5
+    ("tc_bf16x3", (13, 10, 11, 0)): 2.3925e+08,   # c5
+    ("tc_bf16x3", (18, 6, 9, 0)): 1.1464e+09,   # c5
+    ("tc_bf16x3", (13, 14, 3, 0)): 1.0961e+09,   # c5
+    ("tc_bf16x3", (12, 9, 9, 3)): 2.6187e+08,   # c5
+    ("tc_bf16x3", (12, 11, 9, 1)): 2.0207e+08,   # c5
+    ("tc_bf16x3", (18, 6, 8, 0)): 6.0673e+08,   # c5
+    ("tc_bf16x3", (19, 7, 5, 0)): 6.4703e+08,   # c5
+    ("tc_bf16x3", (11, 11, 8, 0)): 5.2409e+07,   # c5
+    ("tc_bf16x3", (12, 5, 12, 0)): 7.2190e+07,   # c5
+    ("tc_bf16x3", (13, 3, 10, 0)): 4.4308e+06,   # c5
+    ("tc_bf16x3", (11, 8, 10, 0)): 8.4800e+06,   # c5
+    ("tc_bf16x3", (16, 6, 6, 0)): 3.3713e+07,   # c5
 }
 
 
