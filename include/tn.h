@@ -253,9 +253,13 @@ tn_status tn_plan_model_time(const tn_plan_t* plan, double peak_flops, double pe
  *   out_amplitudes   DEVICE array of n_batches * 2^k interleaved complex128,
  *                    accumulated (+=) in FP64; owned by the caller.
  *   stream           cudaStream_t; the call is asynchronous on it.
- * The first call on a plan allocates the plan's device arena (freed by
- * tn_plan_destroy) and uploads the leaf tensors; that call synchronises.  A
- * range beyond 2^S, n_batches < 1 or a NULL pointer gives TN_ERR_ARG.  Not
+ * The first call on a plan allocates the plan's device arena, workspace and
+ * the B' image buffers of steps whose B operand depends on no slice (all freed
+ * by tn_plan_destroy) and uploads the leaf tensors; that call synchronises.
+ * Steps that depend on no slice, and those B' images, are computed once per
+ * plan, or once per batch when they depend on the closed bits (main text,
+ * section III: the major part of the network is shared by a correlated batch).
+ * A range beyond 2^S, n_batches < 1 or a NULL pointer gives TN_ERR_ARG.  Not
  * thread-safe per plan. */
 tn_status tn_contract_slices(tn_plan_t* plan, uint64_t slice_first, uint64_t slice_count,
                              const uint64_t* open_bitstrings, int32_t n_batches,
@@ -303,9 +307,10 @@ tn_status tn_plan_get_tuning(const tn_plan_t* plan, int32_t* out, int32_t cap, i
  * plan: every step gets the given kernel as the autotuner would have built it.
  * n must be n_steps * TN_TUNING_INTS; an unknown kernel id, or a choice the
  * step cannot take (a tensor-core kernel for the FP32 mode, rings that do not
- * fit), gives TN_ERR_ARG and leaves the plan's kernels unchanged.  Host only;
- * the next contract call captures the chunk graph again and reruns the
- * prologues. */
+ * fit), gives TN_ERR_ARG and leaves the plan's kernels unchanged.  Launches
+ * nothing; it may resize the plan's device workspace and image buffers (which
+ * synchronises the device).  The next contract call captures the chunk graph
+ * again and reruns the prologues. */
 tn_status tn_plan_set_tuning(tn_plan_t* plan, const int32_t* in, int32_t n);
 
 /* Plan selection by measured time (SI, TN section: the order whose measured
